@@ -1,0 +1,393 @@
+"""Pins of the oracle's particle side against closed forms, brute force and
+the paper's printed tables.
+
+* pushers (Sec. 2): |u| and the gyration phase per step in a pure B field;
+  the Vay mover leaves a force-free (E + v x B = 0) momentum unchanged.
+* E x B drift test of Sec. 4.3 (dipole + corotation field, particle at rest at
+  3 r0 on the equator, analytic drift 0.15 c).
+* move + polar reflection (Sec. 3.3, 3.4.2): the axisymmetric orbit in a
+  uniform B_z equals an independent 2-D Cartesian integration.
+* Villasenor-Buneman deposit (Sec. 2, 3.3): brute-force time integral of the
+  moving unit square's flux through each face; exact charge conservation.
+* filter (App. B): the printed remapping tables; Gauss law with filtered charge.
+* surface injection (Sec. 5.3): total charge against the rotating-conductor
+  surface charge.
+* equator pair test (Sec. 4.2.1): deletion steps and the inverse-square E_r.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.oracle import courant_dt, push
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rot_angle_z(a, b):
+    return math.atan2(a[0] * b[1] - a[1] * b[0], a[0] * b[0] + a[1] * b[1])
+
+
+@pytest.mark.parametrize("pusher", ["vay", "boris"])
+@pytest.mark.parametrize("wdt", [0.1, 1.0, 5.0])
+def test_pure_b_gyration(oracle_mod, pusher, wdt):
+    u = np.array([0.8, -0.3, 0.45])
+    g = math.sqrt(1 + u @ u)
+    B = np.array([0.0, 0.0, 2.0])
+    qmdt = wdt / 2.0
+    un = push(pusher, qmdt, np.zeros(3), B, u)
+    assert abs(np.linalg.norm(un) - np.linalg.norm(u)) < 1e-14 * np.linalg.norm(u)
+    assert un[2] == pytest.approx(u[2], abs=1e-15)
+    # rotation by -2 atan(omega_c dt / (2 gamma)) about +z for positive charge
+    expect = -2.0 * math.atan(qmdt * 2.0 / (2.0 * g))
+    assert rot_angle_z(u, un) == pytest.approx(expect, abs=1e-13)
+
+
+def test_vay_keeps_force_free_momentum(oracle_mod):
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        B = rng.standard_normal(3) * 5.0
+        v = rng.standard_normal(3)
+        v *= 0.9 * rng.random() / np.linalg.norm(v)
+        E = -np.cross(v, B)
+        u = v / math.sqrt(1 - v @ v)
+        for qmdt in (0.01, 1.0, 30.0):
+            uv = push("vay", qmdt, E, B, u)
+            assert np.max(np.abs(uv - u)) < 1e-12 * (1 + np.linalg.norm(u))
+    # Boris does not have this property at large omega_c dt
+    ub = push("boris", 30.0, E, B, u)
+    assert np.max(np.abs(ub - u)) > 1e-3
+
+
+def _drift_run(pusher, wdt, nsteps=2000):
+    # dipole + corotation field with r0/R_l = 0.05 (Sec. 4.3)
+    p = O.params(nr=32, nth=32, r_min=1.0, r_max=10.0, r_map="log", th_map="linear",
+                 vacuum="dipole_corot", omega=0.05, pusher=pusher)
+    dt_max = courant_dt(p, 0.5)
+    # omega_c is held fixed and large (Larmor radius ~1e-4 r), so the drifts the
+    # paper calls negligible (grad-B, centrifugal) stay below 1e-3 of E x B;
+    # omega_c dt is varied through dt.  |B| at r = 3 on the equator is b0 / 27.
+    omega_c = 50.0 / dt_max
+    p.dt = wdt / omega_c
+    p.b0 = 27.0 * omega_c
+    o = O.Oracle(p)
+    x1 = float(o.f_r_inv(3.0))
+    o.load([x1], [16.0], [0.0], [0.0], [0.0], [1e-12])
+    vph = []
+    for _ in range(nsteps):
+        o.step(1)
+        d = o.particles()
+        u = np.array([d["ur"][0], d["uth"][0], d["uph"][0]])
+        vph.append(u[2] / math.sqrt(1 + u @ u))
+    return abs(np.mean(vph)) / 0.15
+
+
+@pytest.mark.parametrize("wdt", [0.1, 1.0, 10.0, 50.0])
+def test_exb_drift_vay(oracle_mod, wdt):
+    assert _drift_run("vay", wdt) == pytest.approx(1.0, abs=0.02)
+
+
+def test_exb_drift_boris(oracle_mod):
+    assert _drift_run("boris", 0.1) == pytest.approx(1.0, abs=0.02)
+    # Sec. 4.3: Boris departs from the drift once omega_c dt >~ 2
+    assert abs(_drift_run("boris", 50.0) - 1.0) > 0.05
+
+
+@pytest.mark.parametrize("pusher", ["vay", "boris"])
+@pytest.mark.parametrize("Rc,rho", [(0.5, 0.3), (0.5, 0.8), (0.5, 0.5004)])
+def test_uniform_bz_orbit_matches_cartesian(oracle_mod, pusher, Rc, rho):
+    """Orbit in uniform B_z: axisymmetric bookkeeping (rotate back to phi = 0
+    every step, reflection through the axis) against a plain 2-D integration."""
+    p = O.params(nr=64, nth=64, r_min=1.0, r_max=10.0, r_map="log", th_map="linear",
+                 vacuum="uniform_bz", pusher=pusher)
+    p.dt = courant_dt(p, 0.5)
+    qmB = 0.3 / p.dt  # omega_c dt = 0.3 / gamma
+    p.b0 = qmB
+    o = O.Oracle(p)
+    z0 = 5.0
+    # start on the orbit point farthest from the axis, moving in +phi
+    X0 = Rc + rho
+    umag = rho * qmB  # gyroradius = u / (q/m B)
+    r0 = math.hypot(X0, z0)
+    th0 = math.atan2(X0, z0)
+    # velocity -y (positive charge gyrates clockwise about +z): u_phi = -umag
+    o.load([float(o.f_r_inv(r0))], [float(o.f_th_inv(th0))], [0.0], [0.0], [-umag], [1e-12])
+    # 2-D Cartesian reference: u^{n+1/2} = rotation of u^{n-1/2}; x += v dt
+    x = np.array([X0, 0.0])
+    u = np.array([0.0, -umag])
+    g = math.sqrt(1 + umag**2)
+    ang = -2.0 * math.atan(qmB * p.dt / (2.0 * g))
+    c, s = math.cos(ang), math.sin(ang)
+    minR = 1e9
+    for n in range(400):
+        o.step(1)
+        u = np.array([c * u[0] - s * u[1], s * u[0] + c * u[1]])
+        x = x + u / g * p.dt
+        d = o.particles()
+        r = float(o.f_r(d["x1"][0]))
+        th = float(o.f_th(d["x2"][0]))
+        R, Z = r * math.sin(th), r * math.cos(th)
+        Rx = float(np.hypot(*x))
+        minR = min(minR, Rx)
+        assert R == pytest.approx(Rx, abs=1e-10)
+        assert Z == pytest.approx(z0, abs=1e-10)
+        # momentum: cylindrical components against the 2-D reference
+        uR = d["ur"][0] * math.sin(th) + d["uth"][0] * math.cos(th)
+        assert uR == pytest.approx((x @ u) / Rx, abs=1e-9)
+        assert d["uph"][0] == pytest.approx((x[0] * u[1] - x[1] * u[0]) / Rx, abs=1e-9)
+    assert minR < abs(Rc - rho) + 1e-2
+
+
+# --------------------------------------------------------------------------
+# Villasenor-Buneman deposit
+# --------------------------------------------------------------------------
+def _tiny_oracle(n=4, n_filt=0):
+    p = O.params(nr=n, nth=n, r_min=1.0, r_max=2.0, r_map="linear", th_map="linear", n_filt=n_filt)
+    p.dt = 1e-3
+    return O.Oracle(p)
+
+
+def _brute_flux(o, qw, a, b, M=40000):
+    """Time integral of q v times the moving unit square's overlap with each
+    dual face, midpoint rule with M samples (independent of the VB formulas)."""
+    g = o.g
+    fr = np.zeros(o.flux_shape[1:])
+    fth = np.zeros(o.flux_shape[1:])
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    d = b - a
+    t = (np.arange(M) + 0.5) / M
+    X = a[0] + t * d[0]
+    Y = a[1] + t * d[1]
+
+    def overlap(c, k):  # overlap of [c-1/2, c+1/2] with [k-1/2, k+1/2]
+        return np.clip(1.0 - np.abs(c - k), 0.0, None)
+
+    for i in range(-g, o.nr + g):
+        # vertical face x = i + 1/2 : the square straddles it when |X - (i+1/2)| < 1/2
+        on = np.abs(X - (i + 0.5)) < 0.5
+        if not on.any():
+            continue
+        for j in range(0, o.nth + 1):
+            fr[i + g, j] = qw * d[0] * np.sum(on * overlap(Y, j)) / M
+    for i in range(-g, o.nr + g + 1):
+        for j in range(0, o.nth):
+            on = np.abs(Y - (j + 0.5)) < 0.5
+            fth[i + g, j] = qw * d[1] * np.sum(on * overlap(X, i)) / M
+    return fr, fth
+
+
+def _cic(o, x1, x2):
+    q = np.zeros(o.flux_shape[1:])
+    i0, j0 = math.floor(x1), math.floor(x2)
+    w1, w2 = x1 - i0, x2 - j0
+    for di, wi in ((0, 1 - w1), (1, w1)):
+        for dj, wj in ((0, 1 - w2), (1, w2)):
+            if 0 <= j0 + dj <= o.nth:
+                q[i0 + di + o.g, j0 + dj] += wi * wj
+    return q
+
+
+def _div(o, fr, fth):
+    """Net outflow of a flux pair from each node's dual cell."""
+    d = np.zeros(o.flux_shape[1:])
+    d += fr
+    d[1:, :] -= fr[:-1, :]
+    d[:, : o.nth] += fth[:, : o.nth]
+    d[:, 1 : o.nth + 1] -= fth[:, : o.nth]
+    return d
+
+
+def _random_paths(n, rng, nmax=4):
+    out = []
+    for _ in range(n):
+        a = np.array([rng.uniform(0.0, nmax), rng.uniform(0.0, nmax)])
+        b = a + rng.uniform(-0.95, 0.95, 2)
+        b[1] = np.clip(b[1], 0.0, nmax)
+        out.append((a, b))
+    # paths through cell corners and along grid lines
+    out += [(np.array([1.2, 1.3]), np.array([2.4, 2.6])), (np.array([1.5, 2.0]), np.array([2.5, 2.0])),
+            (np.array([2.0, 0.3]), np.array([2.0, 1.2])), (np.array([0.7, 0.2]), np.array([1.3, 0.0]))]
+    return out
+
+
+def test_vb_matches_brute_force_integral(oracle_mod):
+    o = _tiny_oracle()
+    rng = np.random.default_rng(11)
+    for a, b in _random_paths(12, rng):
+        rc, fr, fth = o.deposit_path(0.7, a[0], a[1], b[0], b[1])
+        assert rc == 0
+        br, bt = _brute_flux(o, 0.7, a, b)
+        assert np.max(np.abs(fr - br)) < 1e-4, (a, b)
+        assert np.max(np.abs(fth - bt)) < 1e-4, (a, b)
+
+
+def test_vb_conserves_charge_exactly(oracle_mod):
+    o = _tiny_oracle()
+    rng = np.random.default_rng(12)
+    for a, b in _random_paths(200, rng):
+        rc, fr, fth = o.deposit_path(1.0, a[0], a[1], b[0], b[1])
+        dq = _cic(o, *b) - _cic(o, *a)
+        assert np.max(np.abs(dq + _div(o, fr, fth))) < 1e-14
+
+
+def test_vb_additive_along_path(oracle_mod):
+    o = _tiny_oracle()
+    rng = np.random.default_rng(13)
+    for a, b in _random_paths(10, rng):
+        _, fr, fth = o.deposit_path(1.0, a[0], a[1], b[0], b[1])
+        sr, st = np.zeros_like(fr), np.zeros_like(fth)
+        pts = [a + (b - a) * k / 1000.0 for k in range(1001)]
+        for p0, p1 in zip(pts[:-1], pts[1:]):
+            o.deposit_path(1.0, p0[0], p0[1], p1[0], p1[1], sr, st)
+        assert np.max(np.abs(sr - fr)) < 1e-12
+        assert np.max(np.abs(st - fth)) < 1e-12
+
+
+def test_vb_rejects_courant_violation(oracle_mod):
+    o = _tiny_oracle()
+    rc, _, _ = o.deposit_path(1.0, 1.5, 1.5, 3.2, 1.5)  # crosses two grid lines
+    assert rc == -1
+
+
+# --------------------------------------------------------------------------
+# filter
+# --------------------------------------------------------------------------
+def test_filter_fold_weights_match_paper_table(oracle_mod):
+    gold = json.load(open(os.path.join(GOLDEN, "filter_fold_weights.json")))
+    nth = 8
+    o = _tiny_oracle(n=nth)
+    row = o.g + 2
+    for name, half, sign in (("r_phi", 0, +1), ("theta", 1, -1)):
+        nj = nth if half else nth + 1
+        # response to a delta at k: out(j) = V_{k-j}(j); column sums remove the radial pass
+        W = np.zeros((nj, nj))
+        for k in range(nj):
+            f = np.zeros(o.flux_shape[1:])
+            f[row, k] = 1.0
+            W[:, k] = o.filter_pass(f, half, sign).sum(axis=0)[:nj]
+        for key, V in gold[name].items():
+            j0 = eval(key.split("=")[1], {"nth": nth})
+            got = [W[j0, j0 + l] if 0 <= j0 + l < nj else 0.0 for l in (-1, 0, 1)]
+            assert got == pytest.approx(V, abs=1e-15), (name, key, got)
+        # interior rows are the plain 1-2-1 weights
+        assert [W[4, 3], W[4, 4], W[4, 5]] == pytest.approx([0.25, 0.5, 0.25])
+
+
+def test_filter_interior_is_separable_121(oracle_mod):
+    o = _tiny_oracle(n=8)
+    f = np.zeros(o.flux_shape[1:])
+    f[o.g + 4, 4] = 1.0
+    out = o.filter_pass(f, 0, +1)
+    k = np.array([0.25, 0.5, 0.25])
+    np.testing.assert_allclose(out[o.g + 3 : o.g + 6, 3:6], np.outer(k, k), atol=1e-16)
+    assert out.sum() == pytest.approx(1.0)
+
+
+# --------------------------------------------------------------------------
+# whole-step invariants
+# --------------------------------------------------------------------------
+def _plasma_oracle(n_filt, vacuum="monopole_rotator", th_map="linear", nsteps=0, seed=0):
+    from paper_1407_1810_gb300 import synthetic
+
+    N = 16
+    p = O.params(nr=N, nth=N, r_min=1.0, r_max=6.0, r_map="log", th_map=th_map, n_filt=n_filt,
+                 absorb_cells=4, absorb_profile="linear", vacuum=vacuum, b0=20.0, omega=0.2,
+                 t_spin=0.5)
+    p.dt = courant_dt(p, 0.5)
+    o = O.Oracle(p)
+    d = synthetic.pair_plasma(N, N, 3, 0.5, 0.01, seed)
+    o.load(d["x1"], d["x2"], d["ur"], d["uth"], d["uph"], d["qw"])
+    # break the pair co-location so Q is not identically zero
+    o.step(2)
+    o.gauss_snapshot()
+    return o
+
+
+@pytest.mark.parametrize("n_filt", [0, 1, 3])
+@pytest.mark.parametrize("th_map", ["linear", "equal_area"])
+def test_gauss_law_holds_with_filtered_charge(oracle_mod, n_filt, th_map):
+    o = _plasma_oracle(n_filt, th_map=th_map)
+    n0 = o.num_particles()
+    assert o.step(40) == 0
+    assert o.counters()["deleted"] > 0  # particles crossed both conductors
+    assert o.num_particles() < n0
+    assert o.gauss_residual() < 1e-12
+
+
+def test_gauss_law_detects_a_wrong_filter_fold(oracle_mod):
+    """Control: filtering the charge with the odd fold breaks Gauss at the
+    axis, so the invariant above really tests the fold sign."""
+    o = _plasma_oracle(1)
+    o.step(10)
+    q = o.node_charge()
+    good = o.filter_pass(q, 0, +1)
+    bad = o.filter_pass(q, 0, -1)
+    assert np.max(np.abs(good - bad)) > 1e-6
+
+
+# --------------------------------------------------------------------------
+# injection and deletion
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("nth", [64, 63])
+def test_injection_total_charge(oracle_mod, nth):
+    b0, om, fin, npp = 3.0, 0.2, 0.5, 2
+    p = O.params(nr=32, nth=nth, r_min=1.0, r_max=10.0, r_map="log", th_map="linear",
+                 vacuum="monopole_rotator", b0=b0, omega=om, t_spin=0.0, inject=1,
+                 pairs_per_cell=npp, f_inj=fin)
+    p.dt = courant_dt(p, 0.5)
+    o = O.Oracle(p)
+    o.step(1)  # no particles yet: plasma fields stay 0, then injection
+    d = o.particles()
+    rb0 = float(o.f_r(0.5))
+    # surface charge of the rotating conductor, |sigma| = 2 b0 r0^4 Omega |cos th| / r^3
+    # at r = f_r(1/2); integrated over the sphere of radius r0 = 1
+    expect = fin * 4.0 * math.pi * b0 * om / rb0**3
+    assert d["qw"][d["qw"] > 0].sum() == pytest.approx(expect, rel=2e-3)
+    assert d["qw"].sum() == pytest.approx(0.0, abs=1e-15)
+    ncell = nth if nth % 2 == 0 else nth - 1  # the equator cell of odd nth has sigma = 0
+    assert len(d["qw"]) == 2 * npp * ncell
+    assert np.all(d["x1"] == 0.5)
+    assert o.counters()["next_id"] == 2 * npp * nth
+
+
+@pytest.mark.parametrize("th_map", ["linear", "equal_area"])
+def test_equator_pair_deletion_and_inverse_square(oracle_mod, th_map):
+    """Sec. 4.2.1: a pair shot radially along the equator at 0.95 c; both
+    members are deleted once their filtered shape is inside a conductor, and
+    the inverse-square E_r of the charge left on the inner conductor remains
+    once the transient has left through the lossy layer.
+
+    Uniform radial cells: on a coarse log-r grid (28 cells per r0 here, 256 in
+    the paper's runs) the broadband radiation of the deletion is partly
+    trapped near the star, where the grid's cut-off frequency is highest."""
+    N, nf, L = 64, 3, 16
+    p = O.params(nr=N, nth=N, r_min=1.0, r_max=10.0, r_map="linear", th_map=th_map, n_filt=nf,
+                 absorb_cells=L, absorb_profile="linear")
+    p.dt = courant_dt(p, 0.5)
+    o = O.Oracle(p)
+    rmid = 5.5
+    x1 = float(o.f_r_inv(rmid))
+    ur = 0.95 / math.sqrt(1 - 0.95**2)
+    Q = 1e-6
+    o.load([x1, x1], [N / 2, N / 2], [-ur, ur], [0.0, 0.0], [0.0, 0.0], [Q, -Q])
+    # ballistic straight lines: step of deletion = first n with floor(x1) past the ghost depth
+    v = 0.95 * p.dt
+    n_in = next(n for n in range(1, 10**6) if math.floor(o.f_r_inv(rmid - v * n)) < -(nf + 1))
+    n_out = next(n for n in range(1, 10**6) if math.floor(o.f_r_inv(rmid + v * n)) >= N + nf + 1)
+    for n in range(1, max(n_in, n_out) + 1):
+        o.step(1)
+        ids = set(o.particles()["id"].tolist())
+        assert (0 in ids) == (n < n_in), n
+        assert (1 in ids) == (n < n_out), n
+    tc = 10.0 - 1.0
+    o.step(int(4.0 * tc / p.dt) - max(n_in, n_out))
+    f = o.fields()
+    rb = o.f_r(np.arange(N) + 0.5)
+    inner = slice(4, N - L - 4)
+    exact = Q / (4 * math.pi * rb[inner] ** 2)
+    err = np.max(np.abs(f[0, inner, :] - exact[:, None])) / np.max(exact)
+    assert err < 0.02, err
+    assert o.gauss_residual() < 1e-10
