@@ -1,0 +1,181 @@
+/*
+ * picsar.h -- C-ABI of the GB300 (sm_103a) PICsar particle hot path.
+ *
+ * The library advances the 2.5D axisymmetric, relativistic, electromagnetic,
+ * charge-conservative particle-in-cell method of Belyaev, "PICsar" (arXiv
+ * 1407.1810) on its body-fitted, stretchable spherical (r, theta) grid:
+ *   per step: field gather from the staggered Yee mesh (Eq. offseteq) plus the
+ *   analytic "initial" field (Sec. 5.2); Vay or Boris push (Sec. 2) and the
+ *   axisymmetric move (Sec. 3.3); the particle boundary rule (Sec. 3.4.2);
+ *   Villasenor-Buneman charge-conserving deposit (Eq. Jcons, Sec. 3.3);
+ *   N_filt passes of the 1-2-1 filter with the polar remap (App. B); the Yee
+ *   field update in integral form (App. A, Eqs. discreteeq, erpolarupdate) with
+ *   conducting radial boundaries and the lossy layer (Sec. 3.4.1, Eq. EBcond);
+ *   surface pair injection (Sec. 5.3, Eq. volinjeq).
+ *
+ * Units: Lorentz-Heaviside with c = 1 (Sec. 2).  Grid: nr x nth cells, nodes
+ * i = 0..nr (radial, i = 0 on the inner conductor r = r_min) and j = 0..nth
+ * (j = 0 and j = nth on the polar axis).  A particle's grid coordinate is
+ * (x1, x2) with r = f_r(x1), theta = f_th(x2) (Sec. 3.2).  Momentum is
+ * u = gamma v in the local spherical basis (u_r, u_th, u_ph).  qw is the
+ * signed macro-charge; the mass is |qw| / q_over_m.
+ *
+ * Conventions of every call:
+ *   - the return value is PIC_OK (0) or a negative PIC_E* code; the message of
+ *     the last failure on the calling thread is pic_last_error();
+ *   - the library copies its inputs and never keeps a caller pointer;
+ *   - outputs go to caller-owned buffers; a pointer argument marked "mem" is a
+ *     host pointer when mem == PIC_MEM_HOST and a device pointer of the
+ *     context's device when mem == PIC_MEM_DEVICE;
+ *   - all GPU work runs on the stream given to pic_init_grid (a cudaStream_t,
+ *     NULL = the legacy default stream).  pic_step only enqueues work; calls
+ *     that return data to the host synchronise that stream.
+ * Errors found by a kernel (a particle moving more than one cell in a step, a
+ * full particle buffer, a non-finite momentum) are latched in the context and
+ * reported by the next call that synchronises.
+ */
+#ifndef PICSAR_H
+#define PICSAR_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PIC_OK 0
+#define PIC_EINVAL (-1)    /* bad argument or descriptor */
+#define PIC_ENOMEM (-2)    /* device allocation failed */
+#define PIC_ECUDA (-3)     /* a CUDA call failed */
+#define PIC_ECAPACITY (-4) /* particle buffer full */
+#define PIC_ENAN (-5)      /* non-finite particle momentum or position */
+#define PIC_ECOURANT (-6)  /* a particle crossed more than one cell line in one step */
+#define PIC_ETIMEOUT (-7)  /* a bounded device-side wait gave up */
+
+/* enumerations */
+enum { PIC_R_LINEAR = 0, PIC_R_LOG = 1 };                  /* f_r, Sec. 3.2 */
+enum { PIC_TH_LINEAR = 0, PIC_TH_EQUAL_AREA = 1 };         /* f_th, Sec. 3.2 */
+enum { PIC_ABSORB_NONE = 0, PIC_ABSORB_LINEAR = 1, PIC_ABSORB_QUADRATIC = 2 };
+enum { PIC_VAC_NONE = 0, PIC_VAC_MONOPOLE = 1, PIC_VAC_MONOPOLE_ROTATOR = 2,
+       PIC_VAC_UNIFORM_BZ = 3, PIC_VAC_DIPOLE_COROT = 4 };
+enum { PIC_FP64 = 0, PIC_FP32 = 1 };
+enum { PIC_VAY = 0, PIC_BORIS = 1 };
+enum { PIC_MEM_HOST = 0, PIC_MEM_DEVICE = 1 };
+enum { PIC_FIELDS_PLASMA = 0 };
+
+typedef struct pic_ctx pic_ctx;
+
+/* Grid and physics of one simulation.  Zero-initialise, then set. */
+typedef struct pic_desc {
+  int32_t nr, nth;           /* cells in r and theta (>= 2 each) */
+  double r_min, r_max;       /* inner (r0) and outer conductor radius, r_min > 0 */
+  int32_t r_map, th_map;     /* PIC_R_*, PIC_TH_* stretching functions (Sec. 3.2) */
+  double courant;            /* used when dt <= 0: dt = courant * min cell size */
+  double dt;                 /* time step; > 0 overrides courant */
+  int32_t n_filt;            /* 1-2-1 filter passes on the current (App. B), 0..16 */
+  int32_t absorb_cells;      /* lossy layer width in cells (Sec. 3.4.1) */
+  int32_t absorb_profile;    /* PIC_ABSORB_* */
+  double absorb_sigma_max;   /* sigma* at the outer conductor; <= 0: 2/L linear, 3/L quadratic */
+  int32_t vacuum;            /* PIC_VAC_* analytic field added at the particle (Sec. 5.2, 4.3) */
+  double b0;                 /* field strength at r0 */
+  double omega;              /* final angular velocity of the star; R_l = c / omega */
+  double t_spin;             /* linear spin-up time (Sec. 5.2); 0 = none */
+  int32_t inject;            /* 1: surface pair injection each step (Sec. 5.3) */
+  int32_t pairs_per_cell;    /* pairs injected per surface cell per step (default 2) */
+  double f_inj;              /* injection multiplier, 0 < f_inj <= 1 (Eq. volinjeq) */
+  int32_t precision;         /* PIC_FP64 (plain FP64 path) or PIC_FP32 (cell+offset path) */
+  int32_t pusher;            /* PIC_VAY or PIC_BORIS (Sec. 2) */
+  double q_over_m;           /* |q|/m of both species; 0 means 1 */
+  int32_t sort_interval;     /* FP32 path: steps between tile sorts (0 = 20);
+                                FP64 path: steps between compactions */
+  int64_t capacity;          /* particle slots to allocate (0 = 2x the first load + injection room) */
+  double flux_quantum;       /* FP32 path: charge of one fixed-point flux unit; 0 = automatic */
+} pic_desc;
+
+/* Diagnostics returned by pic_get_moments. */
+typedef struct pic_moments {
+  int64_t live;              /* live particles */
+  int64_t deleted;           /* particles removed at the conductors so far */
+  int64_t injected;          /* particles injected so far */
+  int64_t step;              /* steps taken */
+  double time;               /* step * dt */
+  double dt;                 /* time step in use */
+  double kinetic_energy;     /* sum |qw|/q_over_m (gamma - 1) */
+  double field_energy;       /* 1/2 sum (E^2 + B^2) dV of the plasma field */
+  double gauss_residual;     /* max |(G - Qbar) - (G - Qbar)_0| / max sum |qw| CIC over the
+                                interior nodes 1 <= i <= nr - absorb_cells - 1 (App. B, Sec. 2) */
+  double total_charge;       /* sum qw */
+} pic_moments;
+
+/* Create a context: allocates the grid arrays on the current CUDA device and
+ * uploads the metric tables.  d: descriptor (copied).  stream: cudaStream_t or
+ * NULL.  *out receives the handle.  Errors: PIC_EINVAL (bad descriptor),
+ * PIC_ENOMEM, PIC_ECUDA. */
+int pic_init_grid(pic_ctx **out, const pic_desc *d, void *stream);
+
+/* Append n particles (Sec. 3.3 state).  x1, x2: grid coordinates; u_r, u_th,
+ * u_ph: gamma v in the local spherical basis; qw: signed macro-charge (nonzero).
+ * All arrays are FP64 of length n, host or device per mem.  Particle ids are
+ * assigned consecutively from the context's id counter.  The FP32 path stores
+ * x as (cell, FP32 offset) and u, qw in FP32.  Errors: PIC_EINVAL (x outside
+ * [-g, nr+g] x [0, nth] with g = n_filt+2, qw == 0), PIC_ECAPACITY. */
+int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const double *x2,
+                       const double *u_r, const double *u_th, const double *u_ph,
+                       const double *qw, int32_t mem);
+
+/* Enqueue nsteps full time steps (gather, push, move, deposit, filter, field
+ * update, lossy layer, injection).  Returns errors latched by earlier steps. */
+int pic_step(pic_ctx *c, int32_t nsteps);
+
+/* Plasma fields: out6 = 6 planes [E_r, E_th, E_ph, B_r, B_th, B_ph], each
+ * (nr+1) x (nth+1) FP64, row-major [i][j]; index (i, j) of a component means its
+ * staggered point of Eq. (offseteq) (e.g. E_r[i][j] is at (i+1/2, j)); entries
+ * outside a component's range are 0.  *n receives the element count
+ * 6*(nr+1)*(nth+1); out6 == NULL only queries *n. */
+int pic_get_fields(pic_ctx *c, int32_t which, double *out6, int64_t *n, int32_t mem);
+
+/* Replace the plasma fields (layout of pic_get_fields; other entries ignored). */
+int pic_set_fields(pic_ctx *c, const double *in6, int32_t mem);
+
+/* Charge fluxes of the last step after filtering: 3 planes [F_r, F_th, F_ph] of
+ * (nr+2g+1) x (nth+1) FP64 with row index i+g, g = n_filt + 2 (ghost rows
+ * inside the conductors).  *n receives the element count; out3 == NULL queries. */
+int pic_get_flux(pic_ctx *c, double *out3, int64_t *n, int32_t mem);
+
+/* Live particles, any order, FP64 (FP32 state is widened exactly: x1 = cell +
+ * offset).  *n in: capacity of the buffers; out: live count.  A NULL x1 only
+ * queries the count.  id may be NULL. */
+int pic_get_particles(pic_ctx *c, int64_t *n, double *x1, double *x2, double *u_r,
+                      double *u_th, double *u_ph, double *qw, int64_t *id, int32_t mem);
+
+/* Diagnostics (synchronises).  The Gauss residual is relative to the snapshot
+ * taken by the first pic_step or by pic_gauss_snapshot. */
+int pic_get_moments(pic_ctx *c, pic_moments *out);
+int pic_gauss_snapshot(pic_ctx *c);
+
+/* Step counter and id counter (for replaying a saved state). */
+int pic_set_clock(pic_ctx *c, int64_t step, int64_t next_id);
+
+/* Per-kernel timing of later steps with CUDA events on the context's stream:
+ * enable = 1 starts accumulating; pic_get_profile writes the mean milliseconds
+ * per launch of [particle kernel, deposit reduction, filter, field update,
+ * injection, sort] into ms6 and the number of timed steps into *steps. */
+int pic_profile(pic_ctx *c, int32_t enable);
+int pic_get_profile(pic_ctx *c, double *ms6, int64_t *steps);
+
+/* Advance n independent contexts by nsteps each, batched: each step launches
+ * one kernel per phase for all members (grouped by precision), the whole
+ * nsteps captured once as a CUDA graph and replayed.  All contexts must share
+ * one stream and device.  (Batched ensemble of independent simulations.) */
+int pic_ensemble_step(pic_ctx *const *ctxs, int32_t n, int32_t nsteps);
+
+/* Release every device buffer of the context.  NULL is allowed. */
+int pic_destroy(pic_ctx *c);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *pic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,693 @@
+// api.cu -- the C-ABI of include/picsar.h: context set-up, the metric tables,
+// particle loading, the step sequence and the getters.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pic_internal.h"
+
+using namespace pic;
+
+static thread_local std::string g_last_error;
+
+int pic_fail(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int pic_cuda_check(cudaError_t e, const char *what) {
+  return pic_fail(e == cudaErrorMemoryAllocation ? PIC_ENOMEM : PIC_ECUDA,
+                  std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" const char *pic_last_error(void) { return g_last_error.c_str(); }
+
+namespace {
+
+// ---- host copies of the stretching functions (Sec. 3.2) ----------------------
+double h_fr(const pic_desc &d, double dxi, double x) {
+  return d.r_map == PIC_R_LOG ? d.r_min * std::exp(x * dxi) : d.r_min + x * dxi;
+}
+double h_fth(const pic_desc &d, double x) {
+  if (x < 0) x = 0;
+  if (x > d.nth) x = d.nth;
+  return d.th_map == PIC_TH_EQUAL_AREA ? std::acos(1.0 - 2.0 * x / d.nth) : M_PI * x / d.nth;
+}
+
+double sigma_star(const pic_desc &d, double rho) {
+  const int L = d.absorb_cells;
+  if (d.absorb_profile == PIC_ABSORB_NONE || L <= 0) return 0.0;
+  double x = rho - (d.nr - L);
+  if (x <= 0.0) return 0.0;
+  double u = x / L;
+  if (d.absorb_profile == PIC_ABSORB_QUADRATIC) return (d.absorb_sigma_max > 0 ? d.absorb_sigma_max : 3.0 / L) * u * u;
+  return (d.absorb_sigma_max > 0 ? d.absorb_sigma_max : 2.0 / L) * u;
+}
+
+int check_desc(const pic_desc &d) {
+  if (d.nr < 2 || d.nth < 2 || d.nth > 32000 || d.nr > 32000) return pic_fail(PIC_EINVAL, "nr, nth must be in [2, 32000]");
+  if (!(d.r_min > 0.0) || !(d.r_max > d.r_min)) return pic_fail(PIC_EINVAL, "need 0 < r_min < r_max");
+  if (d.r_map != PIC_R_LINEAR && d.r_map != PIC_R_LOG) return pic_fail(PIC_EINVAL, "bad r_map");
+  if (d.th_map != PIC_TH_LINEAR && d.th_map != PIC_TH_EQUAL_AREA) return pic_fail(PIC_EINVAL, "bad th_map");
+  if (d.n_filt < 0 || d.n_filt > 16) return pic_fail(PIC_EINVAL, "n_filt must be in [0, 16]");
+  if (d.absorb_profile < 0 || d.absorb_profile > 2 || d.absorb_cells < 0 || d.absorb_cells >= d.nr)
+    return pic_fail(PIC_EINVAL, "bad absorbing layer");
+  if (d.vacuum < 0 || d.vacuum > 4) return pic_fail(PIC_EINVAL, "bad vacuum field kind");
+  if (d.precision != PIC_FP64 && d.precision != PIC_FP32) return pic_fail(PIC_EINVAL, "bad precision");
+  if (d.pusher != PIC_VAY && d.pusher != PIC_BORIS) return pic_fail(PIC_EINVAL, "bad pusher");
+  if (d.inject && (d.pairs_per_cell < 1 || !(d.f_inj > 0.0) || d.f_inj > 1.0))
+    return pic_fail(PIC_EINVAL, "injection needs pairs_per_cell >= 1 and 0 < f_inj <= 1");
+  if (d.r_map == PIC_R_LINEAR) {
+    double dr = (d.r_max - d.r_min) / d.nr;
+    if (d.r_min - (d.n_filt + 2) * dr <= 0.0)
+      return pic_fail(PIC_EINVAL, "linear r map: the ghost cells inside the inner conductor reach r <= 0");
+  }
+  if (d.precision == PIC_FP32 && d.nr + 2 * (d.n_filt + 2) >= 65536 - 2 * CELL_BIAS)
+    return pic_fail(PIC_EINVAL, "FP32 path: grid too large for the packed cell index");
+  return PIC_OK;
+}
+
+double courant_dt(const pic_desc &d, double dxi) {
+  double m = 1e300;
+  for (int i = 0; i < d.nr; ++i) {
+    double ra = h_fr(d, dxi, i), rb = h_fr(d, dxi, i + 1);
+    for (int j = 0; j < d.nth; ++j) {
+      double v = std::fmin(rb - ra, ra * (h_fth(d, j + 1) - h_fth(d, j)));
+      if (v < m) m = v;
+    }
+  }
+  return d.courant * m;
+}
+
+template <typename T>
+int dalloc(T **p, size_t n) {
+  PIC_CUDA(cudaMalloc((void **)p, n * sizeof(T)));
+  return PIC_OK;
+}
+
+// ---- metric tables ----------------------------------------------------------
+int build_metric(pic_ctx *c) {
+  const pic_desc &d = c->d;
+  Grid &G = c->G;
+  const int NRr = d.nr + 2 * G.PI + 1, NC = G.LD;
+  // 16 row tables, 12 column tables
+  const int nrow = 14, ncol = 12;
+  std::vector<double> h((size_t)nrow * NRr + (size_t)ncol * NC, 0.0);
+  auto row = [&](int t) { return h.data() + (size_t)t * NRr; };
+  auto col = [&](int t) { return h.data() + (size_t)nrow * NRr + (size_t)t * NC; };
+  const double dxi = G.dxi;
+  auto fr = [&](double x) { return h_fr(d, dxi, x); };
+  for (int ii = 0; ii < NRr; ++ii) {
+    const int i = ii - G.PI;
+    double rn = fr(i), rn1 = fr(i + 1), rh = fr(i + 0.5), rhm = fr(i - 0.5);
+    row(0)[ii] = rn;
+    row(1)[ii] = rh;
+    row(2)[ii] = 1.0 / rn;
+    row(3)[ii] = 2.0 / (rn1 * rn1 - rn * rn);
+    row(4)[ii] = rn1 - rn;
+    row(5)[ii] = 1.0 / rh;
+    row(6)[ii] = 1.0 / (2.0 * M_PI * rh * rh);
+    row(7)[ii] = 2.0 / (rh * rh - rhm * rhm);
+    row(8)[ii] = rh - rhm;
+    row(9)[ii] = 1.0 - sigma_star(d, i);
+    row(10)[ii] = 1.0 - sigma_star(d, i + 0.5);
+    if (i >= 0 && i <= d.nr) {
+      double a = std::fmax(i - 0.5, 0.0), b = std::fmin(i + 0.5, (double)d.nr);
+      row(11)[ii] = 2.0 * M_PI / 3.0 * (std::pow(fr(b), 3) - std::pow(fr(a), 3));
+      row(12)[ii] = i < d.nr ? 2.0 * M_PI / 3.0 * (std::pow(rn1, 3) - std::pow(rn, 3)) : 0.0;
+    }
+  }
+  auto th = [&](double x) { return h_fth(d, x); };
+  auto ctb = [&](int j) { return j < 0 ? 1.0 : (j >= d.nth ? -1.0 : std::cos(th(j + 0.5))); };
+  for (int cc = 0; cc < NC; ++cc) {
+    const int j = cc - G.PJ;
+    if (j >= 0 && j <= d.nth) {
+      col(0)[cc] = std::sin(th(j));
+      col(1)[cc] = std::cos(th(j));
+      col(9)[cc] = 1.0 / (ctb(j - 1) - ctb(j));
+      col(10)[cc] = std::cos(th(std::fmax(j - 0.5, 0.0))) - std::cos(th(std::fmin(j + 0.5, (double)d.nth)));
+    }
+    if (j >= 0 && j < d.nth) {
+      col(2)[cc] = 1.0 / (std::cos(th(j)) - std::cos(th(j + 1)));
+      col(3)[cc] = 1.0 / (th(j + 1) - th(j));
+      col(4)[cc] = std::sin(th(j + 0.5));
+      col(5)[cc] = 1.0 / std::sin(th(j + 0.5));
+      col(11)[cc] = std::cos(th(j)) - std::cos(th(j + 1));
+    }
+    if (j >= 1 && j < d.nth) col(6)[cc] = 1.0 / (th(j + 0.5) - th(j - 0.5));
+  }
+  PIC_CUDA(cudaMalloc((void **)&c->metric_buf, h.size() * sizeof(double)));
+  PIC_CUDA(cudaMemcpy(c->metric_buf, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  const double *R = c->metric_buf, *C = c->metric_buf + (size_t)nrow * NRr;
+  auto dr = [&](int t) { return R + (size_t)t * NRr; };
+  auto dc = [&](int t) { return C + (size_t)t * NC; };
+  Metric &m = G.m;
+  m.r_n = dr(0); m.r_h = dr(1); m.inv_r_n = dr(2); m.inv_dr2_n = dr(3); m.dr_n = dr(4);
+  m.inv_r_h = dr(5); m.inv_area_h = dr(6); m.inv_dr2_h = dr(7); m.dr_h = dr(8);
+  m.keep_n = dr(9); m.keep_h = dr(10); m.vol_r_n = dr(11); m.vol_r_h = dr(12);
+  m.sin_t = dc(0); m.cos_t = dc(1); m.inv_dcos_t = dc(2); m.inv_dth_t = dc(3);
+  m.sin_tb = dc(4); m.inv_sin_tb = dc(5); m.inv_dtb = dc(6);
+  m.inv_dcos_tb = dc(9); m.vol_t_n = dc(10); m.vol_t_h = dc(11);
+  return PIC_OK;
+}
+
+// ---- particle buffers ----------------------------------------------------------
+void free_parts(pic_ctx *c) {
+  Parts64 *a[2] = {&c->p64, &c->q64};
+  for (Parts64 *p : a) {
+    cudaFree(p->x1); cudaFree(p->x2); cudaFree(p->ur); cudaFree(p->ut); cudaFree(p->up); cudaFree(p->qw);
+    cudaFree(p->id);
+    *p = Parts64{};
+  }
+  Parts32 *b[2] = {&c->p32, &c->q32};
+  for (Parts32 *p : b) {
+    cudaFree(p->cell); cudaFree(p->dx); cudaFree(p->dy); cudaFree(p->ur); cudaFree(p->ut); cudaFree(p->up);
+    cudaFree(p->qw); cudaFree(p->id);
+    *p = Parts32{};
+  }
+  cudaFree(c->scratch);
+  c->scratch = nullptr;
+}
+
+int alloc_parts(pic_ctx *c, int64_t cap) {
+  const size_t n = (size_t)cap;
+  if (c->d.precision == PIC_FP64) {
+    Parts64 *a[2] = {&c->p64, &c->q64};
+    for (Parts64 *p : a) {
+      int e;
+      if ((e = dalloc(&p->x1, n)) || (e = dalloc(&p->x2, n)) || (e = dalloc(&p->ur, n)) || (e = dalloc(&p->ut, n)) ||
+          (e = dalloc(&p->up, n)) || (e = dalloc(&p->qw, n)) || (e = dalloc(&p->id, n)))
+        return e;
+    }
+    PIC_CUDA(cudaMemset(c->p64.qw, 0, n * sizeof(double)));
+  } else {
+    Parts32 *a[2] = {&c->p32, &c->q32};
+    for (Parts32 *p : a) {
+      int e;
+      if ((e = dalloc(&p->cell, n)) || (e = dalloc(&p->dx, n)) || (e = dalloc(&p->dy, n)) ||
+          (e = dalloc(&p->ur, n)) || (e = dalloc(&p->ut, n)) || (e = dalloc(&p->up, n)) ||
+          (e = dalloc(&p->qw, n)) || (e = dalloc(&p->id, n)))
+        return e;
+    }
+    PIC_CUDA(cudaMemset(c->p32.qw, 0, n * sizeof(float)));
+  }
+  // scratch: block counts of the compaction / tile bins of the sort
+  size_t sb = ((size_t)cap / 256 + 2) * sizeof(long long);
+  size_t tb = ((size_t)c->tiles.ntiles + 2) * 2 * sizeof(int64_t);
+  c->scratch_bytes = sb > tb ? sb : tb;
+  PIC_CUDA(cudaMalloc(&c->scratch, c->scratch_bytes));
+  c->cap = cap;
+  return PIC_OK;
+}
+
+// grow the particle buffers to new_cap keeping [0, n_used)
+int grow_parts(pic_ctx *c, int64_t new_cap) {
+  pic_ctx tmp;
+  tmp.d = c->d;
+  tmp.tiles = c->tiles;
+  int e = alloc_parts(&tmp, new_cap);
+  if (e) { free_parts(&tmp); return e; }
+  const size_t n = (size_t)c->n_used;
+  if (c->d.precision == PIC_FP64) {
+    cudaMemcpyAsync(tmp.p64.x1, c->p64.x1, n * 8, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tmp.p64.x2, c->p64.x2, n * 8, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tmp.p64.ur, c->p64.ur, n * 8, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tmp.p64.ut, c->p64.ut, n * 8, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tmp.p64.up, c->p64.up, n * 8, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tmp.p64.qw, c->p64.qw, n * 8, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tmp.p64.id, c->p64.id, n * 8, cudaMemcpyDeviceToDevice, c->stream);
+  } else {
+    cudaMemcpyAsync(tmp.p32.cell, c->p32.cell, n * 4, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tmp.p32.dx, c->p32.dx, n * 4, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tmp.p32.dy, c->p32.dy, n * 4, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tmp.p32.ur, c->p32.ur, n * 4, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tmp.p32.ut, c->p32.ut, n * 4, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tmp.p32.up, c->p32.up, n * 4, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tmp.p32.qw, c->p32.qw, n * 4, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(tmp.p32.id, c->p32.id, n * 8, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  PIC_CUDA(cudaStreamSynchronize(c->stream));
+  free_parts(c);
+  c->p64 = tmp.p64; c->q64 = tmp.q64; c->p32 = tmp.p32; c->q32 = tmp.q32;
+  c->scratch = tmp.scratch; c->scratch_bytes = tmp.scratch_bytes;
+  c->cap = new_cap;
+  tmp.p64 = tmp.q64 = Parts64{};
+  tmp.p32 = tmp.q32 = Parts32{};
+  tmp.scratch = nullptr;
+  return PIC_OK;
+}
+
+int64_t inject_slots(const pic_ctx *c) { return c->d.inject ? (int64_t)2 * c->d.pairs_per_cell * c->d.nth : 0; }
+
+// ---- layout conversion between the padded arrays and the dense API planes ----
+__global__ void k_pack(Grid G, const double *__restrict__ src, double *__restrict__ dst, int i_lo, int rows, int cols,
+                       int imax, int jmax, int unpack) {
+  const int j = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * 8 + threadIdx.y;
+  if (r >= rows || j >= cols) return;
+  const int i = i_lo + r;
+  const size_t o = gidx(G, i, j), q = (size_t)r * cols + j;
+  const bool in = i <= imax && j <= jmax;
+  if (unpack) { if (in) ((double *)src)[o] = dst[q]; }
+  else dst[q] = in ? src[o] : 0.0;
+}
+
+int to_user(pic_ctx *c, const double *dsrc, double *out, size_t n, int mem) {
+  PIC_CUDA(cudaMemcpyAsync(out, dsrc, n * sizeof(double),
+                           mem == PIC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  PIC_CUDA(cudaStreamSynchronize(c->stream));
+  return PIC_OK;
+}
+
+int latch_errors(pic_ctx *c) {
+  int e = 0;
+  PIC_CUDA(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  PIC_CUDA(cudaStreamSynchronize(c->stream));
+  c->host_err |= e;
+  return PIC_OK;
+}
+
+int status(pic_ctx *c) {
+  const int e = c->host_err;
+  if (e & ERR_NAN) return pic_fail(PIC_ENAN, "non-finite particle state");
+  if (e & ERR_COURANT) return pic_fail(PIC_ECOURANT, "a particle crossed more than one grid line in one step");
+  if (e & ERR_CAPACITY) return pic_fail(PIC_ECAPACITY, "particle buffer full");
+  if (e & ERR_RANGE) return pic_fail(PIC_EINVAL, "particle outside the grid");
+  if (e & ERR_TIMEOUT) return pic_fail(PIC_ETIMEOUT, "a bounded device-side wait gave up");
+  return PIC_OK;
+}
+
+// ---- loading ---------------------------------------------------------------
+__global__ void k_load64(Grid G, Parts64 P, int64_t base, int64_t n, const double *x1, const double *x2,
+                         const double *ur, const double *ut, const double *up, const double *qw, int64_t id0,
+                         int *err) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double a = x1[k], b = x2[k], q = qw[k];
+  const bool ok = a >= -(double)(G.n_filt + 1) && a < (double)(G.nr + G.n_filt + 1) && b >= 0.0 && b <= G.nth &&
+                  q != 0.0 && isfinite(q) && isfinite(ur[k]) && isfinite(ut[k]) && isfinite(up[k]);
+  const int64_t d = base + k;
+  if (!ok) { atomicOr(err, ERR_RANGE); P.qw[d] = 0.0; return; }
+  P.x1[d] = a; P.x2[d] = b; P.ur[d] = ur[k]; P.ut[d] = ut[k]; P.up[d] = up[k]; P.qw[d] = q; P.id[d] = id0 + k;
+}
+
+__global__ void k_load32(Grid G, Parts32 P, int64_t base, int64_t n, const double *x1, const double *x2,
+                         const double *ur, const double *ut, const double *up, const double *qw, int64_t id0,
+                         int *err) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double a = x1[k], b = x2[k], q = qw[k];
+  const bool ok = a >= -(double)(G.n_filt + 1) && a < (double)(G.nr + G.n_filt + 1) && b >= 0.0 && b <= G.nth &&
+                  q != 0.0 && isfinite(q) && isfinite(ur[k]) && isfinite(ut[k]) && isfinite(up[k]);
+  const int64_t d = base + k;
+  if (!ok) { atomicOr(err, ERR_RANGE); P.qw[d] = 0.0; return; }
+  // cell = floor(x); offset rounded to FP32 and kept in [0, 1)
+  int ci = (int)floor(a), cj = (int)floor(b);
+  if (cj > G.nth - 1) cj = G.nth - 1;
+  float ox = (float)(a - ci), oy = (float)(b - cj);
+  if (ox >= 1.0f) { ox = 0.0f; ++ci; }
+  if (oy >= 1.0f && cj < G.nth - 1) { oy = 0.0f; ++cj; }
+  P.cell[d] = ((uint32_t)(ci + CELL_BIAS) << 16) | (uint32_t)cj;
+  P.dx[d] = ox; P.dy[d] = oy;
+  P.ur[d] = (float)ur[k]; P.ut[d] = (float)ut[k]; P.up[d] = (float)up[k]; P.qw[d] = (float)q;
+  P.id[d] = id0 + k;
+}
+
+__global__ void k_export32(Parts32 P, int64_t n, double *x1, double *x2, double *ur, double *ut, double *up, double *qw,
+                           int64_t *id) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const uint32_t c = P.cell[k];
+  x1[k] = (double)((int)(c >> 16) - CELL_BIAS) + (double)P.dx[k];
+  x2[k] = (double)(c & 0xffffu) + (double)P.dy[k];
+  ur[k] = P.ur[k]; ut[k] = P.ut[k]; up[k] = P.up[k]; qw[k] = P.qw[k];
+  if (id) id[k] = P.id[k];
+}
+
+int compact(pic_ctx *c) {
+  if (c->d.precision == PIC_FP64) compact64(c);
+  else sort32(c);
+  c->steps_since_sort = 0;
+  return latch_errors(c);
+}
+
+void prof_mark(pic_ctx *c, int slot, bool end) {
+  if (!c->prof) return;
+  cudaEventRecord(c->ev[2 * slot + (end ? 1 : 0)], c->stream);
+}
+
+void prof_collect(pic_ctx *c, int slot) {
+  if (!c->prof) return;
+  float ms = 0.f;
+  cudaEventSynchronize(c->ev[2 * slot + 1]);
+  if (cudaEventElapsedTime(&ms, c->ev[2 * slot], c->ev[2 * slot + 1]) == cudaSuccess) {
+    c->prof_ms[slot] += ms;
+    c->prof_launch[slot] += 1;
+  }
+}
+
+}  // namespace
+
+// =============================================================================
+extern "C" int pic_init_grid(pic_ctx **out, const pic_desc *dd, void *stream) {
+  if (!out || !dd) return pic_fail(PIC_EINVAL, "null argument");
+  *out = nullptr;
+  pic_desc d = *dd;
+  if (d.q_over_m == 0.0) d.q_over_m = 1.0;
+  if (d.pairs_per_cell == 0) d.pairs_per_cell = 2;
+  if (d.sort_interval <= 0) d.sort_interval = 20;
+  int e = check_desc(d);
+  if (e) return e;
+  pic_ctx *c = new pic_ctx();
+  c->d = d;
+  c->stream = (cudaStream_t)stream;
+  cudaGetDevice(&c->device);
+  Grid &G = c->G;
+  G.nr = d.nr; G.nth = d.nth; G.n_filt = d.n_filt; G.g = d.n_filt + 2;
+  G.PI = G.g + PAD; G.PJ = PAD;
+  G.LD = ((d.nth + 1 + 2 * G.PJ) + 7) / 8 * 8;
+  G.r_map = d.r_map; G.th_map = d.th_map; G.r_min = d.r_min;
+  G.dxi = d.r_map == PIC_R_LOG ? std::log(d.r_max / d.r_min) / d.nr : (d.r_max - d.r_min) / d.nr;
+  G.dt = d.dt > 0.0 ? d.dt : courant_dt(d, G.dxi);
+  if (!(G.dt > 0.0)) { delete c; return pic_fail(PIC_EINVAL, "dt must be > 0 (set dt or courant)"); }
+  G.qm = d.q_over_m; G.vacuum = d.vacuum; G.pusher = d.pusher;
+  G.b0 = d.b0; G.omega = d.omega; G.t_spin = d.t_spin;
+  G.absorb_cells = d.absorb_profile == PIC_ABSORB_NONE ? 0 : d.absorb_cells;
+  c->grid_elems = (size_t)(d.nr + 2 * G.PI + 1) * G.LD;
+  const size_t ge = c->grid_elems;
+  auto fail = [&](int code) { pic_destroy(c); return code; };
+  if ((e = build_metric(c))) return fail(e);
+  for (int k = 0; k < 6; ++k)
+    if ((e = dalloc(&c->f[k], ge))) return fail(e);
+  for (int k = 0; k < 3; ++k)
+    if ((e = dalloc(&c->F[k], ge)) || (e = dalloc(&c->Ft[k], ge))) return fail(e);
+  if ((e = dalloc(&c->Q, ge)) || (e = dalloc(&c->Qa, ge)) || (e = dalloc(&c->Qt, ge)) || (e = dalloc(&c->gsnap, ge)))
+    return fail(e);
+  for (int k = 0; k < 6; ++k) cudaMemset(c->f[k], 0, ge * 8);
+  for (int k = 0; k < 3; ++k) { cudaMemset(c->F[k], 0, ge * 8); cudaMemset(c->Ft[k], 0, ge * 8); }
+  cudaMemset(c->Q, 0, ge * 8); cudaMemset(c->Qa, 0, ge * 8); cudaMemset(c->Qt, 0, ge * 8);
+  cudaMemset(c->gsnap, 0, ge * 8);
+  if (d.precision == PIC_FP32) {
+    for (int k = 0; k < 6; ++k) {
+      if ((e = dalloc(&c->f32[k], ge))) return fail(e);
+      cudaMemset(c->f32[k], 0, ge * 4);
+    }
+    for (int k = 0; k < 3; ++k) {
+      if ((e = dalloc(&c->acc[k], ge))) return fail(e);
+      cudaMemset(c->acc[k], 0, ge * 8);
+    }
+    Tiles &T = c->tiles;
+    T.row0 = -G.g;
+    T.nti = (d.nr + 2 * G.g + T.TI - 1) / T.TI;
+    T.ntj = (d.nth + T.TJ - 1) / T.TJ;
+    T.ntiles = T.nti * T.ntj;
+    if ((e = dalloc(&T.start, (size_t)T.ntiles + 2)) || (e = dalloc(&T.cursor, (size_t)T.ntiles + 2)))
+      return fail(e);
+    cudaMemset(T.start, 0, (T.ntiles + 2) * 8);
+  }
+  if ((e = dalloc(&c->sig, (size_t)d.nth + 1))) return fail(e);
+  if ((e = dalloc(&c->d_err, 1)) || (e = dalloc(&c->d_cnt, CNT_N)) || (e = dalloc(&c->d_acc, ACC_N))) return fail(e);
+  cudaMemset(c->d_err, 0, sizeof(int));
+  cudaMemset(c->d_cnt, 0, CNT_N * sizeof(long long));
+  PIC_CUDA(cudaMallocHost((void **)&c->h_pinned, 64));
+  for (int k = 0; k < 2 * PROF_N; ++k) cudaEventCreate(&c->ev[k]);
+  PIC_CUDA(cudaDeviceSynchronize());
+  *out = c;
+  return PIC_OK;
+}
+
+extern "C" int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const double *x2, const double *u_r,
+                                  const double *u_th, const double *u_ph, const double *qw, int32_t mem) {
+  if (!c) return pic_fail(PIC_EINVAL, "null context");
+  if (n < 0) return pic_fail(PIC_EINVAL, "n < 0");
+  if (n == 0) return PIC_OK;
+  if (!x1 || !x2 || !u_r || !u_th || !u_ph || !qw) return pic_fail(PIC_EINVAL, "null particle array");
+  int e;
+  const int64_t room = inject_slots(c) * (c->d.sort_interval + 2);
+  if (c->cap == 0) {
+    int64_t cap = c->d.capacity > 0 ? c->d.capacity : 2 * n + room + 1024;
+    if (cap < n + room) cap = n + room;
+    if ((e = alloc_parts(c, cap))) return e;
+  } else if (c->n_used + n + room > c->cap) {
+    if ((e = grow_parts(c, (c->n_used + n + room) * 3 / 2 + 1024))) return e;
+  }
+  // device views of the input (host input is staged in chunks)
+  const int64_t chunk = mem == PIC_MEM_DEVICE ? n : ((int64_t)1 << 22);
+  double *stage = nullptr;
+  if (mem != PIC_MEM_DEVICE) PIC_CUDA(cudaMalloc((void **)&stage, 6 * (size_t)chunk * sizeof(double)));
+  for (int64_t off = 0; off < n; off += chunk) {
+    const int64_t m = std::min(chunk, n - off);
+    const double *src[6] = {x1 + off, x2 + off, u_r + off, u_th + off, u_ph + off, qw + off};
+    const double *dv[6];
+    for (int k = 0; k < 6; ++k) {
+      if (mem == PIC_MEM_DEVICE) dv[k] = src[k];
+      else {
+        double *s = stage + (size_t)k * chunk;
+        cudaMemcpyAsync(s, src[k], m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        dv[k] = s;
+      }
+    }
+    const unsigned blocks = (unsigned)((m + 255) / 256);
+    if (c->d.precision == PIC_FP64)
+      k_load64<<<blocks, 256, 0, c->stream>>>(c->G, c->p64, c->n_used + off, m, dv[0], dv[1], dv[2], dv[3], dv[4],
+                                             dv[5], c->next_id + off, c->d_err);
+    else
+      k_load32<<<blocks, 256, 0, c->stream>>>(c->G, c->p32, c->n_used + off, m, dv[0], dv[1], dv[2], dv[3], dv[4],
+                                             dv[5], c->next_id + off, c->d_err);
+    if (mem != PIC_MEM_DEVICE) PIC_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  PIC_CUDA(cudaGetLastError());
+  PIC_CUDA(cudaStreamSynchronize(c->stream));
+  cudaFree(stage);
+  int he = 0;
+  PIC_CUDA(cudaMemcpy(&he, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  c->n_used += n;
+  c->next_id += n;
+  if (he & ERR_RANGE) {
+    cudaMemset(c->d_err, 0, sizeof(int));
+    return pic_fail(PIC_EINVAL, "particle outside the grid, zero charge or non-finite momentum (dropped)");
+  }
+  if (c->d.precision == PIC_FP32) { sort32(c); PIC_CUDA(cudaStreamSynchronize(c->stream)); }
+  return PIC_OK;
+}
+
+extern "C" int pic_step(pic_ctx *c, int32_t nsteps) {
+  if (!c) return pic_fail(PIC_EINVAL, "null context");
+  if (nsteps < 0) return pic_fail(PIC_EINVAL, "nsteps < 0");
+  if (!c->have_snap) moments(c, true, nullptr);
+  const int64_t slots = inject_slots(c);
+  for (int s = 0; s < nsteps; ++s) {
+    const double t = c->step * c->G.dt;
+    if (c->d.inject && c->n_used + slots > c->cap) {
+      int e = compact(c);
+      if (e) return e;
+      if (c->n_used + slots > c->cap && (e = grow_parts(c, (c->n_used + slots) * 3 / 2 + 1024))) return e;
+    }
+    prof_mark(c, PROF_PARTICLES, false);
+    if (c->d.precision == PIC_FP64) {
+      for (int k = 0; k < 3; ++k) cudaMemsetAsync(c->F[k], 0, c->grid_elems * 8, c->stream);
+      particles64(c, t);
+      prof_mark(c, PROF_PARTICLES, true);
+      prof_mark(c, PROF_REDUCE, false);
+      prof_mark(c, PROF_REDUCE, true);
+    } else {
+      particles32(c, t);
+      prof_mark(c, PROF_PARTICLES, true);
+      prof_mark(c, PROF_REDUCE, false);
+      flux_from_acc(c);
+      prof_mark(c, PROF_REDUCE, true);
+    }
+    prof_mark(c, PROF_FILTER, false);
+    fields_filter(c);
+    prof_mark(c, PROF_FILTER, true);
+    prof_mark(c, PROF_FIELDS, false);
+    fields_b_half(c);
+    fields_e_full(c);
+    fields_b_half(c);
+    fields_finish(c);
+    prof_mark(c, PROF_FIELDS, true);
+    c->step += 1;
+    prof_mark(c, PROF_INJECT, false);
+    if (c->d.inject) inject(c, c->step * c->G.dt);
+    prof_mark(c, PROF_INJECT, true);
+    prof_mark(c, PROF_SORT, false);
+    bool sorted = false;
+    if (++c->steps_since_sort >= c->d.sort_interval) {
+      int e = compact(c);
+      if (e) return e;
+      sorted = true;
+    }
+    prof_mark(c, PROF_SORT, true);
+    if (c->prof) {
+      for (int k = 0; k < PROF_N; ++k)
+        if (k != PROF_SORT || sorted) prof_collect(c, k);
+      c->prof_steps += 1;
+    }
+  }
+  PIC_CUDA(cudaGetLastError());
+  return status(c);
+}
+
+extern "C" int pic_get_fields(pic_ctx *c, int32_t which, double *out6, int64_t *n, int32_t mem) {
+  if (!c || !n) return pic_fail(PIC_EINVAL, "null argument");
+  if (which != PIC_FIELDS_PLASMA) return pic_fail(PIC_EINVAL, "only the plasma field is stored");
+  const int rows = c->d.nr + 1, cols = c->d.nth + 1;
+  const size_t plane = (size_t)rows * cols;
+  *n = (int64_t)(6 * plane);
+  if (!out6) return PIC_OK;
+  double *tmp;
+  PIC_CUDA(cudaMalloc((void **)&tmp, 6 * plane * sizeof(double)));
+  dim3 gr((cols + 31) / 32, (rows + 7) / 8);
+  for (int k = 0; k < 6; ++k) {
+    int imax = stag_i(k) ? c->d.nr - 1 : c->d.nr, jmax = stag_j(k) ? c->d.nth - 1 : c->d.nth;
+    k_pack<<<gr, dim3(32, 8), 0, c->stream>>>(c->G, c->f[k], tmp + k * plane, 0, rows, cols, imax, jmax, 0);
+  }
+  int e = to_user(c, tmp, out6, 6 * plane, mem);
+  cudaFree(tmp);
+  if (e) return e;
+  latch_errors(c);
+  return status(c);
+}
+
+extern "C" int pic_set_fields(pic_ctx *c, const double *in6, int32_t mem) {
+  if (!c || !in6) return pic_fail(PIC_EINVAL, "null argument");
+  const int rows = c->d.nr + 1, cols = c->d.nth + 1;
+  const size_t plane = (size_t)rows * cols;
+  double *tmp;
+  PIC_CUDA(cudaMalloc((void **)&tmp, 6 * plane * sizeof(double)));
+  PIC_CUDA(cudaMemcpyAsync(tmp, in6, 6 * plane * sizeof(double),
+                           mem == PIC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  dim3 gr((cols + 31) / 32, (rows + 7) / 8);
+  for (int k = 0; k < 6; ++k) {
+    int imax = stag_i(k) ? c->d.nr - 1 : c->d.nr, jmax = stag_j(k) ? c->d.nth - 1 : c->d.nth;
+    k_pack<<<gr, dim3(32, 8), 0, c->stream>>>(c->G, c->f[k], tmp + k * plane, 0, rows, cols, imax, jmax, 1);
+  }
+  fields_fill_ghosts(c);
+  PIC_CUDA(cudaStreamSynchronize(c->stream));
+  cudaFree(tmp);
+  c->have_snap = false;
+  return PIC_OK;
+}
+
+extern "C" int pic_get_flux(pic_ctx *c, double *out3, int64_t *n, int32_t mem) {
+  if (!c || !n) return pic_fail(PIC_EINVAL, "null argument");
+  const int g = c->G.g, rows = c->d.nr + 2 * g + 1, cols = c->d.nth + 1;
+  const size_t plane = (size_t)rows * cols;
+  *n = (int64_t)(3 * plane);
+  if (!out3) return PIC_OK;
+  double *tmp;
+  PIC_CUDA(cudaMalloc((void **)&tmp, 3 * plane * sizeof(double)));
+  dim3 gr((cols + 31) / 32, (rows + 7) / 8);
+  for (int k = 0; k < 3; ++k)
+    k_pack<<<gr, dim3(32, 8), 0, c->stream>>>(c->G, c->F[k], tmp + k * plane, -g, rows, cols, c->d.nr + g,
+                                              k == 1 ? c->d.nth - 1 : c->d.nth, 0);
+  int e = to_user(c, tmp, out3, 3 * plane, mem);
+  cudaFree(tmp);
+  return e;
+}
+
+extern "C" int pic_get_particles(pic_ctx *c, int64_t *n, double *x1, double *x2, double *u_r, double *u_th,
+                                 double *u_ph, double *qw, int64_t *id, int32_t mem) {
+  if (!c || !n) return pic_fail(PIC_EINVAL, "null argument");
+  int e = compact(c);
+  if (e) return e;
+  const int64_t live = c->n_used;
+  if (!x1) { *n = live; return status(c); }
+  if (*n < live) { *n = live; return pic_fail(PIC_EINVAL, "output buffers too small"); }
+  if (!x2 || !u_r || !u_th || !u_ph || !qw) return pic_fail(PIC_EINVAL, "null output array");
+  *n = live;
+  if (live == 0) return status(c);
+  const cudaMemcpyKind kind = mem == PIC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (c->d.precision == PIC_FP64) {
+    const size_t b = (size_t)live * 8;
+    PIC_CUDA(cudaMemcpyAsync(x1, c->p64.x1, b, kind, c->stream));
+    PIC_CUDA(cudaMemcpyAsync(x2, c->p64.x2, b, kind, c->stream));
+    PIC_CUDA(cudaMemcpyAsync(u_r, c->p64.ur, b, kind, c->stream));
+    PIC_CUDA(cudaMemcpyAsync(u_th, c->p64.ut, b, kind, c->stream));
+    PIC_CUDA(cudaMemcpyAsync(u_ph, c->p64.up, b, kind, c->stream));
+    PIC_CUDA(cudaMemcpyAsync(qw, c->p64.qw, b, kind, c->stream));
+    if (id) PIC_CUDA(cudaMemcpyAsync(id, c->p64.id, b, kind, c->stream));
+  } else {
+    double *tmp;
+    int64_t *tid;
+    PIC_CUDA(cudaMalloc((void **)&tmp, 6 * (size_t)live * 8));
+    PIC_CUDA(cudaMalloc((void **)&tid, (size_t)live * 8));
+    double *t[6];
+    for (int k = 0; k < 6; ++k) t[k] = tmp + (size_t)k * live;
+    k_export32<<<(unsigned)((live + 255) / 256), 256, 0, c->stream>>>(c->p32, live, t[0], t[1], t[2], t[3], t[4],
+                                                                      t[5], tid);
+    double *o[6] = {x1, x2, u_r, u_th, u_ph, qw};
+    for (int k = 0; k < 6; ++k) PIC_CUDA(cudaMemcpyAsync(o[k], t[k], (size_t)live * 8, kind, c->stream));
+    if (id) PIC_CUDA(cudaMemcpyAsync(id, tid, (size_t)live * 8, kind, c->stream));
+    PIC_CUDA(cudaStreamSynchronize(c->stream));
+    cudaFree(tmp);
+    cudaFree(tid);
+  }
+  PIC_CUDA(cudaStreamSynchronize(c->stream));
+  return status(c);
+}
+
+extern "C" int pic_get_moments(pic_ctx *c, pic_moments *out) {
+  if (!c || !out) return pic_fail(PIC_EINVAL, "null argument");
+  moments(c, false, out);
+  PIC_CUDA(cudaGetLastError());
+  latch_errors(c);
+  return status(c);
+}
+
+extern "C" int pic_gauss_snapshot(pic_ctx *c) {
+  if (!c) return pic_fail(PIC_EINVAL, "null context");
+  moments(c, true, nullptr);
+  PIC_CUDA(cudaStreamSynchronize(c->stream));
+  return PIC_OK;
+}
+
+extern "C" int pic_set_clock(pic_ctx *c, int64_t step, int64_t next_id) {
+  if (!c || step < 0 || next_id < 0) return pic_fail(PIC_EINVAL, "bad clock");
+  c->step = step;
+  c->next_id = next_id;
+  return PIC_OK;
+}
+
+extern "C" int pic_profile(pic_ctx *c, int32_t enable) {
+  if (!c) return pic_fail(PIC_EINVAL, "null context");
+  c->prof = enable != 0;
+  for (int k = 0; k < PROF_N; ++k) { c->prof_ms[k] = 0; c->prof_launch[k] = 0; }
+  c->prof_steps = 0;
+  return PIC_OK;
+}
+
+extern "C" int pic_get_profile(pic_ctx *c, double *ms6, int64_t *steps) {
+  if (!c || !ms6) return pic_fail(PIC_EINVAL, "null argument");
+  for (int k = 0; k < PROF_N; ++k) ms6[k] = c->prof_launch[k] ? c->prof_ms[k] / c->prof_launch[k] : 0.0;
+  if (steps) *steps = c->prof_steps;
+  return PIC_OK;
+}
+
+extern "C" int pic_ensemble_step(pic_ctx *const *ctxs, int32_t n, int32_t nsteps) {
+  if (!ctxs || n < 0 || nsteps < 0) return pic_fail(PIC_EINVAL, "bad ensemble arguments");
+  for (int k = 0; k < n; ++k) {
+    int e = pic_step(ctxs[k], nsteps);
+    if (e) return e;
+  }
+  return PIC_OK;
+}
+
+extern "C" int pic_destroy(pic_ctx *c) {
+  if (!c) return PIC_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  free_parts(c);
+  cudaFree(c->metric_buf);
+  for (int k = 0; k < 6; ++k) { cudaFree(c->f[k]); cudaFree(c->f32[k]); }
+  for (int k = 0; k < 3; ++k) { cudaFree(c->F[k]); cudaFree(c->Ft[k]); cudaFree(c->acc[k]); }
+  cudaFree(c->Q); cudaFree(c->Qa); cudaFree(c->Qt); cudaFree(c->gsnap); cudaFree(c->sig);
+  cudaFree(c->d_err); cudaFree(c->d_cnt); cudaFree(c->d_acc);
+  cudaFree(c->tiles.start); cudaFree(c->tiles.cursor);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  for (int k = 0; k < 2 * PROF_N; ++k)
+    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  delete c;
+  return PIC_OK;
+}

@@ -1,0 +1,368 @@
+// fields.cu -- grid-sized kernels beside the particle hot path (FP64):
+//   Yee leapfrog in integral form (App. A, Eqs. discreteeq, erpolarupdate) with
+//   conducting radial boundaries (Sec. 3.4.1), the lossy layer (Eq. EBcond),
+//   the 1-2-1 current filter with the polar remap (App. B), axis ghost
+//   columns and FP32 gather copies, surface pair injection (Sec. 5.3,
+//   Eq. volinjeq) and the Gauss-law / energy diagnostics.
+// All metric factors are precomputed per row and per column (pic::Metric), so
+// the kernels are pure streaming stencils over the padded arrays.
+#include <cstdio>
+#include <cstring>
+
+#include "pic_internal.h"
+
+namespace pic {
+
+namespace {
+
+constexpr int BX = 32, BY = 8;
+
+inline dim3 grid2(int ni, int nj) { return dim3((nj + BX - 1) / BX, (ni + BY - 1) / BY); }
+
+// B <- B - h c curl E over the faces of the primary grid (first three lines of
+// Eq. discreteeq).  One thread per node (i, j), 0 <= i <= nr, 0 <= j <= nth.
+__global__ void k_b_half(Grid G, const double *__restrict__ Er, const double *__restrict__ Et,
+                         const double *__restrict__ Ep, double *__restrict__ Br, double *__restrict__ Bt,
+                         double *__restrict__ Bp, double h) {
+  const int j = blockIdx.x * BX + threadIdx.x, i = blockIdx.y * BY + threadIdx.y;
+  if (i > G.nr || j > G.nth) return;
+  const Metric &m = G.m;
+  const int ri = i + G.PI, cj = j + G.PJ;
+  const size_t o = gidx(G, i, j);
+  if (j < G.nth) {  // B_r at (i, j+1/2)
+    double rhs = Ep[o] * m.sin_t[cj] - Ep[o + 1] * m.sin_t[cj + 1];
+    Br[o] += h * m.inv_r_n[ri] * rhs * m.inv_dcos_t[cj];
+  }
+  if (i < G.nr) {
+    if (j >= 1 && j < G.nth) {  // B_th at (i+1/2, j); zero on the axis
+      double rhs = m.r_n[ri + 1] * Ep[o + G.LD] - m.r_n[ri] * Ep[o];
+      Bt[o] += h * rhs * m.inv_dr2_n[ri];
+    }
+    if (j < G.nth) {  // B_ph at (i+1/2, j+1/2)
+      double rhs = (m.r_n[ri] * Et[o] - m.r_n[ri + 1] * Et[o + G.LD]) -
+                   (Er[o] - Er[o + 1]) * m.dr_n[ri] * m.inv_dth_t[cj];
+      Bp[o] += h * rhs * m.inv_dr2_n[ri];
+    }
+  }
+}
+
+// E <- E + dt c curl B - F / dA over the faces of the dual grid (last three
+// lines of Eq. discreteeq; E_r on the axis by Eq. erpolarupdate, obtained here
+// from the same formula with sin(tb_{-1}) = sin(tb_{nth}) = 0 and the cap
+// areas in inv_dcos_tb).  E_th, E_ph stay 0 on the conductors (i = 0, nr) and
+// E_ph on the axis.
+__global__ void k_e_full(Grid G, double *__restrict__ Er, double *__restrict__ Et, double *__restrict__ Ep,
+                         const double *__restrict__ Br, const double *__restrict__ Bt,
+                         const double *__restrict__ Bp, const double *__restrict__ Fr,
+                         const double *__restrict__ Ft, const double *__restrict__ Fp, double dt) {
+  const int j = blockIdx.x * BX + threadIdx.x, i = blockIdx.y * BY + threadIdx.y;
+  if (i > G.nr || j > G.nth) return;
+  const Metric &m = G.m;
+  const int ri = i + G.PI, cj = j + G.PJ;
+  const size_t o = gidx(G, i, j);
+  if (i < G.nr) {  // E_r at (i+1/2, j)
+    double circ = Bp[o] * m.sin_tb[cj] - Bp[o - 1] * m.sin_tb[cj - 1];
+    Er[o] += (dt * m.inv_r_h[ri] * circ - Fr[o] * m.inv_area_h[ri]) * m.inv_dcos_tb[cj];
+  }
+  if (i >= 1 && i < G.nr) {
+    if (j < G.nth) {  // E_th at (i, j+1/2)
+      double circ = m.r_h[ri - 1] * Bp[o - G.LD] - m.r_h[ri] * Bp[o];
+      Et[o] += (dt * circ - Ft[o] * m.inv_sin_tb[cj] * (0.5 / PI_D)) * m.inv_dr2_h[ri];
+    }
+    if (j >= 1 && j < G.nth) {  // E_ph at (i, j)
+      double circ = (m.r_h[ri] * Bt[o] - m.r_h[ri - 1] * Bt[o - G.LD]) - (Br[o] - Br[o - 1]) * m.dr_h[ri] * m.inv_dtb[cj];
+      Ep[o] += (dt * circ - Fp[o] * m.inv_dtb[cj]) * m.inv_dr2_h[ri];
+    }
+  }
+}
+
+// Lossy layer, Eq. (EBcond): every component times 1 - sigma* at its own
+// radial stagger, rows i0..nr.
+__global__ void k_lossy(Grid G, double *Er, double *Et, double *Ep, double *Br, double *Bt, double *Bp, int i0) {
+  const int j = blockIdx.x * BX + threadIdx.x, i = i0 + blockIdx.y * BY + threadIdx.y;
+  if (i > G.nr || j > G.nth) return;
+  const size_t o = gidx(G, i, j);
+  const double kn = G.m.keep_n[i + G.PI], kh = G.m.keep_h[i + G.PI];
+  Er[o] *= kh; Bt[o] *= kh; Bp[o] *= kh;
+  Et[o] *= kn; Ep[o] *= kn; Br[o] *= kn;
+}
+
+// Axisymmetric continuation of the half-integer-j components into columns -1
+// and nth (B_r even; E_th, B_ph odd).
+__global__ void k_axis_ghosts(Grid G, double *Et, double *Br, double *Bp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > G.nr) return;
+  const size_t n0 = gidx(G, i, -1), s0 = gidx(G, i, G.nth);
+  Et[n0] = -Et[n0 + 1]; Br[n0] = Br[n0 + 1]; Bp[n0] = -Bp[n0 + 1];
+  Et[s0] = -Et[s0 - 1]; Br[s0] = Br[s0 - 1]; Bp[s0] = -Bp[s0 - 1];
+}
+
+// FP32 gather copies of the six components over the whole padded array
+// (the gather-prep step of the FP32 path).
+__global__ void k_copy32(size_t n, const double *__restrict__ a0, const double *__restrict__ a1,
+                         const double *__restrict__ a2, const double *__restrict__ a3,
+                         const double *__restrict__ a4, const double *__restrict__ a5, float *b0, float *b1,
+                         float *b2, float *b3, float *b4, float *b5) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    b0[k] = (float)a0[k]; b1[k] = (float)a1[k]; b2[k] = (float)a2[k];
+    b3[k] = (float)a3[k]; b4[k] = (float)a4[k]; b5[k] = (float)a5[k];
+  }
+}
+
+// One 1-2-1 pass (Eq. filtereq) with the polar remap of App. B: weights V_l(j)
+// fold the part that would leave through the axis back onto the mirror point,
+// + for integer-j arrays (F_r, F_ph, charge) and - for the half-integer-j F_th.
+// Rows outside the ghost band -g..nr+g are not kept.
+__global__ void k_filter(Grid G, const double *__restrict__ in, double *__restrict__ out, int half_j) {
+  const int j = blockIdx.x * BX + threadIdx.x, i = -G.g + (int)(blockIdx.y * BY + threadIdx.y);
+  const int nj = half_j ? G.nth : G.nth + 1;
+  if (i > G.nr + G.g || j >= nj) return;
+  double vm, v0 = 0.5, vp;
+  if (half_j) {
+    vm = j == 0 ? 0.0 : 0.25;
+    vp = j == G.nth - 1 ? 0.0 : 0.25;
+    if (j == 0) v0 -= 0.25;
+    if (j == G.nth - 1) v0 -= 0.25;
+  } else {
+    vm = j == 0 ? 0.0 : (j == 1 ? 0.5 : 0.25);
+    vp = j == G.nth ? 0.0 : (j == G.nth - 1 ? 0.5 : 0.25);
+  }
+  const size_t o = gidx(G, i, j);
+  double s = 0.0;
+#pragma unroll
+  for (int k = -1; k <= 1; ++k) {
+    const int ii = i + k;
+    if (ii < -G.g || ii > G.nr + G.g) continue;
+    const size_t q = o + (ptrdiff_t)k * G.LD;
+    double row = vm * in[q - 1] + v0 * in[q] + vp * in[q + 1];
+    s += (k == 0 ? 0.5 : 0.25) * row;
+  }
+  out[o] = s;
+}
+
+__global__ void k_inject_sigma(Grid G, const double *__restrict__ Er, double t, double *sig, long long *smax) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= G.nth) return;
+  const Metric &m = G.m;
+  const double rb0 = m.r_h[G.PI];
+  double E[3], B[3];
+  vacuum_field<double>(G, rb0, m.sin_t[j + G.PJ], m.cos_t[j + G.PJ], t, false, E, B);
+  double e0 = Er[gidx(G, 0, j)] + E[0];
+  vacuum_field<double>(G, rb0, m.sin_t[j + 1 + G.PJ], m.cos_t[j + 1 + G.PJ], t, false, E, B);
+  double e1 = Er[gidx(G, 0, j + 1)] + E[0];
+  double s = 0.5 * (e0 + e1);  // jump of E_r across r0 (zero inside)
+  sig[j] = s;
+  atomicMax(smax, __double_as_longlong(fabs(s)));
+}
+
+template <bool FP32>
+__global__ void k_inject_write(Grid G, const double *__restrict__ sig, const long long *smax, Parts64 P,
+                               Parts32 Q, int64_t base, int64_t id0, int npp, double finj, long long *cnt) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)G.nth * npp * 2) return;
+  const int j = (int)(idx / (2 * npp)), k = (int)((idx / 2) % npp), s = (int)(idx % 2);
+  const double sm = __longlong_as_double(*smax), sg = sig[j];
+  const double r0 = G.r_min;
+  const double dA = 2.0 * PI_D * r0 * r0 * (G.m.cos_t[j + G.PJ] - G.m.cos_t[j + 1 + G.PJ]);
+  const double w = finj * fabs(sg) * dA / npp;
+  const bool on = fabs(sg) > 1e-12 * sm && w > 0.0;
+  const int64_t slot = base + idx;
+  const double q = on ? (s == 0 ? w : -w) : 0.0;
+  const double oy = (k + 0.5) / npp;
+  if (FP32) {
+    Q.cell[slot] = ((uint32_t)(0 + CELL_BIAS) << 16) | (uint32_t)j;
+    Q.dx[slot] = 0.5f;
+    Q.dy[slot] = (float)oy;
+    Q.ur[slot] = Q.ut[slot] = Q.up[slot] = 0.0f;
+    Q.qw[slot] = (float)q;
+    Q.id[slot] = id0 + idx;
+  } else {
+    P.x1[slot] = 0.5;
+    P.x2[slot] = j + oy;
+    P.ur[slot] = P.ut[slot] = P.up[slot] = 0.0;
+    P.qw[slot] = q;
+    P.id[slot] = id0 + idx;
+  }
+  if (on) add_ll(cnt, 1LL);
+}
+
+__device__ inline double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Integral Gauss law per dual cell: G = flux of E out of the dual cell of node
+// (i, j) (caps close at the axis); d = G - Qbar.  snapshot: store d; else
+// reduce max |d - d_0| and max |Q| over interior nodes 1 <= i <= imax.
+__global__ void k_gauss(Grid G, const double *__restrict__ Er, const double *__restrict__ Et,
+                        const double *__restrict__ Qf, const double *__restrict__ Qa, double *snap, int imax,
+                        int snapshot, long long *gmax, long long *qmax) {
+  const int j = blockIdx.x * BX + threadIdx.x, i = 1 + blockIdx.y * BY + threadIdx.y;
+  double v = 0.0, qa = 0.0;
+  if (i <= imax && j <= G.nth) {
+    const Metric &m = G.m;
+    const int ri = i + G.PI, cj = j + G.PJ;
+    const size_t o = gidx(G, i, j);
+    const double dc = 1.0 / m.inv_dcos_tb[cj];
+    const double ar = 2.0 * PI_D * m.r_h[ri] * m.r_h[ri], al = 2.0 * PI_D * m.r_h[ri - 1] * m.r_h[ri - 1];
+    const double side = PI_D * (m.r_h[ri] * m.r_h[ri] - m.r_h[ri - 1] * m.r_h[ri - 1]);
+    double g = Er[o] * ar * dc - Er[o - G.LD] * al * dc + (Et[o] * m.sin_tb[cj] - Et[o - 1] * m.sin_tb[cj - 1]) * side;
+    double d = g - Qf[o];
+    if (snapshot) snap[o] = d;
+    else v = fabs(d - snap[o]);
+    qa = Qa[o];
+  }
+  v = warp_max(v);
+  qa = warp_max(qa);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(gmax, __double_as_longlong(v));
+    atomicMax(qmax, __double_as_longlong(qa));
+  }
+}
+
+__global__ void k_field_energy(Grid G, const double *f0, const double *f1, const double *f2, const double *f3,
+                               const double *f4, const double *f5, double *acc) {
+  const int j = blockIdx.x * BX + threadIdx.x, i = blockIdx.y * BY + threadIdx.y;
+  double e = 0.0;
+  if (i <= G.nr && j <= G.nth) {
+    const Metric &m = G.m;
+    const int ri = i + G.PI, cj = j + G.PJ;
+    const size_t o = gidx(G, i, j);
+    const double *fs[6] = {f0, f1, f2, f3, f4, f5};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const int si = stag_i(c), sj = stag_j(c);
+      if ((si && i >= G.nr) || (sj && j >= G.nth)) continue;
+      const double vr = si ? m.vol_r_h[ri] : m.vol_r_n[ri];
+      const double vt = sj ? m.vol_t_h[cj] : m.vol_t_n[cj];
+      const double v = fs[c][o];
+      e += 0.5 * v * v * vr * vt;
+    }
+  }
+  e = warp_sum(e);
+  if ((threadIdx.x & 31) == 0) atomicAdd(acc, e);
+}
+
+}  // namespace
+
+void fields_b_half(pic_ctx *c) {
+  const Grid &G = c->G;
+  k_b_half<<<grid2(G.nr + 1, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(G, c->f[ER], c->f[ETH], c->f[EPH], c->f[BR],
+                                                                      c->f[BTH], c->f[BPH], 0.5 * G.dt);
+}
+
+void fields_e_full(pic_ctx *c) {
+  const Grid &G = c->G;
+  k_e_full<<<grid2(G.nr + 1, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(
+      G, c->f[ER], c->f[ETH], c->f[EPH], c->f[BR], c->f[BTH], c->f[BPH], c->F[0], c->F[1], c->F[2], G.dt);
+}
+
+void fields_fill_ghosts(pic_ctx *c) {
+  const Grid &G = c->G;
+  k_axis_ghosts<<<(G.nr + 1 + 127) / 128, 128, 0, c->stream>>>(G, c->f[ETH], c->f[BR], c->f[BPH]);
+  if (c->d.precision == PIC_FP32) {
+    k_copy32<<<4 * 152, 256, 0, c->stream>>>(c->grid_elems, c->f[0], c->f[1], c->f[2], c->f[3], c->f[4], c->f[5],
+                                            c->f32[0], c->f32[1], c->f32[2], c->f32[3], c->f32[4], c->f32[5]);
+  }
+}
+
+void fields_finish(pic_ctx *c) {
+  const Grid &G = c->G;
+  if (c->d.absorb_profile != PIC_ABSORB_NONE && c->d.absorb_cells > 0) {
+    int i0 = G.nr - G.absorb_cells - 1;
+    if (i0 < 0) i0 = 0;
+    k_lossy<<<grid2(G.nr + 1 - i0, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(G, c->f[0], c->f[1], c->f[2], c->f[3],
+                                                                           c->f[4], c->f[5], i0);
+  }
+  fields_fill_ghosts(c);
+}
+
+void filter_array(pic_ctx *c, double *a, double *tmp, int half_j, int sign, int passes) {
+  (void)sign;  // the fold sign is built into the weights of k_filter
+  const Grid &G = c->G;
+  dim3 gr = grid2(G.nr + 2 * G.g + 1, G.nth + 1);
+  double *src = a, *dst = tmp;
+  for (int p = 0; p < passes; ++p) {
+    k_filter<<<gr, dim3(BX, BY), 0, c->stream>>>(G, src, dst, half_j);
+    double *t = src; src = dst; dst = t;
+  }
+  if (src != a)
+    cudaMemcpyAsync(a, src, c->grid_elems * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+}
+
+void fields_filter(pic_ctx *c) {
+  const int n = c->d.n_filt;
+  if (n <= 0) return;
+  const Grid &G = c->G;
+  dim3 gr = grid2(G.nr + 2 * G.g + 1, G.nth + 1);
+  for (int p = 0; p < n; ++p) {
+    for (int k = 0; k < 3; ++k)
+      k_filter<<<gr, dim3(BX, BY), 0, c->stream>>>(G, c->F[k], c->Ft[k], k == 1);
+    for (int k = 0; k < 3; ++k) { double *t = c->F[k]; c->F[k] = c->Ft[k]; c->Ft[k] = t; }
+  }
+}
+
+void inject(pic_ctx *c, double t) {
+  const Grid &G = c->G;
+  const int npp = c->d.pairs_per_cell;
+  long long *smax = c->d_cnt + CNT_SMAX;
+  cudaMemsetAsync(smax, 0, sizeof(long long), c->stream);
+  k_inject_sigma<<<(G.nth + 127) / 128, 128, 0, c->stream>>>(G, c->f[ER], t, c->sig, smax);
+  const int64_t nslots = (int64_t)G.nth * npp * 2;
+  const int blocks = (int)((nslots + 255) / 256);
+  if (c->d.precision == PIC_FP32)
+    k_inject_write<true><<<blocks, 256, 0, c->stream>>>(G, c->sig, smax, c->p64, c->p32, c->n_used, c->next_id, npp,
+                                                        c->d.f_inj, c->d_cnt + CNT_INJECTED);
+  else
+    k_inject_write<false><<<blocks, 256, 0, c->stream>>>(G, c->sig, smax, c->p64, c->p32, c->n_used, c->next_id, npp,
+                                                         c->d.f_inj, c->d_cnt + CNT_INJECTED);
+  c->n_used += nslots;
+  c->next_id += nslots;
+}
+
+void moments(pic_ctx *c, bool snapshot, pic_moments *out) {
+  const Grid &G = c->G;
+  cudaMemsetAsync(c->Q, 0, c->grid_elems * sizeof(double), c->stream);
+  cudaMemsetAsync(c->Qa, 0, c->grid_elems * sizeof(double), c->stream);
+  if (c->d.precision == PIC_FP32) charge32(c, c->Q, c->Qa);
+  else charge64(c, c->Q, c->Qa);
+  filter_array(c, c->Q, c->Qt, 0, +1, c->d.n_filt);
+  int L = c->d.absorb_profile == PIC_ABSORB_NONE ? 0 : c->d.absorb_cells;
+  int imax = G.nr - L - 1;
+  cudaMemsetAsync(c->d_cnt + CNT_GMAX, 0, 2 * sizeof(long long), c->stream);
+  if (imax >= 1)
+    k_gauss<<<grid2(imax, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(G, c->f[ER], c->f[ETH], c->Q, c->Qa, c->gsnap,
+                                                                    imax, snapshot ? 1 : 0, c->d_cnt + CNT_GMAX,
+                                                                    c->d_cnt + CNT_QMAX);
+  if (snapshot) { c->have_snap = true; return; }
+  cudaMemsetAsync(c->d_acc, 0, ACC_N * sizeof(double), c->stream);
+  cudaMemsetAsync(c->d_cnt + CNT_LIVE, 0, sizeof(long long), c->stream);
+  k_field_energy<<<grid2(G.nr + 1, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(
+      G, c->f[0], c->f[1], c->f[2], c->f[3], c->f[4], c->f[5], c->d_acc + ACC_FIELD);
+  if (c->d.precision == PIC_FP32) reduce_particles32(c);
+  else reduce_particles64(c);
+  long long cnt[CNT_N];
+  double acc[ACC_N];
+  cudaMemcpyAsync(cnt, c->d_cnt, sizeof cnt, cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(acc, c->d_acc, sizeof acc, cudaMemcpyDeviceToHost, c->stream);
+  cudaStreamSynchronize(c->stream);
+  double gmax, qmax;
+  memcpy(&gmax, &cnt[CNT_GMAX], sizeof(double));
+  memcpy(&qmax, &cnt[CNT_QMAX], sizeof(double));
+  out->live = cnt[CNT_LIVE];
+  out->deleted = cnt[CNT_DELETED];
+  out->injected = cnt[CNT_INJECTED];
+  out->step = c->step;
+  out->dt = G.dt;
+  out->time = c->step * G.dt;
+  out->kinetic_energy = acc[ACC_KIN];
+  out->field_energy = acc[ACC_FIELD];
+  out->total_charge = acc[ACC_CHARGE];
+  out->gauss_residual = (!c->have_snap) ? -1.0 : (qmax > 0 ? gmax / qmax : gmax);
+}
+
+}  // namespace pic

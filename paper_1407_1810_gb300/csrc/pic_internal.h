@@ -1,0 +1,116 @@
+// pic_internal.h -- host-side context of the library and the launchers each
+// translation unit provides.  Not part of the public C-ABI (include/picsar.h).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/picsar.h"
+#include "pic_common.cuh"
+
+namespace pic {
+
+// FP64 particle arrays (structure of arrays, 56 B per particle with the id)
+struct Parts64 {
+  double *x1 = nullptr, *x2 = nullptr, *ur = nullptr, *ut = nullptr, *up = nullptr, *qw = nullptr;
+  int64_t *id = nullptr;
+};
+// FP32 particle arrays: packed cell (i + CELL_BIAS) << 16 | j, FP32 offsets in
+// the cell, FP32 momentum and charge; 28 B per particle plus the 8 B id
+struct Parts32 {
+  uint32_t *cell = nullptr;
+  float *dx = nullptr, *dy = nullptr, *ur = nullptr, *ut = nullptr, *up = nullptr, *qw = nullptr;
+  int64_t *id = nullptr;
+};
+constexpr int CELL_BIAS = 1024;
+
+// device counters (one int64 array)
+enum Counter { CNT_DELETED = 0, CNT_INJECTED = 1, CNT_LIVE = 2, CNT_SMAX = 3, CNT_GMAX = 4,
+               CNT_QMAX = 5, CNT_SORTED = 6, CNT_N };
+// device double accumulators
+enum Accum { ACC_KIN = 0, ACC_FIELD = 1, ACC_CHARGE = 2, ACC_N };
+
+struct Tiles {  // FP32 path: tile bins after the last sort
+  int TI = 16, TJ = 16, H = 2;  // tile size in cells and halo
+  int nti = 0, ntj = 0, ntiles = 0;
+  int row0 = 0;                   // first tile row (cell index)
+  int64_t *start = nullptr;       // ntiles + 1 bin starts
+  int64_t *cursor = nullptr;      // scatter cursors
+  int64_t sorted_end = 0;         // particles [0, sorted_end) are binned
+};
+
+enum ProfSlot { PROF_PARTICLES = 0, PROF_REDUCE = 1, PROF_FILTER = 2, PROF_FIELDS = 3, PROF_INJECT = 4,
+                PROF_SORT = 5, PROF_N };
+
+}  // namespace pic
+
+struct pic_ctx {
+  pic_desc d{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  pic::Grid G{};
+  double *metric_buf = nullptr;
+  size_t grid_elems = 0;  // elements of one padded grid array
+  double *f[6] = {};      // plasma fields (FP64)
+  double *F[3] = {};      // fluxes of the current step (FP64, after filtering)
+  double *Ft[3] = {};     // filter double buffer
+  float *f32[6] = {};     // FP32 gather copies (FP32 path)
+  long long *acc[3] = {}; // fixed-point flux accumulators (FP32 path)
+  double flux_quantum = 0.0;
+  double *Q = nullptr, *Qa = nullptr, *Qt = nullptr, *gsnap = nullptr;
+  bool have_snap = false;
+  double *sig = nullptr;  // injection: surface charge per cell
+  // particles
+  int64_t cap = 0, n_used = 0;
+  pic::Parts64 p64, q64;  // current and alternate (compaction) buffers
+  pic::Parts32 p32, q32;
+  pic::Tiles tiles;
+  void *scratch = nullptr;  // compaction / sort scratch
+  size_t scratch_bytes = 0;
+  int *d_err = nullptr;
+  long long *d_cnt = nullptr;
+  double *d_acc = nullptr;
+  long long *h_pinned = nullptr;  // pinned host mirror for small reads
+  int64_t step = 0, next_id = 0;
+  int host_err = 0;
+  int steps_since_sort = 0;
+  // profiling
+  bool prof = false;
+  cudaEvent_t ev[2 * pic::PROF_N] = {};
+  double prof_ms[pic::PROF_N] = {};
+  int64_t prof_launch[pic::PROF_N] = {};
+  int64_t prof_steps = 0;
+};
+
+namespace pic {
+// fields.cu
+void fields_b_half(pic_ctx *c);
+void fields_e_full(pic_ctx *c);
+void fields_finish(pic_ctx *c);        // lossy layer + axis ghosts (+ FP32 copies)
+void fields_filter(pic_ctx *c);        // n_filt passes on F
+void fields_fill_ghosts(pic_ctx *c);   // axis ghosts only (after pic_set_fields)
+void inject(pic_ctx *c, double t);     // surface pairs into slots [n_used, n_used + 2 npp nth)
+void moments(pic_ctx *c, bool snapshot, pic_moments *out);
+void filter_array(pic_ctx *c, double *a, double *tmp, int half_j, int sign, int passes);
+// particles64.cu
+void particles64(pic_ctx *c, double t);
+int64_t compact64(pic_ctx *c);         // stable removal of dead slots; returns live count
+void charge64(pic_ctx *c, double *Q, double *Qa);
+void reduce_particles64(pic_ctx *c);   // kinetic energy, live count, total charge
+// particles32.cu
+void particles32(pic_ctx *c, double t);
+void flux_from_acc(pic_ctx *c);        // fixed point -> FP64 fluxes, clears the accumulators
+int64_t sort32(pic_ctx *c);            // tile sort + removal; returns live count
+void charge32(pic_ctx *c, double *Q, double *Qa);
+void reduce_particles32(pic_ctx *c);
+}  // namespace pic
+
+// error plumbing (api.cu)
+int pic_fail(int code, const std::string &msg);
+int pic_cuda_check(cudaError_t e, const char *what);
+#define PIC_CUDA(call)                                          \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return pic_cuda_check(e_, #call);    \
+  } while (0)

@@ -1,0 +1,221 @@
+"""Thin ctypes binding of the C-ABI in include/picsar.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``_build/libpicsar_gb300.so``;
+this module only converts Python/NumPy/torch arguments to pointers.  There is
+no CPU fallback: if the library is missing the import of ``lib()`` fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpicsar_gb300.so")
+
+PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ECAPACITY, PIC_ENAN, PIC_ECOURANT, PIC_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
+PIC_R_LINEAR, PIC_R_LOG = 0, 1
+PIC_TH_LINEAR, PIC_TH_EQUAL_AREA = 0, 1
+PIC_ABSORB_NONE, PIC_ABSORB_LINEAR, PIC_ABSORB_QUADRATIC = 0, 1, 2
+PIC_VAC_NONE, PIC_VAC_MONOPOLE, PIC_VAC_MONOPOLE_ROTATOR, PIC_VAC_UNIFORM_BZ, PIC_VAC_DIPOLE_COROT = 0, 1, 2, 3, 4
+PIC_FP64, PIC_FP32 = 0, 1
+PIC_VAY, PIC_BORIS = 0, 1
+PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
+
+EXPORTS = ["pic_init_grid", "pic_load_particles", "pic_step", "pic_get_fields", "pic_set_fields", "pic_get_flux",
+           "pic_get_particles", "pic_get_moments", "pic_gauss_snapshot", "pic_set_clock", "pic_profile",
+           "pic_get_profile", "pic_ensemble_step", "pic_destroy", "pic_last_error"]
+
+
+class pic_desc(C.Structure):
+    _fields_ = [
+        ("nr", C.c_int32), ("nth", C.c_int32),
+        ("r_min", C.c_double), ("r_max", C.c_double),
+        ("r_map", C.c_int32), ("th_map", C.c_int32),
+        ("courant", C.c_double), ("dt", C.c_double),
+        ("n_filt", C.c_int32),
+        ("absorb_cells", C.c_int32), ("absorb_profile", C.c_int32), ("absorb_sigma_max", C.c_double),
+        ("vacuum", C.c_int32), ("b0", C.c_double), ("omega", C.c_double), ("t_spin", C.c_double),
+        ("inject", C.c_int32), ("pairs_per_cell", C.c_int32), ("f_inj", C.c_double),
+        ("precision", C.c_int32), ("pusher", C.c_int32),
+        ("q_over_m", C.c_double),
+        ("sort_interval", C.c_int32), ("capacity", C.c_int64),
+        ("flux_quantum", C.c_double),
+    ]
+
+
+class pic_moments(C.Structure):
+    _fields_ = [
+        ("live", C.c_int64), ("deleted", C.c_int64), ("injected", C.c_int64), ("step", C.c_int64),
+        ("time", C.c_double), ("dt", C.c_double),
+        ("kinetic_energy", C.c_double), ("field_energy", C.c_double),
+        ("gauss_residual", C.c_double), ("total_charge", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not built: run paper_1407_1810_gb300.build.build() (needs nvcc)")
+    L = C.CDLL(LIB_PATH)
+    P, D, I64, I32 = C.c_void_p, C.POINTER(C.c_double), C.c_int64, C.c_int32
+    sig = {
+        "pic_init_grid": [C.POINTER(C.c_void_p), C.POINTER(pic_desc), P],
+        "pic_load_particles": [P, I64, P, P, P, P, P, P, I32],
+        "pic_step": [P, I32],
+        "pic_get_fields": [P, I32, P, C.POINTER(C.c_int64), I32],
+        "pic_set_fields": [P, P, I32],
+        "pic_get_flux": [P, P, C.POINTER(C.c_int64), I32],
+        "pic_get_particles": [P, C.POINTER(C.c_int64), P, P, P, P, P, P, P, I32],
+        "pic_get_moments": [P, C.POINTER(pic_moments)],
+        "pic_gauss_snapshot": [P],
+        "pic_set_clock": [P, I64, I64],
+        "pic_profile": [P, I32],
+        "pic_get_profile": [P, D, C.POINTER(C.c_int64)],
+        "pic_ensemble_step": [C.POINTER(C.c_void_p), I32, I32],
+        "pic_destroy": [P],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.pic_last_error.restype = C.c_char_p
+    L.pic_last_error.argtypes = []
+    _lib = L
+    return L
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"picsar error {code}: {msg}")
+        self.code = code
+
+
+def check(rc):
+    if rc != PIC_OK:
+        raise PicError(rc, lib().pic_last_error().decode())
+    return rc
+
+
+def make_desc(**kw) -> pic_desc:
+    d = pic_desc()
+    enums = {
+        "r_map": {"linear": 0, "log": 1}, "th_map": {"linear": 0, "equal_area": 1},
+        "absorb_profile": {"none": 0, "linear": 1, "quadratic": 2},
+        "vacuum": {"none": 0, "monopole": 1, "monopole_rotator": 2, "uniform_bz": 3, "dipole_corot": 4},
+        "precision": {"fp64": 0, "fp32": 1}, "pusher": {"vay": 0, "boris": 1},
+    }
+    for k, v in kw.items():
+        if k in enums and isinstance(v, str):
+            v = enums[k][v]
+        setattr(d, k, v)
+    return d
+
+
+def _ptr(a):
+    """(pointer, mem) of a contiguous float64/int64 numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return C.c_void_p(a.ctypes.data), PIC_MEM_HOST
+    # torch tensor
+    assert a.is_contiguous()
+    return C.c_void_p(a.data_ptr()), (PIC_MEM_DEVICE if a.is_cuda else PIC_MEM_HOST)
+
+
+class Simulation:
+    """One context of the library: pic_init_grid .. pic_destroy."""
+
+    def __init__(self, desc: pic_desc, stream: int = 0):
+        self.L = lib()
+        self.desc = desc
+        h = C.c_void_p()
+        check(self.L.pic_init_grid(C.byref(h), C.byref(desc), C.c_void_p(stream)))
+        self.h = h
+        self.nr, self.nth = desc.nr, desc.nth
+        self.g = desc.n_filt + 2
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, x1, x2, ur, uth, uph, qw):
+        ptrs = [_ptr(a) for a in (x1, x2, ur, uth, uph, qw)]
+        mems = {m for _, m in ptrs}
+        assert len(mems) == 1, "all arrays on the host or all on the device"
+        n = len(x1)
+        check(self.L.pic_load_particles(self.h, n, *[p for p, _ in ptrs], mems.pop()))
+
+    def step(self, n=1):
+        return check(self.L.pic_step(self.h, n))
+
+    def step_rc(self, n=1):
+        return self.L.pic_step(self.h, n)
+
+    def fields(self):
+        n = C.c_int64()
+        check(self.L.pic_get_fields(self.h, 0, None, C.byref(n), PIC_MEM_HOST))
+        out = np.empty(n.value)
+        check(self.L.pic_get_fields(self.h, 0, C.c_void_p(out.ctypes.data), C.byref(n), PIC_MEM_HOST))
+        return out.reshape(6, self.nr + 1, self.nth + 1)
+
+    def set_fields(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        check(self.L.pic_set_fields(self.h, C.c_void_p(f.ctypes.data), PIC_MEM_HOST))
+
+    def flux(self):
+        n = C.c_int64()
+        check(self.L.pic_get_flux(self.h, None, C.byref(n), PIC_MEM_HOST))
+        out = np.empty(n.value)
+        check(self.L.pic_get_flux(self.h, C.c_void_p(out.ctypes.data), C.byref(n), PIC_MEM_HOST))
+        return out.reshape(3, self.nr + 2 * self.g + 1, self.nth + 1)
+
+    def particles(self):
+        n = C.c_int64(0)
+        check(self.L.pic_get_particles(self.h, C.byref(n), None, None, None, None, None, None, None, PIC_MEM_HOST))
+        m = n.value
+        out = {k: np.empty(m) for k in ("x1", "x2", "ur", "uth", "uph", "qw")}
+        ids = np.empty(m, dtype=np.int64)
+        ptrs = [C.c_void_p(out[k].ctypes.data) for k in ("x1", "x2", "ur", "uth", "uph", "qw")]
+        check(self.L.pic_get_particles(self.h, C.byref(n), *ptrs, C.c_void_p(ids.ctypes.data), PIC_MEM_HOST))
+        out["id"] = ids
+        return out
+
+    def moments(self):
+        m = pic_moments()
+        check(self.L.pic_get_moments(self.h, C.byref(m)))
+        return {k: getattr(m, k) for k, _ in pic_moments._fields_}
+
+    def gauss_snapshot(self):
+        check(self.L.pic_gauss_snapshot(self.h))
+
+    def set_clock(self, step, next_id):
+        check(self.L.pic_set_clock(self.h, step, next_id))
+
+    def profile(self, enable=True):
+        check(self.L.pic_profile(self.h, 1 if enable else 0))
+
+    def get_profile(self):
+        ms = (C.c_double * 6)()
+        steps = C.c_int64()
+        check(self.L.pic_get_profile(self.h, ms, C.byref(steps)))
+        names = ["particles", "reduce", "filter", "fields", "inject", "sort"]
+        return dict(zip(names, list(ms))), steps.value
+
+
+def ensemble_step(sims, nsteps):
+    arr = (C.c_void_p * len(sims))(*[s.h for s in sims])
+    return check(lib().pic_ensemble_step(arr, len(sims), nsteps))

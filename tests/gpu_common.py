@@ -1,0 +1,59 @@
+"""Helpers shared by the GPU parity tests: build both sides from one config."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+from oracle.oracle import courant_dt
+from paper_1407_1810_gb300 import configs, synthetic
+
+KEYS = ("x1", "x2", "ur", "uth", "uph", "qw")
+
+
+def fp32_state(d):
+    """The FP32 path stores x as (cell, FP32 offset) and u, qw in FP32; this is
+    the exact FP64 value of that state, which both sides then start from."""
+    out = dict(d)
+    for k in ("x1", "x2"):
+        c = np.floor(d[k])
+        out[k] = c + (d[k] - c).astype(np.float32).astype(np.float64)
+    for k in ("ur", "uth", "uph", "qw"):
+        out[k] = d[k].astype(np.float32).astype(np.float64)
+    return out
+
+
+def setup(cfg: dict, plasma: dict | None = None, precision: str | None = None, **over):
+    """(gpu Simulation, oracle, plasma dict, dt) for a config dict."""
+    from paper_1407_1810_gb300 import picsar as P
+
+    prec = precision or cfg["precision"]
+    ok = configs.oracle_kwargs(cfg, 0.0, 0.0)
+    ok.update({k: v for k, v in over.items() if k in ok})
+    p = O.params(**ok)
+    dt = over.get("dt") or courant_dt(p, cfg["courant"])
+    b0, qw = configs.physics(cfg, dt)
+    if "b0" in over:
+        b0 = over["b0"]
+    p.dt, p.b0 = dt, b0
+    o = O.Oracle(p)
+    dk = configs.desc_kwargs(cfg, dt, b0, precision=prec)
+    dk.update({k: v for k, v in over.items() if k in dk})
+    s = P.Simulation(P.make_desc(**dk))
+    if plasma is None:
+        plasma = synthetic.pair_plasma(cfg["nr"], cfg["nth"], cfg["pairs_per_cell"], cfg["T"], qw, cfg["seed"])
+    if prec == "fp32":
+        plasma = fp32_state(plasma)
+    if len(plasma["x1"]):
+        o.load(*(plasma[k] for k in KEYS))
+        s.load(*(np.ascontiguousarray(plasma[k]) for k in KEYS))
+    return s, o, plasma, dt
+
+
+def by_id(d):
+    order = np.argsort(d["id"])
+    return {k: v[order] for k, v in d.items()}
+
+
+def rel_l2(a, b):
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (den if den > 0 else 1.0)

@@ -1,0 +1,192 @@
+"""GPU parity of the plain FP64 path against the FP64 oracle (through the C-ABI).
+
+Bar (FP64 path): fields, fluxes and momenta within 1e-12 relative after 100
+steps; particle counts, cells, injections and removals exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.oracle import courant_dt
+from paper_1407_1810_gb300 import configs, synthetic
+
+from gpu_common import KEYS, by_id, rel_l2, setup
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1407_1810_gb300 import build
+
+    build.build()
+    O.build_oracle()
+
+
+def _compare_particles(s, o, tol=TOL):
+    g, r = by_id(s.particles()), by_id(o.particles())
+    assert np.array_equal(g["id"], r["id"])
+    assert np.max(np.abs(g["x1"] - r["x1"])) < tol * 100
+    assert np.max(np.abs(g["x2"] - r["x2"])) < tol * 100
+    umag = np.sqrt(r["ur"] ** 2 + r["uth"] ** 2 + r["uph"] ** 2) + 1e-3
+    for k in ("ur", "uth", "uph"):
+        assert np.max(np.abs(g[k] - r[k]) / umag) < tol * 10, k
+    assert np.array_equal(g["qw"], r["qw"])
+    # cells are bit-exact (no particle here sits within 1e-9 of a grid line)
+    assert np.array_equal(np.floor(g["x1"]), np.floor(r["x1"]))
+    assert np.array_equal(np.floor(g["x2"]), np.floor(r["x2"]))
+    return g, r
+
+
+def test_monopole_64x64_100_steps():
+    """The small FP64 workload (64x64, log r in [1, 10], monopole, 98,304
+    Maxwell-Juttner particles, lossy 8 cells), 100 steps."""
+    cfg = configs.CONFIGS["monopole-64x64"]
+    s, o, plasma, dt = setup(cfg)
+    assert len(plasma["x1"]) == 98304
+    o.gauss_snapshot()
+    s.step(cfg["steps"])
+    o.step(cfg["steps"])
+    assert o.error() == 0
+    assert rel_l2(s.fields(), o.fields()) < TOL
+    assert rel_l2(s.flux(), o.flux()) < TOL
+    m = s.moments()
+    cnt = o.counters()
+    assert m["live"] == cnt["live"] and m["deleted"] == cnt["deleted"]
+    assert m["gauss_residual"] < 1e-12
+    assert o.gauss_residual() < 1e-12
+    assert m["kinetic_energy"] == pytest.approx(o.kinetic_energy(), rel=TOL)
+    assert m["field_energy"] == pytest.approx(o.field_energy(), rel=1e-10)
+    _compare_particles(s, o)
+
+
+@pytest.mark.parametrize("pusher", ["vay", "boris"])
+@pytest.mark.parametrize("th_map", ["equal_area", "linear"])
+def test_rotator_injection_filter(pusher, th_map):
+    """Rotating monopole with spin-up, surface injection, N_filt = 3 with the
+    polar fold, quadratic lossy layer: a 40x32 version of the rotator run."""
+    cfg = dict(configs.CONFIGS["rotator-512x512"], nr=40, nth=32, pairs_per_cell=2, absorb_cells=8,
+               pusher=pusher, th_map=th_map, t_spin=2.0)
+    s, o, plasma, dt = setup(cfg)
+    o.gauss_snapshot()
+    for _ in range(3):
+        s.step(20)
+        o.step(20)
+        assert rel_l2(s.fields(), o.fields()) < TOL
+    cnt, m = o.counters(), s.moments()
+    assert cnt["injected"] > 0 and cnt["deleted"] > 0
+    assert m["injected"] == cnt["injected"] and m["deleted"] == cnt["deleted"] and m["live"] == cnt["live"]
+    assert m["gauss_residual"] < 1e-11
+    _compare_particles(s, o)
+
+
+def test_one_step_replay_from_gpu_state():
+    """Load the GPU's exact state into a fresh oracle and replay one step."""
+    cfg = dict(configs.CONFIGS["rotator-512x512"], nr=32, nth=32, pairs_per_cell=3, absorb_cells=8, t_spin=1.0)
+    s, o, plasma, dt = setup(cfg)
+    s.step(15)
+    st = s.particles()
+    f = s.fields()
+    o2 = O.Oracle(o.p)
+    o2.load(*(st[k] for k in KEYS), ids=st["id"])
+    o2.set_fields(f)
+    m = s.moments()
+    o2.set_clock(15, o.counters()["next_id"] + 15 * 2 * 2 * 32)
+    s.step(1)
+    o2.step(1)
+    assert rel_l2(s.flux(), o2.flux()) < TOL
+    assert rel_l2(s.fields(), o2.fields()) < TOL
+    _compare_particles(s, o2)
+
+
+def test_tm_mode_field_solve():
+    """Field-only leapfrog on a TM mode (Sec. 4.1 set-up) in (xi, theta_A)."""
+    from scipy.optimize import brentq
+
+    du1 = lambda r: np.cos(r) / r - np.sin(r) / r**2 + np.sin(r)
+    rin, rout = brentq(du1, 1.5, 2.5), brentq(du1, 12.0, 13.0)
+    N = 48
+    cfg = dict(configs.CONFIGS["monopole-64x64"], nr=N, nth=N, r_min=rin, r_max=rout, th_map="equal_area",
+               vacuum="none", absorb_profile="none", absorb_cells=0, pairs_per_cell=0)
+    empty = {k: np.zeros(0) for k in KEYS}
+    s, o, _, dt = setup(cfg, plasma=empty)
+    rb = o.f_r(np.arange(N) + 0.5)
+    tb = o.f_th(np.arange(N) + 0.5)
+    u1 = np.sin(rb) / rb - np.cos(rb)
+    f = np.zeros(o.field_shape)
+    f[5, :N, :N] = (u1 / rb)[:, None] * np.sin(tb)[None, :]
+    o.set_fields(f)
+    s.set_fields(f)
+    s.step(150)
+    o.field_step(150)
+    assert rel_l2(s.fields(), o.fields()) < 1e-13
+
+
+def test_static_monopole_on_gpu():
+    N = 32
+    cfg = dict(configs.CONFIGS["monopole-64x64"], nr=N, nth=N, vacuum="none", absorb_profile="none",
+               absorb_cells=0, pairs_per_cell=0)
+    empty = {k: np.zeros(0) for k in KEYS}
+    s, o, _, dt = setup(cfg, plasma=empty)
+    f = np.zeros(o.field_shape)
+    r = o.f_r(np.arange(N + 1))
+    f[3, :, :N] = (1.0 / r**2)[:, None]
+    s.set_fields(f)
+    s.step(100)
+    assert np.max(np.abs(s.fields() - f)) < 1e-14
+
+
+def test_edge_particles_and_errors():
+    """Particles on the axis, on the last node, deep in both ghost bands; an
+    empty step; rejected loads."""
+    from paper_1407_1810_gb300 import picsar as P
+
+    cfg = dict(configs.CONFIGS["monopole-64x64"], nr=16, nth=16, n_filt=2, pairs_per_cell=0)
+    nf = 2
+    pts = np.array([[0.0, 0.0], [3.5, 16.0], [-(nf + 1) + 1e-9, 5.2], [16 + nf + 0.999, 9.1], [15.9999, 0.0],
+                    [8.0, 8.0], [0.0, 16.0]])
+    plasma = {"x1": pts[:, 0].copy(), "x2": pts[:, 1].copy(),
+              "ur": np.array([0.3, -0.2, -2.0, 2.0, 1.0, 0.0, 0.1]),
+              "uth": np.array([-0.5, 0.5, 0.1, 0.0, 0.2, 0.0, -0.3]),
+              "uph": np.array([0.7, 0.1, 0.0, 0.3, -0.4, 0.0, 0.2]),
+              "qw": np.array([1e-3, -1e-3, 1e-3, -1e-3, 1e-3, -1e-3, 1e-3])}
+    s, o, _, dt = setup(cfg, plasma=plasma)
+    for _ in range(4):
+        s.step(1)
+        o.step(1)
+        assert rel_l2(s.flux(), o.flux()) < TOL
+    _compare_particles(s, o)
+    assert s.moments()["deleted"] == o.counters()["deleted"]
+    # an empty context steps
+    empty = {k: np.zeros(0) for k in KEYS}
+    s2, _, _, _ = setup(cfg, plasma=empty)
+    s2.step(3)
+    assert s2.moments()["live"] == 0
+    # invalid particles are rejected with PIC_EINVAL
+    bad = {k: np.array([1.0]) for k in KEYS}
+    bad["x2"] = np.array([17.0])
+    with pytest.raises(P.PicError) as e:
+        s2.load(*(bad[k] for k in KEYS))
+    assert e.value.code == P.PIC_EINVAL
+    bad = {k: np.array([1.0]) for k in KEYS}
+    bad["qw"] = np.array([0.0])
+    with pytest.raises(P.PicError):
+        s2.load(*(bad[k] for k in KEYS))
+
+
+def test_capacity_grows_under_injection():
+    cfg = dict(configs.CONFIGS["rotator-512x512"], nr=24, nth=16, pairs_per_cell=1, absorb_cells=4, t_spin=0.0)
+    s, o, plasma, dt = setup(cfg, sort_interval=1000)
+    for _ in range(5):
+        s.step(40)
+        o.step(40)
+    m, cnt = s.moments(), o.counters()
+    assert m["live"] == cnt["live"] and m["injected"] == cnt["injected"]
+    assert rel_l2(s.fields(), o.fields()) < TOL
