@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Throughput of the PICsar particle hot path on GB300: particle-steps/s.
+
+Default workload: the large single run on the FP32 cell+offset path (4096 x 4096
+cells, log r in [1, 100], 30 e+/e- pairs per cell = 1.0066e9 particles,
+Maxwell-Juttner T = 0.3 over a monopole field, tile sort every 20 steps), a
+seeded synthetic plasma generated on the device.  One step = the whole time
+step (gather, push, move, deposit, field update, lossy layer, periodic sort).
+
+Printed as one JSON line: the device-timed rate (value), the same metric end to
+end through the C-ABI with the particle state loaded from pinned host memory
+(e2e), the plain FP64 path on the same workload, the hot kernel's roofline,
+the FP64 CPU oracle on a bounded sample (cpu_baseline) and the SM clocks seen
+during the timed region.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun every rank runs an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (gather+push+deposit), FP32 vs FP64 path, at stated Gauss residual"
+UNIT = "particle-steps/s"
+ALG_BYTES_FP32 = 52  # per particle-step: read cell, dx, dy, u (3), qw = 28 B; write cell, dx, dy, u = 24 B
+ALG_BYTES_FP64 = 88  # read x1, x2, u (3), qw = 48 B; write x1, x2, u = 40 B
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="monopole-4096x4096")
+    ap.add_argument("--fp64-steps", type=int, default=20)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic():
+    """DRAM bytes per particle of the tile kernel from the committed ncu
+    summary, if the kernel source has not changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "k_tiles32_traffic.json")
+    src = os.path.join(ROOT, "paper_1407_1810_gb300", "csrc", "particles32.cu")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if d.get("source_sha256_16") != h:
+        return None
+    return float(d["dram_bytes_per_particle"])
+
+
+def make_sim(cfg, precision, stream, capacity):
+    from paper_1407_1810_gb300 import configs
+    from paper_1407_1810_gb300 import picsar as P
+
+    dt = configs.courant_dt(cfg)
+    b0, qw = configs.physics(cfg, dt)
+    kw = configs.desc_kwargs(cfg, dt, b0, precision=precision, capacity=capacity)
+    return P.Simulation(P.make_desc(**kw), stream=stream), qw
+
+
+def load_plasma(sim, cfg, qw, device, stream):
+    import torch
+
+    from paper_1407_1810_gb300 import synthetic
+
+    n = 0
+    with torch.cuda.stream(stream):
+        for ch in synthetic.pair_plasma_torch(cfg["nr"], cfg["nth"], cfg["pairs_per_cell"], cfg["T"], qw,
+                                              cfg["seed"], device, rows_per_chunk=128):
+            sim.load(ch["x1"], ch["x2"], ch["ur"], ch["uth"], ch["uph"], ch["qw"])
+            n += ch["x1"].numel()
+            del ch
+    return n
+
+
+def time_steps(sim, K, stream):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    live0 = sim.live()
+    torch.cuda.synchronize()
+    l0 = sim.launches()
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    l1 = sim.launches()
+    live1 = sim.live()
+    return ms, 0.5 * (live0 + live1) * K, l1 - l0
+
+
+def gpu_arm(args):
+    import torch
+
+    from paper_1407_1810_gb300 import configs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = configs.CONFIGS[args.workload]
+    stream = torch.cuda.Stream(device=dev)
+    ntot = cfg["nr"] * cfg["nth"] * cfg["pairs_per_cell"] * 2
+    cap = ntot + ntot // 64 + (1 << 20)
+    sim, qw = make_sim(cfg, cfg["precision"], stream.cuda_stream, cap)
+    n = load_plasma(sim, cfg, qw, dev, stream)
+    torch.cuda.synchronize()
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    sim.profile(True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ms, units, launches = time_steps(sim, args.steps, stream)
+    ck = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms, units], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        ms_max, units_all = float(mx[0]), float(t[1])
+    else:
+        ms_max, units_all = ms, units
+    prof, psteps = sim.get_profile()
+    mom = sim.moments()
+    value = units_all / (ms_max * 1e-3)
+    live = mom["live"]
+    precision = cfg["precision"]
+    alg = ALG_BYTES_FP32 if precision == "fp32" else ALG_BYTES_FP64
+    kname = "k_tiles32" if precision == "fp32" else "k_particles64"
+    peak, peak_kind = measured_peaks()
+    kms = prof["particles"]
+    achieved = alg * live / (kms * 1e-3) / 1e9 if kms > 0 else None
+    tr = recorded_traffic() if precision == "fp32" else None
+    hot_rate = live / (kms * 1e-3) if kms > 0 else None
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": f"{cfg['nr']}x{cfg['nth']}", "particles": n,
+                   "pairs_per_cell": cfg["pairs_per_cell"], "T": cfg["T"], "path": precision,
+                   "sort_interval": cfg.get("sort_interval", 20), "field_update": "f64",
+                   "l2": "inputs larger than L2 (particle state %.1f GB)" % (n * (36 if precision == "fp32" else 56) / 1e9)},
+        "gauss_residual": mom["gauss_residual"],
+        "hot_kernel": {"name": kname, "ms_per_launch": kms, "particle_steps_per_s": hot_rate},
+        "phase_ms_per_step": prof,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": (tr * live) if tr else None, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_particle_step": alg},
+        "clocks": ck,
+        "gpu_launches": launches,
+    }
+    sim.close()
+    del sim
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_fp64 and precision == "fp32":
+        out["fp64_path"] = fp64_run(cfg, dev, stream, args)
+        if out["fp64_path"].get("value"):
+            out["speedup_vs_fp64_path"] = value / out["fp64_path"]["value"]
+    if not args.no_e2e:
+        try:
+            out["e2e"] = e2e_run(cfg, dev, stream, args)
+        except Exception as exc:  # e.g. not enough pinned host memory for the state
+            out["e2e"] = {"value": None, "unit": UNIT, "error": repr(exc)[:200]}
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(cfg)
+    if world > 1:
+        torch.distributed.barrier()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def fp64_run(cfg, dev, stream, args):
+    import torch
+
+    ntot = cfg["nr"] * cfg["nth"] * cfg["pairs_per_cell"] * 2
+    sim, qw = make_sim(cfg, "fp64", stream.cuda_stream, ntot + (1 << 20))
+    load_plasma(sim, cfg, qw, dev, stream)
+    sim.step(2)
+    sim.profile(True)
+    ms, units, _ = time_steps(sim, args.fp64_steps, stream)
+    prof, _ = sim.get_profile()
+    live = sim.live()
+    kms = prof["particles"]
+    res = {"value": units / (ms * 1e-3), "steps": args.fp64_steps, "ms_per_step": ms / args.fp64_steps,
+           "hot_kernel": {"name": "k_particles64", "ms_per_launch": kms,
+                          "achieved_GBps": ALG_BYTES_FP64 * live / (kms * 1e-3) / 1e9 if kms else None}}
+    sim.close()
+    del sim
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return res
+
+
+def e2e_run(cfg, dev, stream, args):
+    """Same metric through the C-ABI with host buffers: the particle state is
+    copied from pinned host memory by pic_load_particles inside the timed
+    region, then K steps, then the moments are read back to the host."""
+    import torch
+
+    from paper_1407_1810_gb300 import synthetic
+
+    ntot = cfg["nr"] * cfg["nth"] * cfg["pairs_per_cell"] * 2
+    sim, qw = make_sim(cfg, cfg["precision"], stream.cuda_stream, ntot + (1 << 20))
+    host = {k: torch.empty(ntot, dtype=torch.float64, pin_memory=True) for k in ("x1", "x2", "ur", "uth", "uph", "qw")}
+    off = 0
+    with torch.cuda.stream(stream):
+        for ch in synthetic.pair_plasma_torch(cfg["nr"], cfg["nth"], cfg["pairs_per_cell"], cfg["T"], qw,
+                                              cfg["seed"], dev, rows_per_chunk=128):
+            m = ch["x1"].numel()
+            for k in host:
+                host[k][off:off + m].copy_(ch[k])
+            off += m
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.load(*(host[k] for k in ("x1", "x2", "ur", "uth", "uph", "qw")))
+    sim.step(args.steps)
+    mom = sim.moments()  # device -> host read of the step's result (Gauss residual, energies, counts)
+    t1 = time.perf_counter()
+    units = 0.5 * (ntot + mom["live"]) * args.steps
+    sim.close()
+    del sim, host
+    torch.cuda.empty_cache()
+    import ctypes
+
+    from paper_1407_1810_gb300 import picsar as P
+
+    return {"value": units / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": 48 * ntot / args.steps,
+            "d2h_bytes_per_step": ctypes.sizeof(P.pic_moments) / args.steps, "seconds": t1 - t0}
+
+
+SAMPLE_SIDE = 96
+
+
+def oracle_sample(cfg):
+    """A bounded sample of the workload for the FP64 CPU oracle: the same r
+    range and plasma (pairs per cell, temperature, omega_c dt, omega_p dt) on a
+    SAMPLE_SIDE x SAMPLE_SIDE grid."""
+    import oracle as O
+    from paper_1407_1810_gb300 import configs, synthetic
+
+    small = dict(cfg, nr=SAMPLE_SIDE, nth=SAMPLE_SIDE)
+    dt = configs.courant_dt(small)
+    b0, qw = configs.physics(small, dt)
+    o = O.Oracle(O.params(**configs.oracle_kwargs(small, dt, b0)))
+    d = synthetic.pair_plasma(SAMPLE_SIDE, SAMPLE_SIDE, small["pairs_per_cell"], small["T"], qw, small["seed"])
+    o.load(d["x1"], d["x2"], d["ur"], d["uth"], d["uph"], d["qw"])
+    desc = (f"{SAMPLE_SIDE}x{SAMPLE_SIDE} grid, same r range, {small['pairs_per_cell']} pairs/cell "
+            f"({o.num_particles()} particles), FP64 C oracle, 1 thread")
+    return o, desc
+
+
+def time_oracle(o, nsteps):
+    n0 = o.num_particles()
+    t0 = time.perf_counter()
+    o.step(nsteps)
+    t = time.perf_counter() - t0
+    return 0.5 * (n0 + o.num_particles()) * nsteps, t
+
+
+def cpu_baseline(cfg, budget_s=15.0):
+    o, desc = oracle_sample(cfg)
+    units, t = time_oracle(o, 1)
+    steps = 1
+    while t < budget_s and steps < 50:
+        u, dt = time_oracle(o, 1)
+        units += u
+        t += dt
+        steps += 1
+    return {"value": units / t, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"{desc}, {steps} steps"}
+
+
+def reference_arm(args):
+    """The oracle as the reference arm: W untimed steps, then K timed steps,
+    each a step of the bounded sample, on one host core."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1407_1810_gb300 import configs
+
+    cfg = configs.CONFIGS[args.workload]
+    o, desc = oracle_sample(cfg)
+    if args.warmup:
+        o.step(args.warmup)
+    units, t = time_oracle(o, args.steps)
+    v = units / t
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "path": "oracle"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{desc}, {args.steps} steps"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -148,6 +148,10 @@ int pic_get_flux(pic_ctx *c, double *out3, int64_t *n, int32_t mem);
 int pic_get_particles(pic_ctx *c, int64_t *n, double *x1, double *x2, double *u_r,
                       double *u_th, double *u_ph, double *qw, int64_t *id, int32_t mem);
 
+/* Live particle count and total kinetic energy only (one streaming reduction,
+ * synchronises); cheaper than pic_get_moments, which also deposits the charge. */
+int pic_get_live(pic_ctx *c, int64_t *live, double *kinetic_energy);
+
 /* Diagnostics (synchronises).  The Gauss residual is relative to the snapshot
  * taken by the first pic_step or by pic_gauss_snapshot. */
 int pic_get_moments(pic_ctx *c, pic_moments *out);
@@ -162,6 +166,10 @@ int pic_set_clock(pic_ctx *c, int64_t step, int64_t next_id);
  * injection, sort] into ms6 and the number of timed steps into *steps. */
 int pic_profile(pic_ctx *c, int32_t enable);
 int pic_get_profile(pic_ctx *c, double *ms6, int64_t *steps);
+
+/* Number of kernels this context has launched so far (every launch of the
+ * library's own kernels, all phases); *n receives the count. */
+int pic_get_launches(pic_ctx *c, int64_t *n);
 
 /* Advance n independent contexts by nsteps each, batched: each step launches
  * one kernel per phase for all members (grouped by precision), the whole

@@ -33,6 +33,13 @@ CONFIGS = {
         absorb_cells=32, absorb_profile="linear", vacuum="monopole", omega=0.0, t_spin=0.0, inject=0,
         pusher="vay", precision="fp32", pairs_per_cell=30, T=0.3, seed=0, steps=200, sort_interval=20,
         wc_dt=0.5, wp_dt=0.05),
+    # the large run's plasma on a 1024^2 grid (6.3e7 particles, 2.3 GB of FP32
+    # state): the small case for hardware-counter captures of the same kernel
+    "monopole-1024x1024": dict(
+        nr=1024, nth=1024, r_min=1.0, r_max=100.0, r_map="log", th_map="linear", courant=0.5, n_filt=0,
+        absorb_cells=32, absorb_profile="linear", vacuum="monopole", omega=0.0, t_spin=0.0, inject=0,
+        pusher="vay", precision="fp32", pairs_per_cell=30, T=0.3, seed=0, steps=200, sort_interval=20,
+        wc_dt=0.5, wp_dt=0.05),
 }
 
 
@@ -80,3 +87,20 @@ def oracle_kwargs(cfg: dict, dt: float, b0: float, **over):
               f_inj=cfg.get("f_inj", 0.0), pusher=cfg["pusher"], q_over_m=1.0)
     kw.update(over)
     return kw
+
+
+def courant_dt(cfg: dict) -> float:
+    """dt = courant * min over domain cells of min(dr, r_inner dtheta)."""
+    import numpy as np
+
+    i = np.arange(cfg["nr"] + 1, dtype=np.float64)
+    if cfg["r_map"] == "log":
+        r = cfg["r_min"] * np.exp(i * math.log(cfg["r_max"] / cfg["r_min"]) / cfg["nr"])
+    else:
+        r = cfg["r_min"] + i * (cfg["r_max"] - cfg["r_min"]) / cfg["nr"]
+    j = np.arange(cfg["nth"] + 1, dtype=np.float64)
+    th = np.arccos(1.0 - 2.0 * j / cfg["nth"]) if cfg["th_map"] == "equal_area" else math.pi * j / cfg["nth"]
+    dr = np.diff(r)
+    dth = np.diff(th)
+    m = min(dr.min(), (r[:-1] * dth.min()).min())
+    return cfg["courant"] * float(m)

@@ -332,19 +332,41 @@ int compact(pic_ctx *c) {
   return latch_errors(c);
 }
 
-void prof_mark(pic_ctx *c, int slot, bool end) {
-  if (!c->prof) return;
-  cudaEventRecord(c->ev[2 * slot + (end ? 1 : 0)], c->stream);
+// Profiling records a start/stop event pair per phase per step on the
+// context's stream; the durations are summed when pic_get_profile reads them.
+int prof_begin(pic_ctx *c, int slot) {
+  if (!c->prof) return -1;
+  if (c->ev_used + 2 > c->ev_pool.size()) {
+    for (int k = 0; k < 64; ++k) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      c->ev_pool.push_back(e);
+    }
+    c->ev_slot.resize(c->ev_pool.size() / 2, 0);
+  }
+  const int pair = (int)(c->ev_used / 2);
+  c->ev_slot[pair] = slot;
+  cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
+  c->ev_used += 2;
+  return pair;
 }
 
-void prof_collect(pic_ctx *c, int slot) {
-  if (!c->prof) return;
-  float ms = 0.f;
-  cudaEventSynchronize(c->ev[2 * slot + 1]);
-  if (cudaEventElapsedTime(&ms, c->ev[2 * slot], c->ev[2 * slot + 1]) == cudaSuccess) {
-    c->prof_ms[slot] += ms;
-    c->prof_launch[slot] += 1;
+void prof_end(pic_ctx *c, int pair) {
+  if (pair < 0) return;
+  cudaEventRecord(c->ev_pool[2 * (size_t)pair + 1], c->stream);
+}
+
+void prof_drain(pic_ctx *c) {
+  if (c->ev_used == 0) return;
+  cudaEventSynchronize(c->ev_pool[c->ev_used - 1]);
+  for (size_t p = 0; p < c->ev_used / 2; ++p) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[2 * p], c->ev_pool[2 * p + 1]) == cudaSuccess) {
+      c->prof_ms[c->ev_slot[p]] += ms;
+      c->prof_launch[c->ev_slot[p]] += 1;
+    }
   }
+  c->ev_used = 0;
 }
 
 }  // namespace
@@ -397,6 +419,12 @@ extern "C" int pic_init_grid(pic_ctx **out, const pic_desc *dd, void *stream) {
       if ((e = dalloc(&c->acc[k], ge))) return fail(e);
       cudaMemset(c->acc[k], 0, ge * 8);
     }
+    {
+      std::vector<float> rn(d.nr + 2 * G.PI + 1);
+      for (size_t ii = 0; ii < rn.size(); ++ii) rn[ii] = (float)h_fr(d, G.dxi, (double)ii - G.PI);
+      if ((e = dalloc(&c->r_n32, rn.size()))) return fail(e);
+      PIC_CUDA(cudaMemcpy(c->r_n32, rn.data(), rn.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
     Tiles &T = c->tiles;
     T.row0 = -G.g;
     T.nti = (d.nr + 2 * G.g + T.TI - 1) / T.TI;
@@ -411,7 +439,6 @@ extern "C" int pic_init_grid(pic_ctx **out, const pic_desc *dd, void *stream) {
   cudaMemset(c->d_err, 0, sizeof(int));
   cudaMemset(c->d_cnt, 0, CNT_N * sizeof(long long));
   PIC_CUDA(cudaMallocHost((void **)&c->h_pinned, 64));
-  for (int k = 0; k < 2 * PROF_N; ++k) cudaEventCreate(&c->ev[k]);
   PIC_CUDA(cudaDeviceSynchronize());
   *out = c;
   return PIC_OK;
@@ -450,10 +477,10 @@ extern "C" int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const
     }
     const unsigned blocks = (unsigned)((m + 255) / 256);
     if (c->d.precision == PIC_FP64)
-      k_load64<<<blocks, 256, 0, c->stream>>>(c->G, c->p64, c->n_used + off, m, dv[0], dv[1], dv[2], dv[3], dv[4],
+      ++c->launches, k_load64<<<blocks, 256, 0, c->stream>>>(c->G, c->p64, c->n_used + off, m, dv[0], dv[1], dv[2], dv[3], dv[4],
                                              dv[5], c->next_id + off, c->d_err);
     else
-      k_load32<<<blocks, 256, 0, c->stream>>>(c->G, c->p32, c->n_used + off, m, dv[0], dv[1], dv[2], dv[3], dv[4],
+      ++c->launches, k_load32<<<blocks, 256, 0, c->stream>>>(c->G, c->p32, c->n_used + off, m, dv[0], dv[1], dv[2], dv[3], dv[4],
                                              dv[5], c->next_id + off, c->d_err);
     if (mem != PIC_MEM_DEVICE) PIC_CUDA(cudaStreamSynchronize(c->stream));
   }
@@ -468,13 +495,21 @@ extern "C" int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const
     cudaMemset(c->d_err, 0, sizeof(int));
     return pic_fail(PIC_EINVAL, "particle outside the grid, zero charge or non-finite momentum (dropped)");
   }
-  if (c->d.precision == PIC_FP32) { sort32(c); PIC_CUDA(cudaStreamSynchronize(c->stream)); }
+  if (c->d.precision == PIC_FP32) {
+    c->flux_quantum = 0.0;  // recomputed from the new charges at the next step
+    c->need_sort = true;    // binned by the next step (appended particles are valid unbinned)
+  }
   return PIC_OK;
 }
 
 extern "C" int pic_step(pic_ctx *c, int32_t nsteps) {
   if (!c) return pic_fail(PIC_EINVAL, "null context");
   if (nsteps < 0) return pic_fail(PIC_EINVAL, "nsteps < 0");
+  if (c->need_sort) {
+    int e = compact(c);
+    if (e) return e;
+    c->need_sort = false;
+  }
   if (!c->have_snap) moments(c, true, nullptr);
   const int64_t slots = inject_slots(c);
   for (int s = 0; s < nsteps; ++s) {
@@ -484,46 +519,43 @@ extern "C" int pic_step(pic_ctx *c, int32_t nsteps) {
       if (e) return e;
       if (c->n_used + slots > c->cap && (e = grow_parts(c, (c->n_used + slots) * 3 / 2 + 1024))) return e;
     }
-    prof_mark(c, PROF_PARTICLES, false);
+    int pr = prof_begin(c, PROF_PARTICLES);
     if (c->d.precision == PIC_FP64) {
       for (int k = 0; k < 3; ++k) cudaMemsetAsync(c->F[k], 0, c->grid_elems * 8, c->stream);
       particles64(c, t);
-      prof_mark(c, PROF_PARTICLES, true);
-      prof_mark(c, PROF_REDUCE, false);
-      prof_mark(c, PROF_REDUCE, true);
+      prof_end(c, pr);
     } else {
       particles32(c, t);
-      prof_mark(c, PROF_PARTICLES, true);
-      prof_mark(c, PROF_REDUCE, false);
+      prof_end(c, pr);
+      pr = prof_begin(c, PROF_REDUCE);
       flux_from_acc(c);
-      prof_mark(c, PROF_REDUCE, true);
+      prof_end(c, pr);
     }
-    prof_mark(c, PROF_FILTER, false);
-    fields_filter(c);
-    prof_mark(c, PROF_FILTER, true);
-    prof_mark(c, PROF_FIELDS, false);
+    if (c->d.n_filt > 0) {
+      pr = prof_begin(c, PROF_FILTER);
+      fields_filter(c);
+      prof_end(c, pr);
+    }
+    pr = prof_begin(c, PROF_FIELDS);
     fields_b_half(c);
     fields_e_full(c);
     fields_b_half(c);
     fields_finish(c);
-    prof_mark(c, PROF_FIELDS, true);
+    prof_end(c, pr);
     c->step += 1;
-    prof_mark(c, PROF_INJECT, false);
-    if (c->d.inject) inject(c, c->step * c->G.dt);
-    prof_mark(c, PROF_INJECT, true);
-    prof_mark(c, PROF_SORT, false);
-    bool sorted = false;
+    if (c->d.inject) {
+      pr = prof_begin(c, PROF_INJECT);
+      inject(c, c->step * c->G.dt);
+      prof_end(c, pr);
+    }
     if (++c->steps_since_sort >= c->d.sort_interval) {
+      pr = prof_begin(c, PROF_SORT);
       int e = compact(c);
+      prof_end(c, pr);
       if (e) return e;
-      sorted = true;
     }
-    prof_mark(c, PROF_SORT, true);
-    if (c->prof) {
-      for (int k = 0; k < PROF_N; ++k)
-        if (k != PROF_SORT || sorted) prof_collect(c, k);
-      c->prof_steps += 1;
-    }
+    if (c->prof) c->prof_steps += 1;
+    if (c->ev_used > 4096) prof_drain(c);
   }
   PIC_CUDA(cudaGetLastError());
   return status(c);
@@ -541,7 +573,7 @@ extern "C" int pic_get_fields(pic_ctx *c, int32_t which, double *out6, int64_t *
   dim3 gr((cols + 31) / 32, (rows + 7) / 8);
   for (int k = 0; k < 6; ++k) {
     int imax = stag_i(k) ? c->d.nr - 1 : c->d.nr, jmax = stag_j(k) ? c->d.nth - 1 : c->d.nth;
-    k_pack<<<gr, dim3(32, 8), 0, c->stream>>>(c->G, c->f[k], tmp + k * plane, 0, rows, cols, imax, jmax, 0);
+    ++c->launches, k_pack<<<gr, dim3(32, 8), 0, c->stream>>>(c->G, c->f[k], tmp + k * plane, 0, rows, cols, imax, jmax, 0);
   }
   int e = to_user(c, tmp, out6, 6 * plane, mem);
   cudaFree(tmp);
@@ -561,7 +593,7 @@ extern "C" int pic_set_fields(pic_ctx *c, const double *in6, int32_t mem) {
   dim3 gr((cols + 31) / 32, (rows + 7) / 8);
   for (int k = 0; k < 6; ++k) {
     int imax = stag_i(k) ? c->d.nr - 1 : c->d.nr, jmax = stag_j(k) ? c->d.nth - 1 : c->d.nth;
-    k_pack<<<gr, dim3(32, 8), 0, c->stream>>>(c->G, c->f[k], tmp + k * plane, 0, rows, cols, imax, jmax, 1);
+    ++c->launches, k_pack<<<gr, dim3(32, 8), 0, c->stream>>>(c->G, c->f[k], tmp + k * plane, 0, rows, cols, imax, jmax, 1);
   }
   fields_fill_ghosts(c);
   PIC_CUDA(cudaStreamSynchronize(c->stream));
@@ -580,7 +612,7 @@ extern "C" int pic_get_flux(pic_ctx *c, double *out3, int64_t *n, int32_t mem) {
   PIC_CUDA(cudaMalloc((void **)&tmp, 3 * plane * sizeof(double)));
   dim3 gr((cols + 31) / 32, (rows + 7) / 8);
   for (int k = 0; k < 3; ++k)
-    k_pack<<<gr, dim3(32, 8), 0, c->stream>>>(c->G, c->F[k], tmp + k * plane, -g, rows, cols, c->d.nr + g,
+    ++c->launches, k_pack<<<gr, dim3(32, 8), 0, c->stream>>>(c->G, c->F[k], tmp + k * plane, -g, rows, cols, c->d.nr + g,
                                               k == 1 ? c->d.nth - 1 : c->d.nth, 0);
   int e = to_user(c, tmp, out3, 3 * plane, mem);
   cudaFree(tmp);
@@ -615,7 +647,7 @@ extern "C" int pic_get_particles(pic_ctx *c, int64_t *n, double *x1, double *x2,
     PIC_CUDA(cudaMalloc((void **)&tid, (size_t)live * 8));
     double *t[6];
     for (int k = 0; k < 6; ++k) t[k] = tmp + (size_t)k * live;
-    k_export32<<<(unsigned)((live + 255) / 256), 256, 0, c->stream>>>(c->p32, live, t[0], t[1], t[2], t[3], t[4],
+    ++c->launches, k_export32<<<(unsigned)((live + 255) / 256), 256, 0, c->stream>>>(c->p32, live, t[0], t[1], t[2], t[3], t[4],
                                                                       t[5], tid);
     double *o[6] = {x1, x2, u_r, u_th, u_ph, qw};
     for (int k = 0; k < 6; ++k) PIC_CUDA(cudaMemcpyAsync(o[k], t[k], (size_t)live * 8, kind, c->stream));
@@ -636,6 +668,23 @@ extern "C" int pic_get_moments(pic_ctx *c, pic_moments *out) {
   return status(c);
 }
 
+extern "C" int pic_get_live(pic_ctx *c, int64_t *live, double *kinetic_energy) {
+  if (!c || !live) return pic_fail(PIC_EINVAL, "null argument");
+  cudaMemsetAsync(c->d_acc, 0, ACC_N * sizeof(double), c->stream);
+  cudaMemsetAsync(c->d_cnt + CNT_LIVE, 0, sizeof(long long), c->stream);
+  if (c->d.precision == PIC_FP32) reduce_particles32(c);
+  else reduce_particles64(c);
+  long long n = 0;
+  double acc[ACC_N];
+  PIC_CUDA(cudaMemcpyAsync(&n, c->d_cnt + CNT_LIVE, sizeof n, cudaMemcpyDeviceToHost, c->stream));
+  PIC_CUDA(cudaMemcpyAsync(acc, c->d_acc, sizeof acc, cudaMemcpyDeviceToHost, c->stream));
+  PIC_CUDA(cudaStreamSynchronize(c->stream));
+  *live = n;
+  if (kinetic_energy) *kinetic_energy = acc[ACC_KIN];
+  latch_errors(c);
+  return status(c);
+}
+
 extern "C" int pic_gauss_snapshot(pic_ctx *c) {
   if (!c) return pic_fail(PIC_EINVAL, "null context");
   moments(c, true, nullptr);
@@ -652,6 +701,7 @@ extern "C" int pic_set_clock(pic_ctx *c, int64_t step, int64_t next_id) {
 
 extern "C" int pic_profile(pic_ctx *c, int32_t enable) {
   if (!c) return pic_fail(PIC_EINVAL, "null context");
+  prof_drain(c);
   c->prof = enable != 0;
   for (int k = 0; k < PROF_N; ++k) { c->prof_ms[k] = 0; c->prof_launch[k] = 0; }
   c->prof_steps = 0;
@@ -660,8 +710,15 @@ extern "C" int pic_profile(pic_ctx *c, int32_t enable) {
 
 extern "C" int pic_get_profile(pic_ctx *c, double *ms6, int64_t *steps) {
   if (!c || !ms6) return pic_fail(PIC_EINVAL, "null argument");
+  prof_drain(c);
   for (int k = 0; k < PROF_N; ++k) ms6[k] = c->prof_launch[k] ? c->prof_ms[k] / c->prof_launch[k] : 0.0;
   if (steps) *steps = c->prof_steps;
+  return PIC_OK;
+}
+
+extern "C" int pic_get_launches(pic_ctx *c, int64_t *n) {
+  if (!c || !n) return pic_fail(PIC_EINVAL, "null argument");
+  *n = c->launches;
   return PIC_OK;
 }
 
@@ -681,13 +738,13 @@ extern "C" int pic_destroy(pic_ctx *c) {
   free_parts(c);
   cudaFree(c->metric_buf);
   for (int k = 0; k < 6; ++k) { cudaFree(c->f[k]); cudaFree(c->f32[k]); }
+  cudaFree(c->r_n32);
   for (int k = 0; k < 3; ++k) { cudaFree(c->F[k]); cudaFree(c->Ft[k]); cudaFree(c->acc[k]); }
   cudaFree(c->Q); cudaFree(c->Qa); cudaFree(c->Qt); cudaFree(c->gsnap); cudaFree(c->sig);
   cudaFree(c->d_err); cudaFree(c->d_cnt); cudaFree(c->d_acc);
   cudaFree(c->tiles.start); cudaFree(c->tiles.cursor);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
-  for (int k = 0; k < 2 * PROF_N; ++k)
-    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
   return PIC_OK;
 }

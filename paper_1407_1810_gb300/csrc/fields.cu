@@ -251,21 +251,21 @@ __global__ void k_field_energy(Grid G, const double *f0, const double *f1, const
 
 void fields_b_half(pic_ctx *c) {
   const Grid &G = c->G;
-  k_b_half<<<grid2(G.nr + 1, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(G, c->f[ER], c->f[ETH], c->f[EPH], c->f[BR],
+  ++c->launches, k_b_half<<<grid2(G.nr + 1, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(G, c->f[ER], c->f[ETH], c->f[EPH], c->f[BR],
                                                                       c->f[BTH], c->f[BPH], 0.5 * G.dt);
 }
 
 void fields_e_full(pic_ctx *c) {
   const Grid &G = c->G;
-  k_e_full<<<grid2(G.nr + 1, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(
+  ++c->launches, k_e_full<<<grid2(G.nr + 1, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(
       G, c->f[ER], c->f[ETH], c->f[EPH], c->f[BR], c->f[BTH], c->f[BPH], c->F[0], c->F[1], c->F[2], G.dt);
 }
 
 void fields_fill_ghosts(pic_ctx *c) {
   const Grid &G = c->G;
-  k_axis_ghosts<<<(G.nr + 1 + 127) / 128, 128, 0, c->stream>>>(G, c->f[ETH], c->f[BR], c->f[BPH]);
+  ++c->launches, k_axis_ghosts<<<(G.nr + 1 + 127) / 128, 128, 0, c->stream>>>(G, c->f[ETH], c->f[BR], c->f[BPH]);
   if (c->d.precision == PIC_FP32) {
-    k_copy32<<<4 * 152, 256, 0, c->stream>>>(c->grid_elems, c->f[0], c->f[1], c->f[2], c->f[3], c->f[4], c->f[5],
+    ++c->launches, k_copy32<<<4 * 152, 256, 0, c->stream>>>(c->grid_elems, c->f[0], c->f[1], c->f[2], c->f[3], c->f[4], c->f[5],
                                             c->f32[0], c->f32[1], c->f32[2], c->f32[3], c->f32[4], c->f32[5]);
   }
 }
@@ -275,7 +275,7 @@ void fields_finish(pic_ctx *c) {
   if (c->d.absorb_profile != PIC_ABSORB_NONE && c->d.absorb_cells > 0) {
     int i0 = G.nr - G.absorb_cells - 1;
     if (i0 < 0) i0 = 0;
-    k_lossy<<<grid2(G.nr + 1 - i0, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(G, c->f[0], c->f[1], c->f[2], c->f[3],
+    ++c->launches, k_lossy<<<grid2(G.nr + 1 - i0, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(G, c->f[0], c->f[1], c->f[2], c->f[3],
                                                                            c->f[4], c->f[5], i0);
   }
   fields_fill_ghosts(c);
@@ -287,7 +287,7 @@ void filter_array(pic_ctx *c, double *a, double *tmp, int half_j, int sign, int 
   dim3 gr = grid2(G.nr + 2 * G.g + 1, G.nth + 1);
   double *src = a, *dst = tmp;
   for (int p = 0; p < passes; ++p) {
-    k_filter<<<gr, dim3(BX, BY), 0, c->stream>>>(G, src, dst, half_j);
+    ++c->launches, k_filter<<<gr, dim3(BX, BY), 0, c->stream>>>(G, src, dst, half_j);
     double *t = src; src = dst; dst = t;
   }
   if (src != a)
@@ -301,7 +301,7 @@ void fields_filter(pic_ctx *c) {
   dim3 gr = grid2(G.nr + 2 * G.g + 1, G.nth + 1);
   for (int p = 0; p < n; ++p) {
     for (int k = 0; k < 3; ++k)
-      k_filter<<<gr, dim3(BX, BY), 0, c->stream>>>(G, c->F[k], c->Ft[k], k == 1);
+      ++c->launches, k_filter<<<gr, dim3(BX, BY), 0, c->stream>>>(G, c->F[k], c->Ft[k], k == 1);
     for (int k = 0; k < 3; ++k) { double *t = c->F[k]; c->F[k] = c->Ft[k]; c->Ft[k] = t; }
   }
 }
@@ -311,14 +311,14 @@ void inject(pic_ctx *c, double t) {
   const int npp = c->d.pairs_per_cell;
   long long *smax = c->d_cnt + CNT_SMAX;
   cudaMemsetAsync(smax, 0, sizeof(long long), c->stream);
-  k_inject_sigma<<<(G.nth + 127) / 128, 128, 0, c->stream>>>(G, c->f[ER], t, c->sig, smax);
+  ++c->launches, k_inject_sigma<<<(G.nth + 127) / 128, 128, 0, c->stream>>>(G, c->f[ER], t, c->sig, smax);
   const int64_t nslots = (int64_t)G.nth * npp * 2;
   const int blocks = (int)((nslots + 255) / 256);
   if (c->d.precision == PIC_FP32)
-    k_inject_write<true><<<blocks, 256, 0, c->stream>>>(G, c->sig, smax, c->p64, c->p32, c->n_used, c->next_id, npp,
+    ++c->launches, k_inject_write<true><<<blocks, 256, 0, c->stream>>>(G, c->sig, smax, c->p64, c->p32, c->n_used, c->next_id, npp,
                                                         c->d.f_inj, c->d_cnt + CNT_INJECTED);
   else
-    k_inject_write<false><<<blocks, 256, 0, c->stream>>>(G, c->sig, smax, c->p64, c->p32, c->n_used, c->next_id, npp,
+    ++c->launches, k_inject_write<false><<<blocks, 256, 0, c->stream>>>(G, c->sig, smax, c->p64, c->p32, c->n_used, c->next_id, npp,
                                                          c->d.f_inj, c->d_cnt + CNT_INJECTED);
   c->n_used += nslots;
   c->next_id += nslots;
@@ -335,13 +335,13 @@ void moments(pic_ctx *c, bool snapshot, pic_moments *out) {
   int imax = G.nr - L - 1;
   cudaMemsetAsync(c->d_cnt + CNT_GMAX, 0, 2 * sizeof(long long), c->stream);
   if (imax >= 1)
-    k_gauss<<<grid2(imax, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(G, c->f[ER], c->f[ETH], c->Q, c->Qa, c->gsnap,
+    ++c->launches, k_gauss<<<grid2(imax, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(G, c->f[ER], c->f[ETH], c->Q, c->Qa, c->gsnap,
                                                                     imax, snapshot ? 1 : 0, c->d_cnt + CNT_GMAX,
                                                                     c->d_cnt + CNT_QMAX);
   if (snapshot) { c->have_snap = true; return; }
   cudaMemsetAsync(c->d_acc, 0, ACC_N * sizeof(double), c->stream);
   cudaMemsetAsync(c->d_cnt + CNT_LIVE, 0, sizeof(long long), c->stream);
-  k_field_energy<<<grid2(G.nr + 1, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(
+  ++c->launches, k_field_energy<<<grid2(G.nr + 1, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(
       G, c->f[0], c->f[1], c->f[2], c->f[3], c->f[4], c->f[5], c->d_acc + ACC_FIELD);
   if (c->d.precision == PIC_FP32) reduce_particles32(c);
   else reduce_particles64(c);

@@ -1,11 +1,513 @@
-// particles32.cu -- FP32 cell+offset particle path (placeholder until the
-// tiled kernel lands).
+// particles32.cu -- the FP32 cell+offset particle path (the hot path):
+//
+//  * particles are kept binned by tiles of TI x TJ cells (counting sort by tile,
+//    every sort_interval steps; deleted particles are dropped by the sort);
+//  * one CTA per tile stages a window of the FP32 field copies (tile + halo H
+//    + the stencil) in shared memory, gathers, pushes and moves every particle
+//    of its bin, and deposits the Villasenor-Buneman fluxes into shared-memory
+//    int64 fixed-point accumulators (exact and order independent), flushed
+//    with one global atomic per nonzero window node;
+//  * a particle that drifted out of its tile's window since the last sort, or
+//    was injected after it, takes the same code with global-memory accessors.
+//
+// Position = integer cell + FP32 offset in [0, 1).  The move runs in the
+// particle's local frame: the radial increment comes from log1p of the
+// relative displacement, the meridional one from the exact rotation angle of
+// the displaced point, so an offset keeps ~1e-7 cell accuracy anywhere on the
+// grid instead of the ~1e-4 cell an absolute FP32 r or theta would give.
+#include <cmath>
+#include <cstring>
+
 #include "pic_internal.h"
 
 namespace pic {
-void particles32(pic_ctx *c, double) { (void)c; }
-void flux_from_acc(pic_ctx *c) { (void)c; }
-int64_t sort32(pic_ctx *c) { return c->n_used; }
-void charge32(pic_ctx *c, double *, double *) { (void)c; }
-void reduce_particles32(pic_ctx *c) { (void)c; }
+
+namespace {
+
+constexpr int TI = 16, TJ = 16, H = 2;
+constexpr int WI = TI + 2 * H + 3, WJ = TJ + 2 * H + 3;  // window nodes
+constexpr int WN = WI * WJ;
+constexpr int NT = 256;                                  // threads per tile CTA
+constexpr int KFIX = 40;                                 // fixed point: 2^-40 of the reference charge
+
+struct Args32 {
+  int nr, nth, n_filt, PI, PJ, LD;
+  int r_log, th_ea, vacuum, pusher;
+  float dxi, inv_dxi, dt, qm, inv_nth, nth_f;
+  float fscale;             // 2^KFIX / qref: float contribution -> int64 units
+  const float *r_n;         // f_r(i) per padded row (FP32)
+  const float *f[6];        // FP32 field copies (padded)
+  long long *acc[3];        // global fixed-point flux accumulators (padded)
+  int *err;
+  long long *cnt;
+  // tiles
+  int row0, ntj, ntiles;
+  const int64_t *start;
+  int64_t sorted_end, n_used;
+  // vacuum
+  float b0, r_min, omega_t;
+};
+
+__device__ inline size_t pidx(const Args32 &A, int i, int j) {
+  return (size_t)(i + A.PI) * (size_t)A.LD + (size_t)(j + A.PJ);
+}
+
+struct SmemAcc {  // window accessors (shared memory)
+  const float *f;           // 6 * WN
+  unsigned long long *F;    // 3 * WN
+  int wi0, wj0;
+  __device__ float fld(int c, int i, int j) const { return f[c * WN + (i - wi0) * WJ + (j - wj0)]; }
+  __device__ void add(int k, int i, int j, long long v) const {
+    if (v) atomicAdd(&F[k * WN + (i - wi0) * WJ + (j - wj0)], (unsigned long long)v);
+  }
+};
+
+struct GlobAcc {  // global-memory accessors (particles outside the window)
+  const Args32 *A;
+  __device__ float fld(int c, int i, int j) const { return A->f[c][pidx(*A, i, j)]; }
+  __device__ void add(int k, int i, int j, long long v) const {
+    if (v) atomicAdd(reinterpret_cast<unsigned long long *>(A->acc[k] + pidx(*A, i, j)), (unsigned long long)v);
+  }
+};
+
+template <class W>
+__device__ inline float bilin(const W &w, int c, int i, int j, float a, float b) {
+  return (1.f - a) * (1.f - b) * w.fld(c, i, j) + a * (1.f - b) * w.fld(c, i + 1, j) +
+         (1.f - a) * b * w.fld(c, i, j + 1) + a * b * w.fld(c, i + 1, j + 1);
+}
+
+// Villasenor-Buneman fluxes of a straight path p -> q inside cell (i, j),
+// local coordinates in [0, 1] (Eq. Jcons, Sec. 3.3)
+template <class W>
+__device__ inline void vb_seg(const W &w, float scale, int i, int j, float p1, float p2, float q1, float q2) {
+  const float d1 = q1 - p1, d2 = q2 - p2, m1 = 0.5f * (p1 + q1), m2 = 0.5f * (p2 + q2);
+  const float a = scale * d1, b = scale * d2;
+  const long long fr1 = __float2ll_rn(a * m2), fr0 = __float2ll_rn(a * (1.f - m2));
+  const long long ft1 = __float2ll_rn(b * m1), ft0 = __float2ll_rn(b * (1.f - m1));
+  w.add(0, i, j, fr0);
+  w.add(0, i, j + 1, fr1);
+  w.add(1, i, j, ft0);
+  w.add(1, i + 1, j, ft1);
+}
+
+__device__ inline float clamp01(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
+
+// One particle step.  Returns false when the particle is removed.
+template <class W>
+__device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float &dx, float &dy, float &ur, float &ut,
+                              float &up, const float qw) {
+  const int ci = (int)(cell >> 16) - CELL_BIAS, cj = (int)(cell & 0xffffu);
+  // ---- geometry of the particle's position (Sec. 3.2) -----------------------
+  const float rn = A.r_n[ci + A.PI];
+  const float r = A.r_log ? rn * expf(dx * A.dxi) : rn + dx * A.dxi;
+  const float x2 = (float)cj + dy;
+  float st, ct;
+  if (A.th_ea) {  // cos th = 1 - 2 x2/nth, sin th = 2 sqrt(x2 (nth - x2))/nth
+    const float rest = (float)(A.nth - cj) - dy;
+    ct = ((float)(A.nth - cj) - (float)cj - 2.f * dy) * A.inv_nth;
+    st = 2.f * sqrtf(fmaxf(x2 * rest, 0.f)) * A.inv_nth;
+  } else {
+    sincospif(x2 * A.inv_nth, &st, &ct);
+  }
+  // ---- gather + push (ballistic inside the outer conductor) -----------------
+  if (ci < A.nr) {
+    float E[3], B[3];
+    {
+      Grid Gv;  // only the vacuum-field members are read
+      Gv.vacuum = A.vacuum; Gv.b0 = A.b0; Gv.r_min = A.r_min; Gv.omega = A.omega_t; Gv.t_spin = 0.0;
+      vacuum_field<float>(Gv, r, st, ct, 0.0, ci < 0, E, B);
+    }
+    if (ci >= 0) {  // plasma field only outside the inner conductor
+      const bool hx = dx >= 0.5f, hy = dy >= 0.5f;
+      const int ih = hx ? ci : ci - 1, jh = hy ? cj : cj - 1;
+      const float ah = hx ? dx - 0.5f : dx + 0.5f, bh = hy ? dy - 0.5f : dy + 0.5f;
+      E[0] += bilin(w, ER, ih, cj, ah, dy);
+      E[1] += bilin(w, ETH, ci, jh, dx, bh);
+      E[2] += bilin(w, EPH, ci, cj, dx, dy);
+      B[0] += bilin(w, BR, ci, jh, dx, bh);
+      B[1] += bilin(w, BTH, ih, cj, ah, dy);
+      B[2] += bilin(w, BPH, ih, jh, ah, bh);
+    }
+    float u[3] = {ur, ut, up};
+    // local (r, th, ph) is a right-handed orthonormal frame: the Cartesian
+    // push formulas apply to its components unchanged
+    push<float>(A.pusher, qw > 0.f ? A.qm * A.dt : -A.qm * A.dt, E, B, u);
+    ur = u[0]; ut = u[1]; up = u[2];
+  }
+  // ---- move in the local frame (Sec. 3.3) -----------------------------------
+  const float ig = 1.f / sqrtf(1.f + ur * ur + ut * ut + up * up);
+  const float Dr = ur * ig * A.dt, Dt = ut * ig * A.dt, Dp = up * ig * A.dt;
+  const float ir = 1.f / r;
+  const float a = Dr * ir, b = Dt * ir, c = Dp * ir;
+  const float s = a * (2.f + a) + b * b + c * c;  // (r'/r)^2 - 1
+  const float D1 = A.r_log ? 0.5f * log1pf(s) * A.inv_dxi : r * s / (1.f + sqrtf(1.f + s)) * A.inv_dxi;
+  const float p = r + Dr, q = Dt;
+  const float Px = p * st + q * ct, Pz = p * ct - q * st;  // displaced point, (R, z) before rotating back
+  const float Rn = sqrtf(Px * Px + Dp * Dp);
+  const float kap = Px >= 0.f ? (Rn + Px > 0.f ? Dp * Dp / (Rn + Px) : 0.f) : Rn - Px;  // R' - Px
+  const float dth = atan2f(q + ct * kap, p + st * kap);                                 // theta' - theta
+  float D2;
+  if (A.th_ea) {
+    float sh, ch;
+    sincosf(0.5f * dth, &sh, &ch);
+    D2 = A.nth_f * (st * ch + ct * sh) * sh;
+  } else {
+    D2 = dth * A.nth_f * 0.31830988618379067f;
+  }
+  // new cell and offsets (carries are exact integers)
+  float tx = dx + D1, ty = dy + D2;
+  int kx = (int)floorf(tx), ky = (int)floorf(ty);
+  float nx = tx - (float)kx, ny = ty - (float)ky;
+  if (nx >= 1.f) { nx = 0.f; ++kx; }
+  if (ny >= 1.f) { ny = 0.f; ++ky; }
+  int ncj = cj + ky;
+  if (ncj < 0) { ncj = 0; ky = -cj; ny = 0.f; }                       // rounding below the axis
+  if (ncj > A.nth - 1) { ncj = A.nth - 1; ky = ncj - cj; ny = 1.f; }   // rounding past the south axis
+  // momentum: to Cartesian at phi = 0, rotate back by -phi', to the new frame
+  const float ux = ur * st + ut * ct, uz = ur * ct - ut * st;
+  const float cph = Rn > 0.f ? Px / Rn : 1.f, sph = Rn > 0.f ? Dp / Rn : 0.f;
+  const float uxx = cph * ux + sph * up, uyy = -sph * ux + cph * up;
+  const float irn = rsqrtf(fmaxf(Rn * Rn + Pz * Pz, 1e-30f));
+  const float stn = Rn * irn, ctn = Pz * irn;
+  const float nur = uxx * stn + uz * ctn, nut = uxx * ctn - uz * stn, nup = uyy;
+  if (!(isfinite(nx) && isfinite(ny) && isfinite(nur) && isfinite(nut) && isfinite(nup)) || kx < -1 || kx > 1 ||
+      ky < -1 || ky > 1) {
+    atomicOr(A.err, (isfinite(nx) && isfinite(nur)) ? ERR_COURANT : ERR_NAN);
+    return false;
+  }
+  // ---- Villasenor-Buneman deposit along the grid-coordinate path -----------
+  const float scale = qw * A.fscale;
+  const float Dxs = kx == 0 ? nx - dx : (kx > 0 ? (1.f - dx) + nx : -(dx + (1.f - nx)));
+  const float Dys = ky == 0 ? ny - dy : (ky > 0 ? (1.f - dy) + ny : -(dy + (1.f - ny)));
+  const float sx = kx > 0 ? (1.f - dx) / Dxs : (kx < 0 ? -dx / Dxs : 2.f);
+  const float sy = ky > 0 ? (1.f - dy) / Dys : (ky < 0 ? -dy / Dys : 2.f);
+  const float Xo = kx > 0 ? 1.f : 0.f, Xn = 1.f - Xo;  // boundary in old / new x frame
+  const float Yo = ky > 0 ? 1.f : 0.f, Yn = 1.f - Yo;
+  if (kx == 0 && ky == 0) {
+    vb_seg(w, scale, ci, cj, dx, dy, nx, ny);
+  } else if (ky == 0) {
+    const float yc = clamp01(dy + sx * Dys);
+    vb_seg(w, scale, ci, cj, dx, dy, Xo, yc);
+    vb_seg(w, scale, ci + kx, cj, Xn, yc, nx, ny);
+  } else if (kx == 0) {
+    const float xc = clamp01(dx + sy * Dxs);
+    vb_seg(w, scale, ci, cj, dx, dy, xc, Yo);
+    vb_seg(w, scale, ci, cj + ky, xc, Yn, nx, ny);
+  } else if (sx <= sy) {
+    const float y1 = clamp01(dy + sx * Dys);           // old y frame
+    const float x2c = clamp01(nx - (1.f - sy) * Dxs);  // new x frame
+    vb_seg(w, scale, ci, cj, dx, dy, Xo, y1);
+    vb_seg(w, scale, ci + kx, cj, Xn, y1, x2c, Yo);
+    vb_seg(w, scale, ci + kx, cj + ky, x2c, Yn, nx, ny);
+  } else {
+    const float x1c = clamp01(dx + sy * Dxs);          // old x frame
+    const float y2c = clamp01(ny - (1.f - sx) * Dys);  // new y frame
+    vb_seg(w, scale, ci, cj, dx, dy, x1c, Yo);
+    vb_seg(w, scale, ci, cj + ky, x1c, Yn, Xo, y2c);
+    vb_seg(w, scale, ci + kx, cj + ky, Xn, y2c, nx, ny);
+  }
+  // azimuthal flux: charge crossing the meridional half-plane, qw dphi / 2 pi,
+  // area weights at the midpoint of the grid path
+  {
+    const float phi = atan2f(Dp, Px);
+    const float v = scale * phi * 0.15915494309189535f;
+    const float mx = 0.5f * (dx + (float)kx + nx), my = 0.5f * (dy + (float)ky + ny);
+    const float fx = floorf(mx), fy = floorf(my);
+    const float wx = mx - fx, wy = my - fy;
+    const int i0 = ci + (int)fx, j0 = cj + (int)fy;
+    w.add(2, i0, j0, __float2ll_rn(v * (1.f - wx) * (1.f - wy)));
+    w.add(2, i0 + 1, j0, __float2ll_rn(v * wx * (1.f - wy)));
+    w.add(2, i0, j0 + 1, __float2ll_rn(v * (1.f - wx) * wy));
+    w.add(2, i0 + 1, j0 + 1, __float2ll_rn(v * wx * wy));
+  }
+  // ---- store; removal once the filtered shape is inside a conductor ---------
+  const int nci = ci + kx;
+  if (nci < -(A.n_filt + 1) || nci >= A.nr + A.n_filt + 1) return false;
+  cell = ((uint32_t)(nci + CELL_BIAS) << 16) | (uint32_t)ncj;
+  dx = nx; dy = ny; ur = nur; ut = nut; up = nup;
+  return true;
+}
+
+__device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, const SmemAcc &sw,
+                               const GlobAcc &gw, int wi_lo, int wi_hi, int wj_lo, int wj_hi, int &dead) {
+  const float qw = P.qw[k];
+  if (qw == 0.f) return;
+  uint32_t cell = P.cell[k];
+  float dx = P.dx[k], dy = P.dy[k], ur = P.ur[k], ut = P.ut[k], up = P.up[k];
+  const int ci = (int)(cell >> 16) - CELL_BIAS, cj = (int)(cell & 0xffffu);
+  bool alive;
+  if (win && ci >= wi_lo && ci < wi_hi && cj >= wj_lo && cj < wj_hi) alive = step32(A, sw, cell, dx, dy, ur, ut, up, qw);
+  else alive = step32(A, gw, cell, dx, dy, ur, ut, up, qw);
+  if (!alive) { P.qw[k] = 0.f; ++dead; return; }
+  P.cell[k] = cell;
+  P.dx[k] = dx; P.dy[k] = dy;
+  P.ur[k] = ur; P.ut[k] = ut; P.up[k] = up;
+}
+
+__global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
+  __shared__ float sf[6 * WN];
+  __shared__ unsigned long long sF[3 * WN];
+  __shared__ int sdead;
+  const GlobAcc gw{&A};
+  int dead = 0;
+  if (blockIdx.x < (unsigned)A.ntiles) {
+    const int t = blockIdx.x;
+    const int64_t b0 = A.start[t], b1 = A.start[t + 1];
+    if (b1 <= b0) return;
+    const int i0 = A.row0 + (t / A.ntj) * TI, j0 = (t % A.ntj) * TJ;
+    const int wi0 = i0 - H - 1, wj0 = j0 - H - 1;
+    if (threadIdx.x == 0) sdead = 0;
+    for (int e = threadIdx.x; e < WN; e += NT) {
+      const size_t o = pidx(A, wi0 + e / WJ, wj0 + e % WJ);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) sf[c * WN + e] = A.f[c][o];
+      sF[e] = 0ull; sF[WN + e] = 0ull; sF[2 * WN + e] = 0ull;
+    }
+    __syncthreads();
+    const SmemAcc sw{sf, sF, wi0, wj0};
+    for (int64_t k = b0 + threadIdx.x; k < b1; k += NT)
+      process(A, P, k, true, sw, gw, i0 - H, i0 + TI + H, j0 - H, j0 + TJ + H, dead);
+    if (dead) atomicAdd(&sdead, dead);
+    __syncthreads();
+    for (int e = threadIdx.x; e < WN; e += NT) {
+      const size_t o = pidx(A, wi0 + e / WJ, wj0 + e % WJ);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const unsigned long long v = sF[c * WN + e];
+        if (v) atomicAdd(reinterpret_cast<unsigned long long *>(A.acc[c] + o), v);
+      }
+    }
+    if (threadIdx.x == 0 && sdead) add_ll(A.cnt + CNT_DELETED, sdead);
+  } else {  // particles outside any bin (injected since the last sort)
+    const SmemAcc none{nullptr, nullptr, 0, 0};
+    const int64_t k = A.sorted_end + (int64_t)(blockIdx.x - A.ntiles) * NT + threadIdx.x;
+    if (k < A.n_used) process(A, P, k, false, none, gw, 0, 0, 0, 0, dead);
+    if (dead) add_ll(A.cnt + CNT_DELETED, dead);
+  }
+}
+
+// fixed point -> FP64 fluxes over the ghost band; clears the accumulators
+__global__ void k_flux_from_acc(int nr, int nth, int g, int PI, int PJ, int LD, double q0, long long *a0,
+                                long long *a1, long long *a2, double *F0, double *F1, double *F2) {
+  const int j = blockIdx.x * 32 + threadIdx.x, i = -g + (int)(blockIdx.y * 8 + threadIdx.y);
+  if (i > nr + g || j > nth) return;
+  const size_t o = (size_t)(i + PI) * LD + (size_t)(j + PJ);
+  F0[o] = (double)a0[o] * q0; a0[o] = 0;
+  F1[o] = (double)a1[o] * q0; a1[o] = 0;
+  F2[o] = (double)a2[o] * q0; a2[o] = 0;
+}
+
+// ---- tile counting sort (drops deleted particles) --------------------------
+__device__ inline int tile_key(const Args32 &A, uint32_t cell, float qw) {
+  if (qw == 0.f) return A.ntiles;  // trash bin
+  const int ci = (int)(cell >> 16) - CELL_BIAS, cj = (int)(cell & 0xffffu);
+  return ((ci - A.row0) / TI) * A.ntj + cj / TJ;
+}
+
+__global__ void k_hist(Args32 A, Parts32 P, int64_t n, int64_t *count) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int key = k < n ? tile_key(A, P.cell[k], P.qw[k]) : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  if (key >= 0 && lane == __ffs(peers) - 1)
+    atomicAdd(reinterpret_cast<unsigned long long *>(count + key), (unsigned long long)__popc(peers));
+}
+
+__global__ void k_scan_bins(int64_t *count, int64_t *start, int nb) {
+  // exclusive scan of nb = ntiles + 1 bin counts by one block; count becomes the cursor
+  __shared__ int64_t part[1024];
+  const int t = threadIdx.x;
+  const int per = (nb + 1023) / 1024, a = t * per, b = min(nb, a + per);
+  int64_t s = 0;
+  for (int k = a; k < b; ++k) s += count[k];
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    int64_t v = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int64_t run = part[t] - s;
+  for (int k = a; k < b; ++k) {
+    const int64_t c = count[k];
+    start[k] = run;
+    count[k] = run;
+    run += c;
+  }
+  if (t == 1023) start[nb] = part[1023];
+}
+
+__global__ void k_scatter_tiles(Args32 A, Parts32 S, Parts32 D, int64_t n, int64_t *cursor) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int key = k < n ? tile_key(A, S.cell[k], S.qw[k]) : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+  unsigned long long base = 0;
+  if (key >= 0 && key < A.ntiles && lane == leader)
+    base = atomicAdd(reinterpret_cast<unsigned long long *>(cursor + key), (unsigned long long)__popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (key < 0 || key >= A.ntiles) return;
+  const int64_t d = (int64_t)base + __popc(peers & ((1u << lane) - 1u));
+  D.cell[d] = S.cell[k]; D.dx[d] = S.dx[k]; D.dy[d] = S.dy[k];
+  D.ur[d] = S.ur[k]; D.ut[d] = S.ut[k]; D.up[d] = S.up[k];
+  D.qw[d] = S.qw[k]; D.id[d] = S.id[k];
+}
+
+__global__ void k_charge32(int PI, int PJ, int LD, Parts32 P, int64_t n, double *Q, double *Qa) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double q = P.qw[k];
+  if (q == 0.0) return;
+  const uint32_t c = P.cell[k];
+  const int ci = (int)(c >> 16) - CELL_BIAS, cj = (int)(c & 0xffffu);
+  const double w1 = P.dx[k], w2 = P.dy[k];
+  const size_t o = (size_t)(ci + PI) * LD + (size_t)(cj + PJ);
+  const double c00 = (1 - w1) * (1 - w2), c10 = w1 * (1 - w2), c01 = (1 - w1) * w2, c11 = w1 * w2;
+  atomicAdd(Q + o, q * c00); atomicAdd(Q + o + LD, q * c10);
+  atomicAdd(Q + o + 1, q * c01); atomicAdd(Q + o + LD + 1, q * c11);
+  const double aq = fabs(q);
+  atomicAdd(Qa + o, aq * c00); atomicAdd(Qa + o + LD, aq * c10);
+  atomicAdd(Qa + o + 1, aq * c01); atomicAdd(Qa + o + LD + 1, aq * c11);
+}
+
+__global__ void k_reduce32(Parts32 P, int64_t n, double qm, double *acc, long long *live) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double kin = 0.0, ch = 0.0;
+  int l = 0;
+  if (k < n && P.qw[k] != 0.f) {
+    const double q = P.qw[k], a = P.ur[k], b = P.ut[k], c = P.up[k];
+    kin = fabs(q) / qm * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
+    ch = q;
+    l = 1;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    kin += __shfl_xor_sync(0xffffffffu, kin, o);
+    ch += __shfl_xor_sync(0xffffffffu, ch, o);
+    l += __shfl_xor_sync(0xffffffffu, l, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc + ACC_KIN, kin);
+    atomicAdd(acc + ACC_CHARGE, ch);
+    add_ll(live, (long long)l);
+  }
+}
+
+__global__ void k_max_abs_qw(const float *qw, int64_t n, unsigned *out) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float v = k < n ? fabsf(qw[k]) : 0.f;
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(v));
+}
+
+Args32 make_args(pic_ctx *c, double t) {
+  const Grid &G = c->G;
+  Args32 A;
+  A.nr = G.nr; A.nth = G.nth; A.n_filt = G.n_filt; A.PI = G.PI; A.PJ = G.PJ; A.LD = G.LD;
+  A.r_log = G.r_map == PIC_R_LOG; A.th_ea = G.th_map == PIC_TH_EQUAL_AREA;
+  A.vacuum = G.vacuum; A.pusher = G.pusher;
+  A.dxi = (float)G.dxi; A.inv_dxi = (float)(1.0 / G.dxi); A.dt = (float)G.dt; A.qm = (float)G.qm;
+  A.inv_nth = (float)(1.0 / G.nth); A.nth_f = (float)G.nth;
+  A.fscale = (float)(1.0 / c->flux_quantum);  // a power of two: the scaling is exact
+  A.r_n = c->r_n32;
+  for (int k = 0; k < 6; ++k) A.f[k] = c->f32[k];
+  for (int k = 0; k < 3; ++k) A.acc[k] = c->acc[k];
+  A.err = c->d_err;
+  A.cnt = c->d_cnt;
+  A.row0 = c->tiles.row0; A.ntj = c->tiles.ntj; A.ntiles = c->tiles.ntiles;
+  A.start = c->tiles.start;
+  A.sorted_end = c->tiles.sorted_end;
+  A.n_used = c->n_used;
+  A.b0 = (float)G.b0; A.r_min = (float)G.r_min;
+  double W = G.omega;
+  if (G.t_spin > 0.0 && t < G.t_spin) W = G.omega * (t / G.t_spin);
+  A.omega_t = (float)W;
+  return A;
+}
+
+}  // namespace
+
+// fixed-point quantum: 2^-KFIX of the smallest power of two above the largest
+// charge a particle can carry (loaded charges, and for surface injection 16x
+// the vacuum surface charge of one cell)
+static void update_quantum(pic_ctx *c) {
+  double qref = 0.0;
+  if (c->n_used > 0) {
+    unsigned *d;
+    cudaMalloc(&d, sizeof(unsigned));
+    cudaMemsetAsync(d, 0, sizeof(unsigned), c->stream);
+    ++c->launches, k_max_abs_qw<<<(unsigned)((c->n_used + 255) / 256), 256, 0, c->stream>>>(c->p32.qw, c->n_used, d);
+    unsigned h = 0;
+    cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    float f;
+    memcpy(&f, &h, sizeof f);
+    qref = f;
+  }
+  if (c->d.inject) {
+    const pic_desc &d = c->d;
+    const double r0 = d.r_min, rb = c->G.r_min * (d.r_map == PIC_R_LOG ? std::exp(0.5 * c->G.dxi) : 1.0) +
+                                   (d.r_map == PIC_R_LOG ? 0.0 : 0.5 * c->G.dxi);
+    const double sig = 2.0 * std::fabs(d.b0) * d.omega * std::pow(r0, 4) / std::pow(rb, 3) + 1e-300;
+    const double dA = 2.0 * M_PI * r0 * r0 * 2.0;  // whole sphere bounds any cell
+    qref = std::fmax(qref, 16.0 * d.f_inj * sig * dA / d.pairs_per_cell);
+  }
+  if (c->d.flux_quantum > 0.0) { c->flux_quantum = c->d.flux_quantum; return; }
+  if (!(qref > 0.0)) qref = 1.0;
+  const int e = (int)std::ceil(std::log2(qref));
+  const double q0 = std::ldexp(1.0, e - KFIX);
+  if (q0 > c->flux_quantum) c->flux_quantum = q0;
+}
+
+void particles32(pic_ctx *c, double t) {
+  if (c->flux_quantum == 0.0) update_quantum(c);
+  if (c->n_used == 0) return;
+  Args32 A = make_args(c, t);
+  const int64_t tail = c->n_used - c->tiles.sorted_end;
+  const int64_t blocks = c->tiles.ntiles + (tail + NT - 1) / NT;
+  ++c->launches, k_tiles32<<<(unsigned)blocks, NT, 0, c->stream>>>(A, c->p32);
+}
+
+void flux_from_acc(pic_ctx *c) {
+  const Grid &G = c->G;
+  dim3 gr((G.nth + 1 + 31) / 32, (G.nr + 2 * G.g + 1 + 7) / 8);
+  ++c->launches, k_flux_from_acc<<<gr, dim3(32, 8), 0, c->stream>>>(G.nr, G.nth, G.g, G.PI, G.PJ, G.LD, c->flux_quantum,
+                                                     c->acc[0], c->acc[1], c->acc[2], c->F[0], c->F[1], c->F[2]);
+}
+
+int64_t sort32(pic_ctx *c) {
+  Tiles &T = c->tiles;
+  const int64_t n = c->n_used;
+  if (n == 0) { T.sorted_end = 0; cudaMemsetAsync(T.start, 0, (T.ntiles + 2) * 8, c->stream); return 0; }
+  Args32 A = make_args(c, 0.0);
+  int64_t *count = T.cursor;
+  cudaMemsetAsync(count, 0, (T.ntiles + 2) * sizeof(int64_t), c->stream);
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  ++c->launches, k_hist<<<blocks, 256, 0, c->stream>>>(A, c->p32, n, count);
+  ++c->launches, k_scan_bins<<<1, 1024, 0, c->stream>>>(count, T.start, T.ntiles + 1);
+  ++c->launches, k_scatter_tiles<<<blocks, 256, 0, c->stream>>>(A, c->p32, c->q32, n, count);
+  cudaMemcpyAsync(c->h_pinned, T.start + T.ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+  cudaStreamSynchronize(c->stream);
+  const int64_t live = *c->h_pinned;
+  Parts32 tmp = c->p32;
+  c->p32 = c->q32;
+  c->q32 = tmp;
+  c->n_used = live;
+  T.sorted_end = live;
+  return live;
+}
+
+void charge32(pic_ctx *c, double *Q, double *Qa) {
+  if (c->n_used == 0) return;
+  ++c->launches, k_charge32<<<(unsigned)((c->n_used + 255) / 256), 256, 0, c->stream>>>(c->G.PI, c->G.PJ, c->G.LD, c->p32,
+                                                                        c->n_used, Q, Qa);
+}
+
+void reduce_particles32(pic_ctx *c) {
+  if (c->n_used == 0) return;
+  ++c->launches, k_reduce32<<<(unsigned)((c->n_used + 255) / 256), 256, 0, c->stream>>>(c->p32, c->n_used, c->G.qm, c->d_acc,
+                                                                        c->d_cnt + CNT_LIVE);
+}
+
 }  // namespace pic

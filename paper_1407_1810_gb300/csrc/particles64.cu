@@ -241,7 +241,7 @@ void particles64(pic_ctx *c, double t) {
   for (int k = 0; k < 6; ++k) F.f[k] = c->f[k];
   Flux64 D{c->F[0], c->F[1], c->F[2]};
   const int64_t blocks = (c->n_used + 255) / 256;
-  k_particles64<<<(unsigned)blocks, 256, 0, c->stream>>>(c->G, c->p64, c->n_used, t, F, D, c->d_err, c->d_cnt);
+  ++c->launches, k_particles64<<<(unsigned)blocks, 256, 0, c->stream>>>(c->G, c->p64, c->n_used, t, F, D, c->d_err, c->d_cnt);
 }
 
 int64_t compact64(pic_ctx *c) {
@@ -249,9 +249,9 @@ int64_t compact64(pic_ctx *c) {
   if (n == 0) return 0;
   const int64_t nb = (n + CB - 1) / CB;
   long long *bc = (long long *)c->scratch;
-  k_count_live<<<(unsigned)nb, CB, 0, c->stream>>>(c->p64.qw, n, bc);
-  k_scan_blocks<<<1, 1024, 0, c->stream>>>(bc, nb, c->d_cnt + CNT_SORTED);
-  k_scatter_live<<<(unsigned)nb, CB, 0, c->stream>>>(c->p64, c->q64, n, bc);
+  ++c->launches, k_count_live<<<(unsigned)nb, CB, 0, c->stream>>>(c->p64.qw, n, bc);
+  ++c->launches, k_scan_blocks<<<1, 1024, 0, c->stream>>>(bc, nb, c->d_cnt + CNT_SORTED);
+  ++c->launches, k_scatter_live<<<(unsigned)nb, CB, 0, c->stream>>>(c->p64, c->q64, n, bc);
   cudaMemcpyAsync(c->h_pinned, c->d_cnt + CNT_SORTED, sizeof(long long), cudaMemcpyDeviceToHost, c->stream);
   cudaStreamSynchronize(c->stream);
   const int64_t live = *c->h_pinned;
@@ -264,13 +264,13 @@ int64_t compact64(pic_ctx *c) {
 
 void charge64(pic_ctx *c, double *Q, double *Qa) {
   if (c->n_used == 0) return;
-  k_charge64<<<(unsigned)((c->n_used + 255) / 256), 256, 0, c->stream>>>(c->G, c->p64.x1, c->p64.x2, c->p64.qw,
+  ++c->launches, k_charge64<<<(unsigned)((c->n_used + 255) / 256), 256, 0, c->stream>>>(c->G, c->p64.x1, c->p64.x2, c->p64.qw,
                                                                         c->n_used, Q, Qa);
 }
 
 void reduce_particles64(pic_ctx *c) {
   if (c->n_used == 0) return;
-  k_reduce64<<<(unsigned)((c->n_used + 255) / 256), 256, 0, c->stream>>>(c->p64, c->n_used, c->G.qm, c->d_acc,
+  ++c->launches, k_reduce64<<<(unsigned)((c->n_used + 255) / 256), 256, 0, c->stream>>>(c->p64, c->n_used, c->G.qm, c->d_acc,
                                                                         c->d_cnt + CNT_LIVE);
 }
 

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/picsar.h"
 #include "pic_common.cuh"
@@ -56,6 +57,7 @@ struct pic_ctx {
   double *F[3] = {};      // fluxes of the current step (FP64, after filtering)
   double *Ft[3] = {};     // filter double buffer
   float *f32[6] = {};     // FP32 gather copies (FP32 path)
+  float *r_n32 = nullptr; // f_r(i) per padded row, FP32 (FP32 path)
   long long *acc[3] = {}; // fixed-point flux accumulators (FP32 path)
   double flux_quantum = 0.0;
   double *Q = nullptr, *Qa = nullptr, *Qt = nullptr, *gsnap = nullptr;
@@ -73,11 +75,15 @@ struct pic_ctx {
   double *d_acc = nullptr;
   long long *h_pinned = nullptr;  // pinned host mirror for small reads
   int64_t step = 0, next_id = 0;
+  int64_t launches = 0;  // kernels launched by this context
   int host_err = 0;
   int steps_since_sort = 0;
-  // profiling
+  bool need_sort = false;
+  // profiling: one start/stop event pair per phase per step, read back lazily
   bool prof = false;
-  cudaEvent_t ev[2 * pic::PROF_N] = {};
+  std::vector<cudaEvent_t> ev_pool;           // recorded events, pairs per phase
+  std::vector<int> ev_slot;                   // phase of each pair
+  size_t ev_used = 0;
   double prof_ms[pic::PROF_N] = {};
   int64_t prof_launch[pic::PROF_N] = {};
   int64_t prof_steps = 0;

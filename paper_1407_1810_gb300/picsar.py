@@ -24,8 +24,8 @@ PIC_VAY, PIC_BORIS = 0, 1
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 
 EXPORTS = ["pic_init_grid", "pic_load_particles", "pic_step", "pic_get_fields", "pic_set_fields", "pic_get_flux",
-           "pic_get_particles", "pic_get_moments", "pic_gauss_snapshot", "pic_set_clock", "pic_profile",
-           "pic_get_profile", "pic_ensemble_step", "pic_destroy", "pic_last_error"]
+           "pic_get_particles", "pic_get_live", "pic_get_moments", "pic_gauss_snapshot", "pic_set_clock", "pic_profile",
+           "pic_get_profile", "pic_get_launches", "pic_ensemble_step", "pic_destroy", "pic_last_error"]
 
 
 class pic_desc(C.Structure):
@@ -75,10 +75,12 @@ def lib():
         "pic_get_flux": [P, P, C.POINTER(C.c_int64), I32],
         "pic_get_particles": [P, C.POINTER(C.c_int64), P, P, P, P, P, P, P, I32],
         "pic_get_moments": [P, C.POINTER(pic_moments)],
+        "pic_get_live": [P, C.POINTER(C.c_int64), C.POINTER(C.c_double)],
         "pic_gauss_snapshot": [P],
         "pic_set_clock": [P, I64, I64],
         "pic_profile": [P, I32],
         "pic_get_profile": [P, D, C.POINTER(C.c_int64)],
+        "pic_get_launches": [P, C.POINTER(C.c_int64)],
         "pic_ensemble_step": [C.POINTER(C.c_void_p), I32, I32],
         "pic_destroy": [P],
     }
@@ -194,6 +196,11 @@ class Simulation:
         out["id"] = ids
         return out
 
+    def live(self):
+        n, k = C.c_int64(), C.c_double()
+        check(self.L.pic_get_live(self.h, C.byref(n), C.byref(k)))
+        return n.value
+
     def moments(self):
         m = pic_moments()
         check(self.L.pic_get_moments(self.h, C.byref(m)))
@@ -207,6 +214,11 @@ class Simulation:
 
     def profile(self, enable=True):
         check(self.L.pic_profile(self.h, 1 if enable else 0))
+
+    def launches(self):
+        n = C.c_int64()
+        check(self.L.pic_get_launches(self.h, C.byref(n)))
+        return n.value
 
     def get_profile(self):
         ms = (C.c_double * 6)()

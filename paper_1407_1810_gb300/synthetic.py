@@ -85,3 +85,58 @@ def ensemble_member(m: int):
     n = int(round(10 ** (4 + 2.301 * U)))
     T = 0.05 + 0.95 * U2
     return {"nr": nr, "nth": nth, "particles": n, "T": T, "seed": m}
+
+
+def pair_plasma_cells(nr: int, nth: int, cells, pairs_per_cell: int, T: float, qw: float, seed: int,
+                      dtype=np.float64):
+    """As pair_plasma, restricted to the listed cells (flat indices i * nth + j
+    counted from row 0); used to draw a bounded sample of a large workload."""
+    rng = np.random.default_rng(seed)
+    cells = np.asarray(cells, dtype=np.int64)
+    npair = len(cells) * pairs_per_cell
+    cell = np.repeat(cells, pairs_per_cell)
+    ox, oy = rng.random(npair), rng.random(npair)
+    x1 = np.repeat(cell // nth + ox, 2)
+    x2 = np.repeat(cell % nth + oy, 2)
+    u = mj_momenta(2 * npair, T, rng)
+    q = np.tile(np.array([qw, -qw]), npair)
+    out = {"x1": x1, "x2": x2, "ur": u[:, 0], "uth": u[:, 1], "uph": u[:, 2], "qw": q}
+    return {k: np.ascontiguousarray(v, dtype=dtype) for k, v in out.items()}
+
+
+def pair_plasma_torch(nr: int, nth: int, pairs_per_cell: int, T: float, qw: float, seed: int, device,
+                      rows_per_chunk: int = 64):
+    """The pair-plasma recipe drawn with torch's generator on a device, yielded
+    in chunks of rows (dicts of float64 tensors), for workloads too large for
+    host generation.  Same distribution as pair_plasma, different stream."""
+    import torch
+
+    cdf, ugrid = _mj_table(T)
+    cdf_t = torch.tensor(cdf, device=device, dtype=torch.float64)
+    u_t = torch.tensor(ugrid, device=device, dtype=torch.float64)
+    for r0 in range(0, nr, rows_per_chunk):
+        r1 = min(nr, r0 + rows_per_chunk)
+        g = torch.Generator(device=device)
+        g.manual_seed(seed * 1000003 + r0)
+        ncell = (r1 - r0) * nth
+        npair = ncell * pairs_per_cell
+        cell = torch.arange(ncell, device=device, dtype=torch.int64).repeat_interleave(pairs_per_cell)
+        ox = torch.rand(npair, generator=g, device=device, dtype=torch.float64)
+        oy = torch.rand(npair, generator=g, device=device, dtype=torch.float64)
+        x1 = (r0 + cell // nth).to(torch.float64).add_(ox).repeat_interleave(2)
+        x2 = (cell % nth).to(torch.float64).add_(oy).repeat_interleave(2)
+        del cell, ox, oy
+        n = 2 * npair
+        U = torch.rand(n, generator=g, device=device, dtype=torch.float64)
+        k = torch.searchsorted(cdf_t, U).clamp_(1, len(ugrid) - 1)
+        c0, c1 = cdf_t[k - 1], cdf_t[k]
+        mag = u_t[k - 1] + (U - c0) / (c1 - c0).clamp_min(1e-300) * (u_t[k] - u_t[k - 1])
+        del k, c0, c1, U
+        cosa = torch.rand(n, generator=g, device=device, dtype=torch.float64).mul_(2.0).sub_(1.0)
+        beta = torch.rand(n, generator=g, device=device, dtype=torch.float64).mul_(2.0 * np.pi)
+        sina = (1.0 - cosa * cosa).clamp_min_(0.0).sqrt_()
+        ur = mag * cosa
+        uth = mag * sina * torch.cos(beta)
+        uph = mag * sina * torch.sin(beta)
+        q = torch.tensor([qw, -qw], device=device, dtype=torch.float64).repeat(npair)
+        yield {"x1": x1, "x2": x2, "ur": ur, "uth": uth, "uph": uph, "qw": q}

@@ -1,0 +1,143 @@
+"""GPU parity of the FP32 cell+offset path against the FP64 oracle.
+
+Both sides start from the same FP32-representable state.  Bar: cells and
+removals exact in one-step replay except particles whose coordinate lies
+within TAU = 2e-6 cell of a grid line (counted, must be <= 1e-4 of all);
+positions within 2e-6 cell; fields within 1e-5 relative L2 after 100 steps;
+Gauss residual <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1407_1810_gb300 import configs
+
+from gpu_common import KEYS, by_id, fp32_state, rel_l2, setup
+
+pytestmark = pytest.mark.gpu
+TAU = 2e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1407_1810_gb300 import build
+
+    build.build()
+    O.build_oracle()
+
+
+def _cfg(**over):
+    base = dict(configs.CONFIGS["monopole-64x64"], nr=48, nth=48, pairs_per_cell=4, T=0.3, precision="fp32")
+    base.update(over)
+    return base
+
+
+def _replay_compare(s, o2):
+    """Compare a GPU step with the oracle's replay of the same step."""
+    g, r = by_id(s.particles()), by_id(o2.particles())
+    common = np.intersect1d(g["id"], r["id"])
+    gi = np.isin(g["id"], common)
+    ri = np.isin(r["id"], common)
+    g = {k: v[gi] for k, v in g.items()}
+    r = {k: v[ri] for k, v in r.items()}
+    # near-tie particles: the oracle's coordinate within TAU of a grid line
+    tie = (np.abs(r["x1"] - np.round(r["x1"])) < TAU) | (np.abs(r["x2"] - np.round(r["x2"])) < TAU)
+    ok = ~tie
+    assert tie.sum() <= max(1, 1e-4 * len(tie)), tie.sum()
+    assert np.array_equal(np.floor(g["x1"][ok]), np.floor(r["x1"][ok]))
+    assert np.array_equal(np.floor(g["x2"][ok]), np.floor(r["x2"][ok]))
+    assert np.max(np.abs(g["x1"] - r["x1"])) < TAU
+    assert np.max(np.abs(g["x2"] - r["x2"])) < TAU
+    umag = np.sqrt(r["ur"] ** 2 + r["uth"] ** 2 + r["uph"] ** 2) + 1e-2
+    for k in ("ur", "uth", "uph"):
+        assert np.max(np.abs(g[k] - r[k]) / umag) < 2e-6, k
+    return tie.sum()
+
+
+def _replay(s, o, step, next_id):
+    """Fresh oracle holding the GPU's exact state (fields, particles, clock)."""
+    st = s.particles()
+    o2 = O.Oracle(o.p)
+    o2.load(*(st[k] for k in KEYS), ids=st["id"])
+    o2.set_fields(s.fields())
+    o2.set_clock(step, next_id)
+    return o2
+
+
+@pytest.mark.parametrize("r_map,th_map", [("log", "linear"), ("log", "equal_area"), ("linear", "linear")])
+def test_one_step_replay(r_map, th_map):
+    cfg = _cfg(r_map=r_map, th_map=th_map, r_max=10.0 if r_map == "log" else 4.0)
+    s, o, plasma, dt = setup(cfg)
+    n0 = len(plasma["x1"])
+    s.step(7)
+    o2 = _replay(s, o, 7, n0)
+    s.step(1)
+    o2.step(1)
+    _replay_compare(s, o2)
+    # fluxes of the replayed step (fixed-point sums of FP32 terms)
+    assert rel_l2(s.flux(), o2.flux()) < 1e-5
+    assert s.moments()["deleted"] >= 0
+
+
+def test_monopole_100_steps_fields_and_gauss():
+    cfg = _cfg()
+    s, o, plasma, dt = setup(cfg)
+    o.gauss_snapshot()
+    s.step(100)
+    o.step(100)
+    assert rel_l2(s.fields(), o.fields()) < 1e-5
+    m = s.moments()
+    assert m["gauss_residual"] < 1e-6
+    assert abs(m["live"] - o.num_particles()) <= max(1, 1e-4 * o.num_particles())
+    assert m["kinetic_energy"] == pytest.approx(o.kinetic_energy(), rel=1e-5)
+
+
+@pytest.mark.parametrize("th_map", ["equal_area", "linear"])
+def test_rotator_injection_filter_fp32(th_map):
+    cfg = dict(configs.CONFIGS["rotator-1024x1024"], nr=40, nth=32, pairs_per_cell=2, absorb_cells=8, t_spin=2.0,
+               th_map=th_map)
+    s, o, plasma, dt = setup(cfg)
+    o.gauss_snapshot()
+    s.step(60)
+    o.step(60)
+    assert rel_l2(s.fields(), o.fields()) < 1e-5
+    m, cnt = s.moments(), o.counters()
+    assert m["injected"] == cnt["injected"]
+    assert abs(m["live"] - cnt["live"]) <= 2
+    assert m["gauss_residual"] < 1e-6
+
+
+@pytest.mark.parametrize("sort_interval", [1, 1000])
+def test_window_and_global_paths_agree(sort_interval):
+    """sort_interval 1000: particles drift out of their tile windows and take
+    the global-memory path; the result must not depend on it."""
+    cfg = _cfg(T=1.0, sort_interval=sort_interval)
+    s, o, plasma, dt = setup(cfg)
+    s.step(40)
+    o.step(40)
+    assert rel_l2(s.fields(), o.fields()) < 1e-5
+
+
+def test_fixed_point_deposit_is_deterministic():
+    cfg = _cfg()
+    out = []
+    for _ in range(2):
+        s, o, plasma, dt = setup(cfg)
+        s.step(20)
+        out.append((s.fields(), s.flux()))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_fp32_against_fp64_gpu_path():
+    cfg = _cfg()
+    s32, o, plasma, dt = setup(cfg)
+    s64, _, _, _ = setup(cfg, plasma=plasma, precision="fp64")
+    s32.step(100)
+    s64.step(100)
+    assert rel_l2(s32.fields(), s64.fields()) < 1e-5
