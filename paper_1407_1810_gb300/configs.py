@@ -60,7 +60,7 @@ def physics(cfg: dict, dt: float, q_over_m: float = 1.0):
     b0 = cfg["wc_dt"] / (dt * q_over_m)
     j = cfg["nth"] // 2  # equatorial cell (upper edge at the equator for even nth)
     vol = 2 * math.pi / 3 * (_fr(cfg, 1) ** 3 - _fr(cfg, 0) ** 3) * (_cos_th(cfg, j - 1) - _cos_th(cfg, j))
-    n_in_cell = 2 * cfg["pairs_per_cell"]
+    n_in_cell = 2 * max(cfg["pairs_per_cell"], 1)
     wp = cfg["wp_dt"] / dt
     qw = wp * wp * vol / (n_in_cell * q_over_m)
     return b0, qw

@@ -28,7 +28,13 @@ constexpr int TI = 16, TJ = 16, H = 2;
 constexpr int WI = TI + 2 * H + 3, WJ = TJ + 2 * H + 3;  // window nodes
 constexpr int WN = WI * WJ;
 constexpr int NT = 256;                                  // threads per tile CTA
-constexpr int KFIX = 40;                                 // fixed point: 2^-40 of the reference charge
+constexpr int KFIX = 36;                                 // fixed point: 2^-36 of the reference charge
+// Shared-memory accumulation splits each int64 term v (|v| <= 2^36) into
+// v = a 2^SPLIT + b with 0 <= b < 2^SPLIT and sums a and b with native 32-bit
+// shared atomics: both sums stay exact below 2^31 / 2^18 = 8192 terms per
+// node per tile per step (about 2000 particles per cell); beyond that the
+// flush reports ERR_CAPACITY instead of wrapping silently.
+constexpr int SPLIT = 18;
 
 struct Args32 {
   int nr, nth, n_filt, PI, PJ, LD;
@@ -54,11 +60,16 @@ __device__ inline size_t pidx(const Args32 &A, int i, int j) {
 
 struct SmemAcc {  // window accessors (shared memory)
   const float *f;           // 6 * WN
-  unsigned long long *F;    // 3 * WN
+  int *hi;                  // 3 * WN : sums of v >> SPLIT
+  unsigned *lo;             // 3 * WN : sums of v & (2^SPLIT - 1)
   int wi0, wj0;
   __device__ float fld(int c, int i, int j) const { return f[c * WN + (i - wi0) * WJ + (j - wj0)]; }
   __device__ void add(int k, int i, int j, long long v) const {
-    if (v) atomicAdd(&F[k * WN + (i - wi0) * WJ + (j - wj0)], (unsigned long long)v);
+    if (v) {
+      const int e = k * WN + (i - wi0) * WJ + (j - wj0);
+      atomicAdd(&hi[e], (int)(v >> SPLIT));
+      atomicAdd(&lo[e], (unsigned)(v & ((1LL << SPLIT) - 1)));
+    }
   }
 };
 
@@ -100,14 +111,19 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   // ---- geometry of the particle's position (Sec. 3.2) -----------------------
   const float rn = A.r_n[ci + A.PI];
   const float r = A.r_log ? rn * expf(dx * A.dxi) : rn + dx * A.dxi;
-  const float x2 = (float)cj + dy;
+  // sin and cos of theta from the distance to the nearer pole, which both
+  // offsets resolve to FP32 relative precision (1 - x2/nth would cancel)
+  const float x2 = (float)cj + dy;                 // distance to the north pole
+  const float rest = (float)(A.nth - cj) - dy;     // distance to the south pole
   float st, ct;
   if (A.th_ea) {  // cos th = 1 - 2 x2/nth, sin th = 2 sqrt(x2 (nth - x2))/nth
-    const float rest = (float)(A.nth - cj) - dy;
-    ct = ((float)(A.nth - cj) - (float)cj - 2.f * dy) * A.inv_nth;
+    ct = (rest - x2) * A.inv_nth;
     st = 2.f * sqrtf(fmaxf(x2 * rest, 0.f)) * A.inv_nth;
-  } else {
+  } else if (x2 <= rest) {
     sincospif(x2 * A.inv_nth, &st, &ct);
+  } else {
+    sincospif(rest * A.inv_nth, &st, &ct);
+    ct = -ct;
   }
   // ---- gather + push (ballistic inside the outer conductor) -----------------
   if (ci < A.nr) {
@@ -246,7 +262,8 @@ __device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, 
 
 __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
   __shared__ float sf[6 * WN];
-  __shared__ unsigned long long sF[3 * WN];
+  __shared__ int shi[3 * WN];
+  __shared__ unsigned slo[3 * WN];
   __shared__ int sdead;
   const GlobAcc gw{&A};
   int dead = 0;
@@ -261,10 +278,11 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
       const size_t o = pidx(A, wi0 + e / WJ, wj0 + e % WJ);
 #pragma unroll
       for (int c = 0; c < 6; ++c) sf[c * WN + e] = A.f[c][o];
-      sF[e] = 0ull; sF[WN + e] = 0ull; sF[2 * WN + e] = 0ull;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { shi[c * WN + e] = 0; slo[c * WN + e] = 0u; }
     }
     __syncthreads();
-    const SmemAcc sw{sf, sF, wi0, wj0};
+    const SmemAcc sw{sf, shi, slo, wi0, wj0};
     for (int64_t k = b0 + threadIdx.x; k < b1; k += NT)
       process(A, P, k, true, sw, gw, i0 - H, i0 + TI + H, j0 - H, j0 + TJ + H, dead);
     if (dead) atomicAdd(&sdead, dead);
@@ -273,13 +291,15 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
       const size_t o = pidx(A, wi0 + e / WJ, wj0 + e % WJ);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const unsigned long long v = sF[c * WN + e];
-        if (v) atomicAdd(reinterpret_cast<unsigned long long *>(A.acc[c] + o), v);
+        const unsigned l = slo[c * WN + e];
+        if (l >= 0x80000000u) atomicOr(A.err, ERR_CAPACITY);  // near the exact-sum limit
+        const long long v = ((long long)shi[c * WN + e] << SPLIT) + (long long)l;
+        if (v) atomicAdd(reinterpret_cast<unsigned long long *>(A.acc[c] + o), (unsigned long long)v);
       }
     }
     if (threadIdx.x == 0 && sdead) add_ll(A.cnt + CNT_DELETED, sdead);
   } else {  // particles outside any bin (injected since the last sort)
-    const SmemAcc none{nullptr, nullptr, 0, 0};
+    const SmemAcc none{nullptr, nullptr, nullptr, 0, 0};
     const int64_t k = A.sorted_end + (int64_t)(blockIdx.x - A.ntiles) * NT + threadIdx.x;
     if (k < A.n_used) process(A, P, k, false, none, gw, 0, 0, 0, 0, dead);
     if (dead) add_ll(A.cnt + CNT_DELETED, dead);
@@ -374,30 +394,27 @@ __global__ void k_charge32(int PI, int PJ, int LD, Parts32 P, int64_t n, double 
 __global__ void k_reduce32(Parts32 P, int64_t n, double qm, double *acc, long long *live) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double kin = 0.0, ch = 0.0;
-  int l = 0;
+  long long l = 0;
   if (k < n && P.qw[k] != 0.f) {
     const double q = P.qw[k], a = P.ur[k], b = P.ut[k], c = P.up[k];
     kin = fabs(q) / qm * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
     ch = q;
     l = 1;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    kin += __shfl_xor_sync(0xffffffffu, kin, o);
-    ch += __shfl_xor_sync(0xffffffffu, ch, o);
-    l += __shfl_xor_sync(0xffffffffu, l, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(acc + ACC_KIN, kin);
-    atomicAdd(acc + ACC_CHARGE, ch);
-    add_ll(live, (long long)l);
-  }
+  block_sum3(kin, ch, l, acc + ACC_KIN, acc + ACC_CHARGE, live);
 }
 
 __global__ void k_max_abs_qw(const float *qw, int64_t n, unsigned *out) {
+  __shared__ float sm[32];
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   float v = k < n ? fabsf(qw[k]) : 0.f;
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(v));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, sm[w]);
+    atomicMax(out, __float_as_uint(v));
+  }
 }
 
 Args32 make_args(pic_ctx *c, double t) {

@@ -214,23 +214,14 @@ __global__ void k_charge64(Grid G, const double *__restrict__ x1, const double *
 __global__ void k_reduce64(Parts64 P, int64_t n, double qm, double *acc, long long *live) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double kin = 0.0, ch = 0.0;
-  int l = 0;
+  long long l = 0;
   if (k < n && P.qw[k] != 0.0) {
     const double q = P.qw[k], u2 = P.ur[k] * P.ur[k] + P.ut[k] * P.ut[k] + P.up[k] * P.up[k];
     kin = fabs(q) / qm * (sqrt(1.0 + u2) - 1.0);
     ch = q;
     l = 1;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    kin += __shfl_xor_sync(0xffffffffu, kin, o);
-    ch += __shfl_xor_sync(0xffffffffu, ch, o);
-    l += __shfl_xor_sync(0xffffffffu, l, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(acc + ACC_KIN, kin);
-    atomicAdd(acc + ACC_CHARGE, ch);
-    add_ll(live, (long long)l);
-  }
+  block_sum3(kin, ch, l, acc + ACC_KIN, acc + ACC_CHARGE, live);
 }
 
 }  // namespace

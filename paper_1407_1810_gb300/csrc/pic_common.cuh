@@ -168,6 +168,28 @@ __device__ inline void push(int pusher, T qmdt, const T E[3], const T B[3], T u[
 }
 
 __device__ inline void set_err(int *err, int bits) { atomicOr(err, bits); }
+// block-wide sums of (double, double, int) with one atomic per block:
+// warp shuffles, then the warp leaders through shared memory
+__device__ inline void block_sum3(double a, double b, long long n, double *pa, double *pb, long long *pn) {
+  __shared__ double sa[32], sb[32];
+  __shared__ long long sn[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    n += __shfl_xor_sync(0xffffffffu, n, o);
+  }
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0) { sa[w] = a; sb[w] = b; sn[w] = n; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    long long tn = 0;
+    for (int k = 0; k < nw; ++k) { ta += sa[k]; tb += sb[k]; tn += sn[k]; }
+    if (pa) atomicAdd(pa, ta);
+    if (pb) atomicAdd(pb, tb);
+    if (pn) atomicAdd(reinterpret_cast<unsigned long long *>(pn), static_cast<unsigned long long>(tn));
+  }
+}
 // signed 64-bit add through the unsigned overload (two's complement)
 __device__ inline void add_ll(long long *p, long long v) {
   atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
