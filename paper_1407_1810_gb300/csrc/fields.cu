@@ -146,9 +146,10 @@ __global__ void k_inject_sigma(Grid G, const double *__restrict__ Er, double t, 
   const Metric &m = G.m;
   const double rb0 = m.r_h[G.PI];
   double E[3], B[3];
-  vacuum_field<double>(G, rb0, m.sin_t[j + G.PJ], m.cos_t[j + G.PJ], t, false, E, B);
+  const Vac<double> V{G.vacuum, G.b0, G.r_min, omega_at(G.omega, G.t_spin, t)};
+  vacuum_field<double>(V, rb0, m.sin_t[j + G.PJ], m.cos_t[j + G.PJ], false, E, B);
   double e0 = Er[gidx(G, 0, j)] + E[0];
-  vacuum_field<double>(G, rb0, m.sin_t[j + 1 + G.PJ], m.cos_t[j + 1 + G.PJ], t, false, E, B);
+  vacuum_field<double>(V, rb0, m.sin_t[j + 1 + G.PJ], m.cos_t[j + 1 + G.PJ], false, E, B);
   double e1 = Er[gidx(G, 0, j + 1)] + E[0];
   double s = 0.5 * (e0 + e1);  // jump of E_r across r0 (zero inside)
   sig[j] = s;

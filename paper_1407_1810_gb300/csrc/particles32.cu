@@ -29,11 +29,11 @@ constexpr int WI = TI + 2 * H + 3, WJ = TJ + 2 * H + 3;  // window nodes
 constexpr int WN = WI * WJ;
 constexpr int NT = 256;                                  // threads per tile CTA
 constexpr int KFIX = 36;                                 // fixed point: 2^-36 of the reference charge
-// Shared-memory accumulation splits each int64 term v (|v| <= 2^36) into
-// v = a 2^SPLIT + b with 0 <= b < 2^SPLIT and sums a and b with native 32-bit
-// shared atomics: both sums stay exact below 2^31 / 2^18 = 8192 terms per
-// node per tile per step (about 2000 particles per cell); beyond that the
-// flush reports ERR_CAPACITY instead of wrapping silently.
+// Shared-memory accumulation splits each term v (|v| <= 2^36 quanta) into
+// v = h 2^SPLIT + l with |h| <= 2^18, |l| <= 2^17 and sums h and l with
+// native 32-bit shared atomics: both sums stay exact below 2^31 / 2^18 = 8192
+// terms per node per tile per step (about 2000 particles per cell); sums
+// approaching that limit are reported as ERR_CAPACITY.
 constexpr int SPLIT = 18;
 
 struct Args32 {
@@ -60,26 +60,40 @@ __device__ inline size_t pidx(const Args32 &A, int i, int j) {
 
 struct SmemAcc {  // window accessors (shared memory)
   const float *f;           // 6 * WN
-  int *hi;                  // 3 * WN : sums of v >> SPLIT
-  unsigned *lo;             // 3 * WN : sums of v & (2^SPLIT - 1)
+  int *hi;                  // 3 * WN : sums of the high parts
+  int *lo;                  // 3 * WN : sums of the low parts
   int wi0, wj0;
   __device__ float fld(int c, int i, int j) const { return f[c * WN + (i - wi0) * WJ + (j - wj0)]; }
-  __device__ void add(int k, int i, int j, long long v) const {
-    if (v) {
-      const int e = k * WN + (i - wi0) * WJ + (j - wj0);
-      atomicAdd(&hi[e], (int)(v >> SPLIT));
-      atomicAdd(&lo[e], (unsigned)(v & ((1LL << SPLIT) - 1)));
-    }
+  __device__ void add(int k, int i, int j, int h, int l) const {
+    const int e = k * WN + (i - wi0) * WJ + (j - wj0);
+    if (h) atomicAdd(&hi[e], h);
+    if (l) atomicAdd(&lo[e], l);
   }
 };
 
 struct GlobAcc {  // global-memory accessors (particles outside the window)
   const Args32 *A;
   __device__ float fld(int c, int i, int j) const { return A->f[c][pidx(*A, i, j)]; }
-  __device__ void add(int k, int i, int j, long long v) const {
+  __device__ void add(int k, int i, int j, int h, int l) const {
+    const long long v = ((long long)h << SPLIT) + (long long)l;
     if (v) atomicAdd(reinterpret_cast<unsigned long long *>(A->acc[k] + pidx(*A, i, j)), (unsigned long long)v);
   }
 };
+
+// Fixed-point split of a flux term cs (in quanta, |cs| <= 2^36) into integers
+// h, l with h 2^SPLIT + l = rint(cs), |h| <= 2^18, |l| <= 2^17.  Rounding to
+// an integer by adding 1.5 * 2^23 is exact for |x| < 2^22; the subtraction
+// cs - h 2^SPLIT is exact (Sterbenz).  Only FP32 adds and integer ops, no
+// 64-bit conversions.
+__device__ inline void split_fix(float cs, int &h, int &l) {
+  const float MAGIC = 12582912.0f;
+  const float hf = cs * (1.0f / (float)(1 << SPLIT));
+  const float hm = hf + MAGIC;
+  h = __float_as_int(hm) - 0x4B400000;
+  const float hr = hm - MAGIC;
+  const float lf = cs - hr * (float)(1 << SPLIT);
+  l = __float_as_int(lf + MAGIC) - 0x4B400000;
+}
 
 template <class W>
 __device__ inline float bilin(const W &w, int c, int i, int j, float a, float b) {
@@ -93,12 +107,39 @@ template <class W>
 __device__ inline void vb_seg(const W &w, float scale, int i, int j, float p1, float p2, float q1, float q2) {
   const float d1 = q1 - p1, d2 = q2 - p2, m1 = 0.5f * (p1 + q1), m2 = 0.5f * (p2 + q2);
   const float a = scale * d1, b = scale * d2;
-  const long long fr1 = __float2ll_rn(a * m2), fr0 = __float2ll_rn(a * (1.f - m2));
-  const long long ft1 = __float2ll_rn(b * m1), ft0 = __float2ll_rn(b * (1.f - m1));
-  w.add(0, i, j, fr0);
-  w.add(0, i, j + 1, fr1);
-  w.add(1, i, j, ft0);
-  w.add(1, i + 1, j, ft1);
+  int h, l;
+  if (a != 0.f) {
+    split_fix(a * (1.f - m2), h, l);
+    w.add(0, i, j, h, l);
+    split_fix(a * m2, h, l);
+    w.add(0, i, j + 1, h, l);
+  }
+  if (b != 0.f) {
+    split_fix(b * (1.f - m1), h, l);
+    w.add(1, i, j, h, l);
+    split_fix(b * m1, h, l);
+    w.add(1, i + 1, j, h, l);
+  }
+}
+
+// log1p, atan and expm1 for the small arguments of a single step: truncated
+// Taylor series (remainders below 1e-11 relative for |x| < 1/32), otherwise
+// the library functions
+__device__ inline float log1p_small(float s) {
+  if (fabsf(s) < 0.03125f)
+    return s * (1.f - s * (0.5f - s * (0.33333334f - s * (0.25f - s * (0.2f - s * 0.16666667f)))));
+  return log1pf(s);
+}
+__device__ inline float atan2_small(float y, float x) {
+  if (x > 0.f && fabsf(y) < 0.03125f * x) {
+    const float t = y * rcp_(x), t2 = t * t;
+    return t * (1.f - t2 * (0.33333334f - t2 * (0.2f - t2 * 0.14285715f)));
+  }
+  return atan2f(y, x);
+}
+__device__ inline float exp_small(float y) {
+  if (fabsf(y) < 0.03125f) return 1.f + y * (1.f + y * (0.5f + y * (0.16666667f + y * (0.041666668f + y * 0.008333334f))));
+  return expf(y);
 }
 
 __device__ inline float clamp01(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
@@ -110,7 +151,7 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   const int ci = (int)(cell >> 16) - CELL_BIAS, cj = (int)(cell & 0xffffu);
   // ---- geometry of the particle's position (Sec. 3.2) -----------------------
   const float rn = A.r_n[ci + A.PI];
-  const float r = A.r_log ? rn * expf(dx * A.dxi) : rn + dx * A.dxi;
+  const float r = A.r_log ? rn * exp_small(dx * A.dxi) : rn + dx * A.dxi;
   // sin and cos of theta from the distance to the nearer pole, which both
   // offsets resolve to FP32 relative precision (1 - x2/nth would cancel)
   const float x2 = (float)cj + dy;                 // distance to the north pole
@@ -128,11 +169,8 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   // ---- gather + push (ballistic inside the outer conductor) -----------------
   if (ci < A.nr) {
     float E[3], B[3];
-    {
-      Grid Gv;  // only the vacuum-field members are read
-      Gv.vacuum = A.vacuum; Gv.b0 = A.b0; Gv.r_min = A.r_min; Gv.omega = A.omega_t; Gv.t_spin = 0.0;
-      vacuum_field<float>(Gv, r, st, ct, 0.0, ci < 0, E, B);
-    }
+    const Vac<float> V{A.vacuum, A.b0, A.r_min, A.omega_t};
+    vacuum_field<float>(V, r, st, ct, ci < 0, E, B);
     if (ci >= 0) {  // plasma field only outside the inner conductor
       const bool hx = dx >= 0.5f, hy = dy >= 0.5f;
       const int ih = hx ? ci : ci - 1, jh = hy ? cj : cj - 1;
@@ -151,17 +189,17 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
     ur = u[0]; ut = u[1]; up = u[2];
   }
   // ---- move in the local frame (Sec. 3.3) -----------------------------------
-  const float ig = 1.f / sqrtf(1.f + ur * ur + ut * ut + up * up);
+  const float ig = rsqrt_(1.f + ur * ur + ut * ut + up * up);
   const float Dr = ur * ig * A.dt, Dt = ut * ig * A.dt, Dp = up * ig * A.dt;
-  const float ir = 1.f / r;
+  const float ir = rcp_(r);
   const float a = Dr * ir, b = Dt * ir, c = Dp * ir;
   const float s = a * (2.f + a) + b * b + c * c;  // (r'/r)^2 - 1
-  const float D1 = A.r_log ? 0.5f * log1pf(s) * A.inv_dxi : r * s / (1.f + sqrtf(1.f + s)) * A.inv_dxi;
+  const float D1 = A.r_log ? 0.5f * log1p_small(s) * A.inv_dxi : r * s * rcp_(1.f + sqrtf(1.f + s)) * A.inv_dxi;
   const float p = r + Dr, q = Dt;
   const float Px = p * st + q * ct, Pz = p * ct - q * st;  // displaced point, (R, z) before rotating back
   const float Rn = sqrtf(Px * Px + Dp * Dp);
-  const float kap = Px >= 0.f ? (Rn + Px > 0.f ? Dp * Dp / (Rn + Px) : 0.f) : Rn - Px;  // R' - Px
-  const float dth = atan2f(q + ct * kap, p + st * kap);                                 // theta' - theta
+  const float kap = Px >= 0.f ? (Rn + Px > 0.f ? Dp * Dp * rcp_(Rn + Px) : 0.f) : Rn - Px;  // R' - Px
+  const float dth = atan2_small(q + ct * kap, p + st * kap);                                 // theta' - theta
   float D2;
   if (A.th_ea) {
     float sh, ch;
@@ -181,7 +219,8 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   if (ncj > A.nth - 1) { ncj = A.nth - 1; ky = ncj - cj; ny = 1.f; }   // rounding past the south axis
   // momentum: to Cartesian at phi = 0, rotate back by -phi', to the new frame
   const float ux = ur * st + ut * ct, uz = ur * ct - ut * st;
-  const float cph = Rn > 0.f ? Px / Rn : 1.f, sph = Rn > 0.f ? Dp / Rn : 0.f;
+  const float iRn = Rn > 0.f ? rcp_(Rn) : 0.f;
+  const float cph = Rn > 0.f ? Px * iRn : 1.f, sph = Dp * iRn;
   const float uxx = cph * ux + sph * up, uyy = -sph * ux + cph * up;
   const float irn = rsqrtf(fmaxf(Rn * Rn + Pz * Pz, 1e-30f));
   const float stn = Rn * irn, ctn = Pz * irn;
@@ -195,8 +234,10 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   const float scale = qw * A.fscale;
   const float Dxs = kx == 0 ? nx - dx : (kx > 0 ? (1.f - dx) + nx : -(dx + (1.f - nx)));
   const float Dys = ky == 0 ? ny - dy : (ky > 0 ? (1.f - dy) + ny : -(dy + (1.f - ny)));
-  const float sx = kx > 0 ? (1.f - dx) / Dxs : (kx < 0 ? -dx / Dxs : 2.f);
-  const float sy = ky > 0 ? (1.f - dy) / Dys : (ky < 0 ? -dy / Dys : 2.f);
+  // crossing parameters: any point on the crossed grid line keeps charge
+  // conservation exact, so an approximate reciprocal is enough here
+  const float sx = kx > 0 ? (1.f - dx) * rcp_(Dxs) : (kx < 0 ? -dx * rcp_(Dxs) : 2.f);
+  const float sy = ky > 0 ? (1.f - dy) * rcp_(Dys) : (ky < 0 ? -dy * rcp_(Dys) : 2.f);
   const float Xo = kx > 0 ? 1.f : 0.f, Xn = 1.f - Xo;  // boundary in old / new x frame
   const float Yo = ky > 0 ? 1.f : 0.f, Yn = 1.f - Yo;
   if (kx == 0 && ky == 0) {
@@ -225,16 +266,23 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   // azimuthal flux: charge crossing the meridional half-plane, qw dphi / 2 pi,
   // area weights at the midpoint of the grid path
   {
-    const float phi = atan2f(Dp, Px);
+    const float phi = atan2_small(Dp, Px);
     const float v = scale * phi * 0.15915494309189535f;
     const float mx = 0.5f * (dx + (float)kx + nx), my = 0.5f * (dy + (float)ky + ny);
     const float fx = floorf(mx), fy = floorf(my);
     const float wx = mx - fx, wy = my - fy;
     const int i0 = ci + (int)fx, j0 = cj + (int)fy;
-    w.add(2, i0, j0, __float2ll_rn(v * (1.f - wx) * (1.f - wy)));
-    w.add(2, i0 + 1, j0, __float2ll_rn(v * wx * (1.f - wy)));
-    w.add(2, i0, j0 + 1, __float2ll_rn(v * (1.f - wx) * wy));
-    w.add(2, i0 + 1, j0 + 1, __float2ll_rn(v * wx * wy));
+    if (v != 0.f) {
+      int h, l;
+      split_fix(v * (1.f - wx) * (1.f - wy), h, l);
+      w.add(2, i0, j0, h, l);
+      split_fix(v * wx * (1.f - wy), h, l);
+      w.add(2, i0 + 1, j0, h, l);
+      split_fix(v * (1.f - wx) * wy, h, l);
+      w.add(2, i0, j0 + 1, h, l);
+      split_fix(v * wx * wy, h, l);
+      w.add(2, i0 + 1, j0 + 1, h, l);
+    }
   }
   // ---- store; removal once the filtered shape is inside a conductor ---------
   const int nci = ci + kx;
@@ -263,7 +311,7 @@ __device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, 
 __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
   __shared__ float sf[6 * WN];
   __shared__ int shi[3 * WN];
-  __shared__ unsigned slo[3 * WN];
+  __shared__ int slo[3 * WN];
   __shared__ int sdead;
   const GlobAcc gw{&A};
   int dead = 0;
@@ -279,7 +327,7 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
 #pragma unroll
       for (int c = 0; c < 6; ++c) sf[c * WN + e] = A.f[c][o];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) { shi[c * WN + e] = 0; slo[c * WN + e] = 0u; }
+      for (int c = 0; c < 3; ++c) { shi[c * WN + e] = 0; slo[c * WN + e] = 0; }
     }
     __syncthreads();
     const SmemAcc sw{sf, shi, slo, wi0, wj0};
@@ -291,9 +339,9 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
       const size_t o = pidx(A, wi0 + e / WJ, wj0 + e % WJ);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const unsigned l = slo[c * WN + e];
-        if (l >= 0x80000000u) atomicOr(A.err, ERR_CAPACITY);  // near the exact-sum limit
-        const long long v = ((long long)shi[c * WN + e] << SPLIT) + (long long)l;
+        const int hsum = shi[c * WN + e], lsum = slo[c * WN + e];
+        if (abs(hsum) >= (1 << 30) || abs(lsum) >= (1 << 30)) atomicOr(A.err, ERR_CAPACITY);  // near the limit
+        const long long v = ((long long)hsum << SPLIT) + (long long)lsum;
         if (v) atomicAdd(reinterpret_cast<unsigned long long *>(A.acc[c] + o), (unsigned long long)v);
       }
     }
@@ -436,9 +484,7 @@ Args32 make_args(pic_ctx *c, double t) {
   A.sorted_end = c->tiles.sorted_end;
   A.n_used = c->n_used;
   A.b0 = (float)G.b0; A.r_min = (float)G.r_min;
-  double W = G.omega;
-  if (G.t_spin > 0.0 && t < G.t_spin) W = G.omega * (t / G.t_spin);
-  A.omega_t = (float)W;
+  A.omega_t = (float)omega_at(G.omega, G.t_spin, t);
   return A;
 }
 

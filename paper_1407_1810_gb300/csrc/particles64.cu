@@ -83,7 +83,8 @@ __global__ void __launch_bounds__(256) k_particles64(Grid G, Parts64 P, int64_t 
   double u[3] = {ur * st + ut * ct, up, ur * ct - ut * st};
   if (x1 < G.nr) {  // inside the outer conductor particles fly ballistically
     double Es[3], Bs[3];
-    vacuum_field<double>(G, r, st, ct, t, x1 < 0.0, Es, Bs);
+    const Vac<double> V{G.vacuum, G.b0, G.r_min, omega_at(G.omega, G.t_spin, t)};
+    vacuum_field<double>(V, r, st, ct, x1 < 0.0, Es, Bs);
     if (x1 >= 0.0) {  // no plasma field inside the inner conductor
       Es[0] += interp64(G, F.f[ER], x1, x2, 1, 0);
       Es[1] += interp64(G, F.f[ETH], x1, x2, 0, 1);

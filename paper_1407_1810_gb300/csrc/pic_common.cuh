@@ -82,16 +82,25 @@ __device__ inline double map_th_inv(const Grid &G, double th) {
 }
 
 // ---- analytic "initial" fields: Sec. 5.2 (monopole, rotator inside/outside),
-//      Sec. 4.3 (dipole + corotation), uniform B_z.  Spherical components. ------
+//      Sec. 4.3 (dipole + corotation), uniform B_z.  Spherical components.
+//      W = Omega(t)/c after the linear spin-up. -----------------------------------
 template <typename T>
-__device__ inline void vacuum_field(const Grid &G, T r, T st, T ct, double t, bool inside, T E[3], T B[3]) {
+struct Vac {
+  int kind;
+  T b0, r0, W;
+};
+
+__host__ __device__ inline double omega_at(double omega, double t_spin, double t) {
+  return (t_spin > 0.0 && t < t_spin) ? omega * (t / t_spin) : omega;
+}
+
+template <typename T>
+__device__ inline void vacuum_field(const Vac<T> &V, T r, T st, T ct, bool inside, T E[3], T B[3]) {
   E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = T(0);
-  if (G.vacuum == 0) return;
-  const T b0 = T(G.b0), r0 = T(G.r_min);
-  T W = T(G.omega);  // Omega(t) / c, linear spin-up
-  if (G.t_spin > 0.0 && t < G.t_spin) W = T(G.omega * (t / G.t_spin));
+  if (V.kind == 0) return;
+  const T b0 = V.b0, r0 = V.r0, W = V.W;
   const T ir = T(1) / r, q = r0 * ir;
-  switch (G.vacuum) {
+  switch (V.kind) {
     case 1:  // monopole
       B[0] = b0 * q * q;
       break;
@@ -122,15 +131,22 @@ __device__ inline void vacuum_field(const Grid &G, T r, T st, T ct, double t, bo
   }
 }
 
+// reciprocal and reciprocal square root: hardware approximations (a few ulp)
+// in FP32, exact division in FP64
+__device__ inline float rcp_(float x) { return __frcp_rn(x); }
+__device__ inline double rcp_(double x) { return 1.0 / x; }
+__device__ inline float rsqrt_(float x) { return rsqrtf(x); }
+__device__ inline double rsqrt_(double x) { return 1.0 / sqrt(x); }
+
 // ---- pushers, Sec. 2 (Boris 1970; Vay 2008).  Any right-handed orthonormal
 //      basis; qmdt = (q/m) dt.  u = gamma v updated in place. -------------------
 template <typename T>
 __device__ inline void push_boris(T qmdt, const T E[3], const T B[3], T u[3]) {
   const T h = T(0.5) * qmdt;
   T um0 = u[0] + h * E[0], um1 = u[1] + h * E[1], um2 = u[2] + h * E[2];
-  T ig = T(1) / sqrt(T(1) + um0 * um0 + um1 * um1 + um2 * um2);
+  T ig = rsqrt_(T(1) + um0 * um0 + um1 * um1 + um2 * um2);
   T t0 = h * B[0] * ig, t1 = h * B[1] * ig, t2 = h * B[2] * ig;
-  T f = T(2) / (T(1) + t0 * t0 + t1 * t1 + t2 * t2);
+  T f = T(2) * rcp_(T(1) + t0 * t0 + t1 * t1 + t2 * t2);
   T up0 = um0 + (um1 * t2 - um2 * t1), up1 = um1 + (um2 * t0 - um0 * t2), up2 = um2 + (um0 * t1 - um1 * t0);
   T s0 = f * t0, s1 = f * t1, s2 = f * t2;
   u[0] = um0 + (up1 * s2 - up2 * s1) + h * E[0];
@@ -141,7 +157,7 @@ __device__ inline void push_boris(T qmdt, const T E[3], const T B[3], T u[3]) {
 template <typename T>
 __device__ inline void push_vay(T qmdt, const T E[3], const T B[3], T u[3]) {
   const T h = T(0.5) * qmdt;
-  T ig0 = T(1) / sqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  T ig0 = rsqrt_(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   T tau0 = h * B[0], tau1 = h * B[1], tau2 = h * B[2];
   T v0 = u[0] * ig0, v1 = u[1] * ig0, v2 = u[2] * ig0;
   // u' = u + (q dt/m) E + v x tau
@@ -152,9 +168,9 @@ __device__ inline void push_vay(T qmdt, const T E[3], const T B[3], T u[3]) {
   T ustar = a0 * tau0 + a1 * tau1 + a2 * tau2;
   T sigma = T(1) + a0 * a0 + a1 * a1 + a2 * a2 - tau2s;
   T g2 = T(0.5) * (sigma + sqrt(sigma * sigma + T(4) * (tau2s + ustar * ustar)));
-  T ig = T(1) / sqrt(g2);
+  T ig = rsqrt_(g2);
   T t0 = tau0 * ig, t1 = tau1 * ig, t2 = tau2 * ig;
-  T s = T(1) / (T(1) + t0 * t0 + t1 * t1 + t2 * t2);
+  T s = rcp_(T(1) + t0 * t0 + t1 * t1 + t2 * t2);
   T at = a0 * t0 + a1 * t1 + a2 * t2;
   u[0] = s * (a0 + at * t0 + (a1 * t2 - a2 * t1));
   u[1] = s * (a1 + at * t1 + (a2 * t0 - a0 * t2));
