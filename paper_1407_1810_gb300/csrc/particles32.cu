@@ -231,6 +231,10 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
     return false;
   }
   // ---- Villasenor-Buneman deposit along the grid-coordinate path -----------
+  // Always three segments, split where the path crosses the x and y grid
+  // lines in the order it meets them; a line not crossed puts its segment at
+  // zero length (zero terms are skipped).  Branch-free, so lanes that cross
+  // and lanes that do not run the same instructions.
   const float scale = qw * A.fscale;
   const float Dxs = kx == 0 ? nx - dx : (kx > 0 ? (1.f - dx) + nx : -(dx + (1.f - nx)));
   const float Dys = ky == 0 ? ny - dy : (ky > 0 ? (1.f - dy) + ny : -(dy + (1.f - ny)));
@@ -238,31 +242,28 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   // conservation exact, so an approximate reciprocal is enough here
   const float sx = kx > 0 ? (1.f - dx) * rcp_(Dxs) : (kx < 0 ? -dx * rcp_(Dxs) : 2.f);
   const float sy = ky > 0 ? (1.f - dy) * rcp_(Dys) : (ky < 0 ? -dy * rcp_(Dys) : 2.f);
-  const float Xo = kx > 0 ? 1.f : 0.f, Xn = 1.f - Xo;  // boundary in old / new x frame
+  const float Xo = kx > 0 ? 1.f : 0.f, Xn = 1.f - Xo;  // crossed x line in the old / new x frame
   const float Yo = ky > 0 ? 1.f : 0.f, Yn = 1.f - Yo;
-  if (kx == 0 && ky == 0) {
-    vb_seg(w, scale, ci, cj, dx, dy, nx, ny);
-  } else if (ky == 0) {
-    const float yc = clamp01(dy + sx * Dys);
-    vb_seg(w, scale, ci, cj, dx, dy, Xo, yc);
-    vb_seg(w, scale, ci + kx, cj, Xn, yc, nx, ny);
-  } else if (kx == 0) {
-    const float xc = clamp01(dx + sy * Dxs);
-    vb_seg(w, scale, ci, cj, dx, dy, xc, Yo);
-    vb_seg(w, scale, ci, cj + ky, xc, Yn, nx, ny);
-  } else if (sx <= sy) {
-    const float y1 = clamp01(dy + sx * Dys);           // old y frame
-    const float x2c = clamp01(nx - (1.f - sy) * Dxs);  // new x frame
-    vb_seg(w, scale, ci, cj, dx, dy, Xo, y1);
-    vb_seg(w, scale, ci + kx, cj, Xn, y1, x2c, Yo);
-    vb_seg(w, scale, ci + kx, cj + ky, x2c, Yn, nx, ny);
+  const bool xfirst = sx <= sy;
+  // first crossing point, in the frame of the cell the path leaves
+  float c1x, c1y;
+  if (xfirst) { c1x = kx ? Xo : nx; c1y = kx ? clamp01(dy + sx * Dys) : ny; }
+  else        { c1y = Yo; c1x = clamp01(dx + sy * Dxs); }
+  // cell of the middle segment and the entry point there
+  const int mi = ci + (xfirst ? kx : 0), mj = cj + (xfirst ? 0 : ky);
+  const float e1x = (xfirst && kx) ? Xn : c1x, e1y = (!xfirst) ? Yn : c1y;
+  // second crossing point, in the frame of the middle cell
+  float c2x, c2y;
+  if (kx && ky) {
+    if (xfirst) { c2y = Yo; c2x = clamp01(nx - (1.f - sy) * Dxs); }
+    else        { c2x = Xo; c2y = clamp01(ny - (1.f - sx) * Dys); }
   } else {
-    const float x1c = clamp01(dx + sy * Dxs);          // old x frame
-    const float y2c = clamp01(ny - (1.f - sx) * Dys);  // new y frame
-    vb_seg(w, scale, ci, cj, dx, dy, x1c, Yo);
-    vb_seg(w, scale, ci, cj + ky, x1c, Yn, Xo, y2c);
-    vb_seg(w, scale, ci + kx, cj + ky, Xn, y2c, nx, ny);
+    c2x = nx; c2y = ny;
   }
+  const float e2x = (kx && ky && !xfirst) ? Xn : c2x, e2y = (kx && ky && xfirst) ? Yn : c2y;
+  vb_seg(w, scale, ci, cj, dx, dy, c1x, c1y);
+  vb_seg(w, scale, mi, mj, e1x, e1y, c2x, c2y);
+  vb_seg(w, scale, ci + kx, cj + ky, e2x, e2y, nx, ny);
   // azimuthal flux: charge crossing the meridional half-plane, qw dphi / 2 pi,
   // area weights at the midpoint of the grid path
   {
@@ -292,8 +293,16 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   return true;
 }
 
+// the rare path (particle outside its tile's window) kept out of line so the
+// hot loop's code stays small
+__device__ __noinline__ bool step32_global(const Args32 &A, uint32_t &cell, float &dx, float &dy, float &ur,
+                                           float &ut, float &up, const float qw) {
+  const GlobAcc gw{&A};
+  return step32(A, gw, cell, dx, dy, ur, ut, up, qw);
+}
+
 __device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, const SmemAcc &sw,
-                               const GlobAcc &gw, int wi_lo, int wi_hi, int wj_lo, int wj_hi, int &dead) {
+                               int wi_lo, int wi_hi, int wj_lo, int wj_hi, int &dead) {
   const float qw = P.qw[k];
   if (qw == 0.f) return;
   uint32_t cell = P.cell[k];
@@ -301,7 +310,7 @@ __device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, 
   const int ci = (int)(cell >> 16) - CELL_BIAS, cj = (int)(cell & 0xffffu);
   bool alive;
   if (win && ci >= wi_lo && ci < wi_hi && cj >= wj_lo && cj < wj_hi) alive = step32(A, sw, cell, dx, dy, ur, ut, up, qw);
-  else alive = step32(A, gw, cell, dx, dy, ur, ut, up, qw);
+  else alive = step32_global(A, cell, dx, dy, ur, ut, up, qw);
   if (!alive) { P.qw[k] = 0.f; ++dead; return; }
   P.cell[k] = cell;
   P.dx[k] = dx; P.dy[k] = dy;
@@ -313,7 +322,6 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
   __shared__ int shi[3 * WN];
   __shared__ int slo[3 * WN];
   __shared__ int sdead;
-  const GlobAcc gw{&A};
   int dead = 0;
   if (blockIdx.x < (unsigned)A.ntiles) {
     const int t = blockIdx.x;
@@ -332,7 +340,7 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
     __syncthreads();
     const SmemAcc sw{sf, shi, slo, wi0, wj0};
     for (int64_t k = b0 + threadIdx.x; k < b1; k += NT)
-      process(A, P, k, true, sw, gw, i0 - H, i0 + TI + H, j0 - H, j0 + TJ + H, dead);
+      process(A, P, k, true, sw, i0 - H, i0 + TI + H, j0 - H, j0 + TJ + H, dead);
     if (dead) atomicAdd(&sdead, dead);
     __syncthreads();
     for (int e = threadIdx.x; e < WN; e += NT) {
@@ -349,7 +357,7 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
   } else {  // particles outside any bin (injected since the last sort)
     const SmemAcc none{nullptr, nullptr, nullptr, 0, 0};
     const int64_t k = A.sorted_end + (int64_t)(blockIdx.x - A.ntiles) * NT + threadIdx.x;
-    if (k < A.n_used) process(A, P, k, false, none, gw, 0, 0, 0, 0, dead);
+    if (k < A.n_used) process(A, P, k, false, none, 0, 0, 0, 0, dead);
     if (dead) add_ll(A.cnt + CNT_DELETED, dead);
   }
 }

@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/picsar.h"
+#include "picsar.h"  // include/ is on the include path
 #include "pic_common.cuh"
 
 namespace pic {
