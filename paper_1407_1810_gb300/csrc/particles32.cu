@@ -293,9 +293,9 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   return true;
 }
 
-// the rare path (particle outside its tile's window) kept out of line so the
-// hot loop's code stays small
-__device__ __noinline__ bool step32_global(const Args32 &A, uint32_t &cell, float &dx, float &dy, float &ur,
+// the rare path: a particle outside its tile's window (inlined: an
+// out-of-line call costs register spills around it in the hot loop)
+__device__ inline bool step32_global(const Args32 &A, uint32_t &cell, float &dx, float &dy, float &ur,
                                            float &ut, float &up, const float qw) {
   const GlobAcc gw{&A};
   return step32(A, gw, cell, dx, dy, ur, ut, up, qw);
