@@ -40,6 +40,11 @@ struct Args32 {
   int nr, nth, n_filt, PI, PJ, LD;
   int r_log, th_ea, vacuum, pusher;
   float dxi, inv_dxi, dt, qm, inv_nth, nth_f;
+  // constants carried as FP32 hi + lo pairs: a constant rounded once to FP32
+  // would bias every particle's step the same way (a systematic error that
+  // grows linearly with the step count)
+  float dt_lo, inv_dxi_lo, k2_hi, k2_lo;  // k2 = nth / pi (linear theta map)
+  float b0_lo, qmdt;     // qmdt = (q/m) dt rounded once
   float fscale;             // 2^KFIX / qref: float contribution -> int64 units
   const float *r_n;         // f_r(i) per padded row (FP32)
   const float *f[6];        // FP32 field copies (padded)
@@ -171,6 +176,10 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
     float E[3], B[3];
     const Vac<float> V{A.vacuum, A.b0, A.r_min, A.omega_t};
     vacuum_field<float>(V, r, st, ct, ci < 0, E, B);
+    if (A.vacuum == 1 || A.vacuum == 2) {  // monopole B_r = b0 (r0/r)^2 with b0 to ~1e-14
+      const float q = A.r_min * rcp_(r);
+      B[0] = fmaf(A.b0_lo, q * q, B[0]);
+    }
     if (ci >= 0) {  // plasma field only outside the inner conductor
       const bool hx = dx >= 0.5f, hy = dy >= 0.5f;
       const int ih = hx ? ci : ci - 1, jh = hy ? cj : cj - 1;
@@ -185,16 +194,18 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
     float u[3] = {ur, ut, up};
     // local (r, th, ph) is a right-handed orthonormal frame: the Cartesian
     // push formulas apply to its components unchanged
-    push<float>(A.pusher, qw > 0.f ? A.qm * A.dt : -A.qm * A.dt, E, B, u);
+    push<float>(A.pusher, qw > 0.f ? A.qmdt : -A.qmdt, E, B, u);
     ur = u[0]; ut = u[1]; up = u[2];
   }
   // ---- move in the local frame (Sec. 3.3) -----------------------------------
   const float ig = rsqrt_(1.f + ur * ur + ut * ut + up * up);
-  const float Dr = ur * ig * A.dt, Dt = ut * ig * A.dt, Dp = up * ig * A.dt;
+  const float vr = ur * ig, vt = ut * ig, vp = up * ig;
+  const float Dr = fmaf(vr, A.dt, vr * A.dt_lo), Dt = fmaf(vt, A.dt, vt * A.dt_lo), Dp = fmaf(vp, A.dt, vp * A.dt_lo);
   const float ir = rcp_(r);
   const float a = Dr * ir, b = Dt * ir, c = Dp * ir;
   const float s = a * (2.f + a) + b * b + c * c;  // (r'/r)^2 - 1
-  const float D1 = A.r_log ? 0.5f * log1p_small(s) * A.inv_dxi : r * s * rcp_(1.f + sqrtf(1.f + s)) * A.inv_dxi;
+  const float L1 = A.r_log ? 0.5f * log1p_small(s) : r * s * rcp_(1.f + sqrtf(1.f + s));
+  const float D1 = fmaf(L1, A.inv_dxi, L1 * A.inv_dxi_lo);
   const float p = r + Dr, q = Dt;
   const float Px = p * st + q * ct, Pz = p * ct - q * st;  // displaced point, (R, z) before rotating back
   const float Rn = sqrtf(Px * Px + Dp * Dp);
@@ -206,7 +217,7 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
     sincosf(0.5f * dth, &sh, &ch);
     D2 = A.nth_f * (st * ch + ct * sh) * sh;
   } else {
-    D2 = dth * A.nth_f * 0.31830988618379067f;
+    D2 = fmaf(dth, A.k2_hi, dth * A.k2_lo);
   }
   // new cell and offsets (carries are exact integers)
   float tx = dx + D1, ty = dy + D2;
@@ -480,6 +491,10 @@ Args32 make_args(pic_ctx *c, double t) {
   A.r_log = G.r_map == PIC_R_LOG; A.th_ea = G.th_map == PIC_TH_EQUAL_AREA;
   A.vacuum = G.vacuum; A.pusher = G.pusher;
   A.dxi = (float)G.dxi; A.inv_dxi = (float)(1.0 / G.dxi); A.dt = (float)G.dt; A.qm = (float)G.qm;
+  A.dt_lo = (float)(G.dt - (double)A.dt);
+  A.inv_dxi_lo = (float)(1.0 / G.dxi - (double)A.inv_dxi);
+  A.k2_hi = (float)(G.nth / M_PI);
+  A.k2_lo = (float)(G.nth / M_PI - (double)A.k2_hi);
   A.inv_nth = (float)(1.0 / G.nth); A.nth_f = (float)G.nth;
   A.fscale = (float)(1.0 / c->flux_quantum);  // a power of two: the scaling is exact
   A.r_n = c->r_n32;
@@ -492,6 +507,8 @@ Args32 make_args(pic_ctx *c, double t) {
   A.sorted_end = c->tiles.sorted_end;
   A.n_used = c->n_used;
   A.b0 = (float)G.b0; A.r_min = (float)G.r_min;
+  A.b0_lo = (float)(G.b0 - (double)A.b0);
+  A.qmdt = (float)(G.qm * G.dt);
   A.omega_t = (float)omega_at(G.omega, G.t_spin, t);
   return A;
 }
