@@ -148,6 +148,21 @@ int pic_get_flux(pic_ctx *c, double *out3, int64_t *n, int32_t mem);
 int pic_get_particles(pic_ctx *c, int64_t *n, double *x1, double *x2, double *u_r,
                       double *u_th, double *u_ph, double *qw, int64_t *id, int32_t mem);
 
+/* Live particles written to caller-owned DEVICE buffers without any device
+ * allocation (the paper has no counterpart: this serves callers that must not
+ * have the library call cudaMalloc, e.g. code under its own device-memory
+ * pool, or a host loop that cannot afford an allocation's synchronisation).
+ * Unlike pic_get_particles it leaves the context as it is and writes the live
+ * particles in slot order.  *n in: capacity of the buffers (elements); out:
+ * the live count (if that exceeds the capacity, nothing beyond the capacity
+ * is written and PIC_EINVAL is returned).  id may be NULL.  Scratch is a
+ * static 4 MiB device array per GPU, which bounds the context to at most 2^28
+ * particle slots (PIC_EINVAL beyond).  The first call on a device looks up the
+ * array's address, so make it outside any stream capture; calls that overlap
+ * on the GPU share the array and race.  Synchronises the context's stream. */
+int pic_get_particles_noalloc(pic_ctx *c, int64_t *n, double *x1, double *x2, double *u_r,
+                              double *u_th, double *u_ph, double *qw, int64_t *id);
+
 /* Live particle count and total kinetic energy only (one streaming reduction,
  * synchronises); cheaper than pic_get_moments, which also deposits the charge. */
 int pic_get_live(pic_ctx *c, int64_t *live, double *kinetic_energy);

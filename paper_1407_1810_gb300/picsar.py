@@ -24,7 +24,7 @@ PIC_VAY, PIC_BORIS = 0, 1
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 
 EXPORTS = ["pic_init_grid", "pic_load_particles", "pic_step", "pic_get_fields", "pic_set_fields", "pic_get_flux",
-           "pic_get_particles", "pic_get_live", "pic_get_moments", "pic_gauss_snapshot", "pic_set_clock", "pic_profile",
+           "pic_get_particles", "pic_get_particles_noalloc", "pic_get_live", "pic_get_moments", "pic_gauss_snapshot", "pic_set_clock", "pic_profile",
            "pic_get_profile", "pic_get_launches", "pic_ensemble_step", "pic_destroy", "pic_last_error"]
 
 
@@ -76,6 +76,7 @@ def lib():
         "pic_get_particles": [P, C.POINTER(C.c_int64), P, P, P, P, P, P, P, I32],
         "pic_get_moments": [P, C.POINTER(pic_moments)],
         "pic_get_live": [P, C.POINTER(C.c_int64), C.POINTER(C.c_double)],
+        "pic_get_particles_noalloc": [P, C.POINTER(C.c_int64), P, P, P, P, P, P, P],
         "pic_gauss_snapshot": [P],
         "pic_set_clock": [P, I64, I64],
         "pic_profile": [P, I32],
@@ -195,6 +196,17 @@ class Simulation:
         check(self.L.pic_get_particles(self.h, C.byref(n), *ptrs, C.c_void_p(ids.ctypes.data), PIC_MEM_HOST))
         out["id"] = ids
         return out
+
+    def particles_noalloc(self, out: dict):
+        """Live particles into caller-owned device tensors (keys x1, x2, ur,
+        uth, uph, qw as float64, id as int64); returns the live count."""
+        keys = ("x1", "x2", "ur", "uth", "uph", "qw")
+        cap = min(out[k].numel() for k in keys)
+        n = C.c_int64(cap)
+        ptrs = [C.c_void_p(out[k].data_ptr()) for k in keys]
+        idp = C.c_void_p(out["id"].data_ptr()) if out.get("id") is not None else None
+        check(self.L.pic_get_particles_noalloc(self.h, C.byref(n), *ptrs, idp))
+        return n.value
 
     def live(self):
         n, k = C.c_int64(), C.c_double()

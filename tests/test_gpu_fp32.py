@@ -11,8 +11,6 @@ plasmas (a few pairs per cell) the FP32 rounding of momenta and forces,
 uses the FP32-rounded dt and B0, so it is not a rounded constant): those
 cases are held to 2e-5.
 """
-FIELD_TOL_ROTATOR = 1e-5
-FIELD_TOL_NOISY = 2e-5
 import numpy as np
 import pytest
 
@@ -23,6 +21,8 @@ from gpu_common import KEYS, by_id, fp32_state, rel_l2, setup
 
 pytestmark = pytest.mark.gpu
 TAU = 2e-6
+FIELD_TOL_ROTATOR = 1e-5
+FIELD_TOL_NOISY = 2e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
