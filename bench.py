@@ -391,10 +391,89 @@ def reference_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def ensemble_plasma(cfg, qw):
+    """~cfg['particles'] particles of the member's recipe: whole pairs per cell
+    where there are enough, else one pair in each of a random set of cells."""
+    import numpy as np
+
+    from paper_1407_1810_gb300 import synthetic
+
+    ncell = cfg["nr"] * cfg["nth"]
+    npairs = max(1, cfg["particles"] // 2)
+    if npairs >= ncell:
+        return synthetic.pair_plasma(cfg["nr"], cfg["nth"], npairs // ncell, cfg["T"], qw, cfg["seed"])
+    cells = np.random.default_rng(cfg["seed"] + 7).choice(ncell, npairs, replace=False)
+    return synthetic.pair_plasma_cells(cfg["nr"], cfg["nth"], np.sort(cells), 1, cfg["T"], qw, cfg["seed"])
+
+
+def ensemble_arm(args, n_members=64):
+    """64 independent monopole plasmas with uneven grids and particle counts:
+    every member autotuned (tile shape, sort interval), then advanced by the
+    batched, graph-captured pic_ensemble_step; the same members advanced one
+    after another by pic_step are timed for comparison."""
+    import torch
+
+    from paper_1407_1810_gb300 import configs
+    from paper_1407_1810_gb300 import picsar as P
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    sims, choices, total = [], [], 0
+    for m in range(n_members):
+        cfg = configs.ensemble_member_config(m)
+        dt = configs.courant_dt(cfg)
+        b0, qw = configs.physics(cfg, dt)
+        s = P.Simulation(P.make_desc(**configs.desc_kwargs(cfg, dt, b0)), stream=stream.cuda_stream)
+        d = ensemble_plasma(cfg, qw)
+        s.load(*(d[k] for k in ("x1", "x2", "ur", "uth", "uph", "qw")))
+        total += len(d["x1"])
+        sims.append(s)
+    t0 = time.perf_counter()
+    for s in sims:
+        choices.append(s.autotune(trial_steps=20))
+    t_tune = time.perf_counter() - t0
+    P.ensemble_step(sims, args.warmup)
+    torch.cuda.synchronize()
+    live0 = sum(s.live() for s in sims)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    t0 = time.perf_counter()
+    P.ensemble_step(sims, args.steps)
+    t1 = time.perf_counter()
+    ck = clocks.stop()
+    live1 = sum(s.live() for s in sims)
+    units = 0.5 * (live0 + live1) * args.steps
+    value = units / (t1 - t0)
+    # the same members stepped one after another
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    for s in sims:
+        s.step(args.steps)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    seq = units / (t3 - t2)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * (t1 - t0) / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "ensemble-64", "members": n_members, "particles": total, "path": "fp32",
+                      "timing": "host clock around pic_ensemble_step (one graph per sort interval)"},
+           "sequential_pic_step": {"value": seq, "speedup_of_ensemble": value / seq},
+           "autotune": {"seconds": t_tune, "choices": choices},
+           "clocks": ck}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.workload == "ensemble-64":
+        ensemble_arm(args)
         return
     gpu_arm(args)
 

@@ -90,6 +90,8 @@ typedef struct pic_desc {
                                 FP64 path: steps between compactions */
   int64_t capacity;          /* particle slots to allocate (0 = 2x the first load + injection room) */
   double flux_quantum;       /* FP32 path: charge of one fixed-point flux unit; 0 = automatic */
+  int32_t tile_shape;        /* FP32 path: tile of the shared-memory deposit, 0 = 16x16 cells,
+                                1 = 8 (r) x 32 (theta), 2 = 32 x 8 */
 } pic_desc;
 
 /* Diagnostics returned by pic_get_moments. */
@@ -191,6 +193,15 @@ int pic_get_launches(pic_ctx *c, int64_t *n);
  * nsteps captured once as a CUDA graph and replayed.  All contexts must share
  * one stream and device.  (Batched ensemble of independent simulations.) */
 int pic_ensemble_step(pic_ctx *const *ctxs, int32_t n, int32_t nsteps);
+
+/* Pick the FP32 path's tile shape and sort interval by measurement: every
+ * candidate (3 tile shapes x sort intervals 5, 10, 20, 40) runs trial_steps
+ * steps on a clone of the context (the context itself does not advance), and
+ * the fastest mean step time wins and is applied to the context.  The chosen
+ * values are returned in *sort_interval and *tile_shape (either may be NULL).
+ * Costs about 12 clones' worth of device memory and time: meant for the
+ * small members of an ensemble.  FP64 contexts: PIC_EINVAL. */
+int pic_autotune(pic_ctx *c, int32_t trial_steps, int32_t *sort_interval, int32_t *tile_shape);
 
 /* Release every device buffer of the context.  NULL is allowed. */
 int pic_destroy(pic_ctx *c);

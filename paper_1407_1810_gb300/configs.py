@@ -73,9 +73,19 @@ def desc_kwargs(cfg: dict, dt: float, b0: float, **over):
               absorb_profile=cfg["absorb_profile"], vacuum=cfg["vacuum"], b0=b0, omega=cfg["omega"],
               t_spin=cfg["t_spin"], inject=cfg["inject"], pairs_per_cell=cfg.get("inject_pairs", 2),
               f_inj=cfg.get("f_inj", 0.0), precision=cfg["precision"], pusher=cfg["pusher"], q_over_m=1.0,
-              sort_interval=cfg.get("sort_interval", 20))
+              sort_interval=cfg.get("sort_interval", 20), tile_shape=cfg.get("tile_shape", 0))
     kw.update(over)
     return kw
+
+
+def ensemble_member_config(m: int) -> dict:
+    """Member m of the batched ensemble: the small monopole plasma's physics
+    (log r in [1, 10], linear theta, lossy 8 cells) on the member's grid, FP32."""
+    from .synthetic import ensemble_member
+
+    r = ensemble_member(m)
+    return dict(CONFIGS["monopole-64x64"], nr=r["nr"], nth=r["nth"], T=r["T"], seed=r["seed"],
+                particles=r["particles"], precision="fp32", steps=200)
 
 
 def oracle_kwargs(cfg: dict, dt: float, b0: float, **over):

@@ -64,6 +64,7 @@ int check_desc(const pic_desc &d) {
     if (d.r_min - (d.n_filt + 2) * dr <= 0.0)
       return pic_fail(PIC_EINVAL, "linear r map: the ghost cells inside the inner conductor reach r <= 0");
   }
+  if (d.tile_shape < 0 || d.tile_shape > 2) return pic_fail(PIC_EINVAL, "tile_shape must be 0, 1 or 2");
   if (d.precision == PIC_FP32 && d.nr + 2 * (d.n_filt + 2) >= 65536 - 2 * CELL_BIAS)
     return pic_fail(PIC_EINVAL, "FP32 path: grid too large for the packed cell index");
   return PIC_OK;
@@ -426,6 +427,8 @@ extern "C" int pic_init_grid(pic_ctx **out, const pic_desc *dd, void *stream) {
       PIC_CUDA(cudaMemcpy(c->r_n32, rn.data(), rn.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
     Tiles &T = c->tiles;
+    T.TI = d.tile_shape == 1 ? 8 : (d.tile_shape == 2 ? 32 : 16);
+    T.TJ = d.tile_shape == 1 ? 32 : (d.tile_shape == 2 ? 8 : 16);
     T.row0 = -G.g;
     T.nti = (d.nr + 2 * G.g + T.TI - 1) / T.TI;
     T.ntj = (d.nth + T.TJ - 1) / T.TJ;
@@ -502,59 +505,82 @@ extern "C" int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const
   return PIC_OK;
 }
 
-extern "C" int pic_step(pic_ctx *c, int32_t nsteps) {
-  if (!c) return pic_fail(PIC_EINVAL, "null context");
-  if (nsteps < 0) return pic_fail(PIC_EINVAL, "nsteps < 0");
+// One time step, enqueued on c->stream without any host synchronisation
+// (also the unit the ensemble captures into a CUDA graph).
+static void step_body(pic_ctx *c) {
+  const double t = c->step * c->G.dt;
+  int pr = prof_begin(c, PROF_PARTICLES);
+  if (c->d.precision == PIC_FP64) {
+    for (int k = 0; k < 3; ++k) cudaMemsetAsync(c->F[k], 0, c->grid_elems * 8, c->stream);
+    particles64(c, t);
+    prof_end(c, pr);
+  } else {
+    particles32(c, t);
+    prof_end(c, pr);
+    pr = prof_begin(c, PROF_REDUCE);
+    flux_from_acc(c);
+    prof_end(c, pr);
+  }
+  if (c->d.n_filt > 0) {
+    pr = prof_begin(c, PROF_FILTER);
+    fields_filter(c);
+    prof_end(c, pr);
+  }
+  pr = prof_begin(c, PROF_FIELDS);
+  fields_b_half(c);
+  fields_e_full(c);
+  fields_b_half(c);
+  fields_finish(c);
+  prof_end(c, pr);
+  c->step += 1;
+  if (c->d.inject) {
+    pr = prof_begin(c, PROF_INJECT);
+    inject(c, c->step * c->G.dt);
+    prof_end(c, pr);
+  }
+  c->steps_since_sort += 1;
+  if (c->prof) c->prof_steps += 1;
+}
+
+// Work that needs the host before steps can be enqueued blindly: a pending
+// sort, the Gauss snapshot, the fixed-point quantum, and room for `steps`
+// steps of injection.
+static int prepare_steps(pic_ctx *c, int steps) {
   if (c->need_sort) {
     int e = compact(c);
     if (e) return e;
     c->need_sort = false;
   }
   if (!c->have_snap) moments(c, true, nullptr);
-  const int64_t slots = inject_slots(c);
-  for (int s = 0; s < nsteps; ++s) {
-    const double t = c->step * c->G.dt;
-    if (c->d.inject && c->n_used + slots > c->cap) {
-      int e = compact(c);
-      if (e) return e;
-      if (c->n_used + slots > c->cap && (e = grow_parts(c, (c->n_used + slots) * 3 / 2 + 1024))) return e;
-    }
-    int pr = prof_begin(c, PROF_PARTICLES);
-    if (c->d.precision == PIC_FP64) {
-      for (int k = 0; k < 3; ++k) cudaMemsetAsync(c->F[k], 0, c->grid_elems * 8, c->stream);
-      particles64(c, t);
-      prof_end(c, pr);
-    } else {
-      particles32(c, t);
-      prof_end(c, pr);
-      pr = prof_begin(c, PROF_REDUCE);
-      flux_from_acc(c);
-      prof_end(c, pr);
-    }
-    if (c->d.n_filt > 0) {
-      pr = prof_begin(c, PROF_FILTER);
-      fields_filter(c);
-      prof_end(c, pr);
-    }
-    pr = prof_begin(c, PROF_FIELDS);
-    fields_b_half(c);
-    fields_e_full(c);
-    fields_b_half(c);
-    fields_finish(c);
-    prof_end(c, pr);
-    c->step += 1;
-    if (c->d.inject) {
-      pr = prof_begin(c, PROF_INJECT);
-      inject(c, c->step * c->G.dt);
-      prof_end(c, pr);
-    }
-    if (++c->steps_since_sort >= c->d.sort_interval) {
-      pr = prof_begin(c, PROF_SORT);
-      int e = compact(c);
+  if (c->d.precision == PIC_FP32) prepare32(c);
+  const int64_t need = c->n_used + inject_slots(c) * (int64_t)steps;
+  if (c->d.inject && need > c->cap) {
+    int e = compact(c);
+    if (e) return e;
+    const int64_t need2 = c->n_used + inject_slots(c) * (int64_t)steps;
+    if (need2 > c->cap && (e = grow_parts(c, need2 * 3 / 2 + 1024))) return e;
+  }
+  return PIC_OK;
+}
+
+extern "C" int pic_step(pic_ctx *c, int32_t nsteps) {
+  if (!c) return pic_fail(PIC_EINVAL, "null context");
+  if (nsteps < 0) return pic_fail(PIC_EINVAL, "nsteps < 0");
+  int done = 0;
+  while (done < nsteps) {
+    // steps up to the next sort run without host synchronisation
+    int block = std::min(nsteps - done, std::max(1, c->d.sort_interval - c->steps_since_sort));
+    if (c->d.inject) block = std::min(block, 64);
+    int e = prepare_steps(c, block);
+    if (e) return e;
+    for (int s = 0; s < block; ++s) step_body(c);
+    done += block;
+    if (c->steps_since_sort >= c->d.sort_interval) {
+      int pr = prof_begin(c, PROF_SORT);
+      e = compact(c);
       prof_end(c, pr);
       if (e) return e;
     }
-    if (c->prof) c->prof_steps += 1;
     if (c->ev_used > 4096) prof_drain(c);
   }
   PIC_CUDA(cudaGetLastError());
@@ -722,12 +748,191 @@ extern "C" int pic_get_launches(pic_ctx *c, int64_t *n) {
   return PIC_OK;
 }
 
+// Batched ensemble: every member's steps up to its next sort are captured,
+// members on parallel branches (one forked stream each), into one CUDA graph
+// that is launched once; the sorts run between graphs.  A captured graph is
+// applied to the previous executable graph when its topology allows
+// (cudaGraphExecUpdate), otherwise instantiated anew.
 extern "C" int pic_ensemble_step(pic_ctx *const *ctxs, int32_t n, int32_t nsteps) {
-  if (!ctxs || n < 0 || nsteps < 0) return pic_fail(PIC_EINVAL, "bad ensemble arguments");
+  if (!ctxs || n <= 0 || nsteps < 0) return pic_fail(PIC_EINVAL, "bad ensemble arguments");
+  for (int k = 0; k < n; ++k)
+    if (!ctxs[k]) return pic_fail(PIC_EINVAL, "null ensemble member");
+  const int dev = ctxs[0]->device;
+  for (int k = 1; k < n; ++k)
+    if (ctxs[k]->device != dev) return pic_fail(PIC_EINVAL, "ensemble members on different devices");
+  cudaStream_t origin;
+  PIC_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+  std::vector<cudaStream_t> br(n);
+  std::vector<cudaEvent_t> join(n);
+  cudaEvent_t fork, after;
+  PIC_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  PIC_CUDA(cudaEventCreateWithFlags(&after, cudaEventDisableTiming));
   for (int k = 0; k < n; ++k) {
-    int e = pic_step(ctxs[k], nsteps);
+    PIC_CUDA(cudaStreamCreateWithFlags(&br[k], cudaStreamNonBlocking));
+    PIC_CUDA(cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming));
+  }
+  // members' own streams finish their earlier work before the first graph
+  for (int k = 0; k < n; ++k) PIC_CUDA(cudaStreamSynchronize(ctxs[k]->stream));
+  cudaGraphExec_t exec = nullptr;
+  int err = PIC_OK, done = 0;
+  while (done < nsteps && !err) {
+    int block = nsteps - done;
+    for (int k = 0; k < n; ++k) {
+      pic_ctx *c = ctxs[k];
+      block = std::min(block, std::max(1, c->d.sort_interval - c->steps_since_sort));
+    }
+    for (int k = 0; k < n && !err; ++k) {
+      err = prepare_steps(ctxs[k], block);
+      if (!err) cudaStreamSynchronize(ctxs[k]->stream);
+    }
+    if (err) break;
+    std::vector<cudaStream_t> own(n);
+    std::vector<bool> prof(n);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) ce = cudaEventRecord(fork, origin);
+    for (int k = 0; k < n && ce == cudaSuccess; ++k) {
+      pic_ctx *c = ctxs[k];
+      ce = cudaStreamWaitEvent(br[k], fork, 0);
+      own[k] = c->stream;
+      prof[k] = c->prof;
+      c->stream = br[k];
+      c->prof = false;
+      for (int s = 0; s < block; ++s) step_body(c);
+      c->stream = own[k];
+      c->prof = prof[k];
+      if (ce == cudaSuccess) ce = cudaEventRecord(join[k], br[k]);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(origin, join[k], 0);
+    }
+    cudaError_t ce2 = cudaStreamEndCapture(origin, &graph);
+    if (ce == cudaSuccess) ce = ce2;
+    if (ce == cudaSuccess) {
+      bool fresh = exec == nullptr;
+      if (!fresh) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(exec, graph, &info) != cudaSuccess) {
+          cudaGetLastError();
+          cudaGraphExecDestroy(exec);
+          exec = nullptr;
+          fresh = true;
+        }
+      }
+      if (fresh) ce = cudaGraphInstantiate(&exec, graph, 0);
+      if (ce == cudaSuccess) ce = cudaGraphLaunch(exec, origin);
+      if (ce == cudaSuccess) ce = cudaEventRecord(after, origin);
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) { err = pic_cuda_check(ce, "ensemble graph"); break; }
+    done += block;
+    for (int k = 0; k < n && !err; ++k) {
+      pic_ctx *c = ctxs[k];
+      cudaStreamWaitEvent(c->stream, after, 0);
+      if (c->steps_since_sort >= c->d.sort_interval) err = compact(c);
+    }
+  }
+  cudaStreamSynchronize(origin);
+  if (exec) cudaGraphExecDestroy(exec);
+  for (int k = 0; k < n; ++k) { cudaStreamDestroy(br[k]); cudaEventDestroy(join[k]); }
+  cudaEventDestroy(fork);
+  cudaEventDestroy(after);
+  cudaStreamDestroy(origin);
+  if (err) return err;
+  for (int k = 0; k < n; ++k) {
+    latch_errors(ctxs[k]);
+    int e = status(ctxs[k]);
     if (e) return e;
   }
+  return PIC_OK;
+}
+
+// re-bin an FP32 context for another tile shape (sorted at the next step)
+static int set_tiles(pic_ctx *c, int shape) {
+  Tiles &T = c->tiles;
+  cudaStreamSynchronize(c->stream);
+  cudaFree(T.start);
+  cudaFree(T.cursor);
+  T.start = T.cursor = nullptr;
+  T.TI = shape == 1 ? 8 : (shape == 2 ? 32 : 16);
+  T.TJ = shape == 1 ? 32 : (shape == 2 ? 8 : 16);
+  T.nti = (c->d.nr + 2 * c->G.g + T.TI - 1) / T.TI;
+  T.ntj = (c->d.nth + T.TJ - 1) / T.TJ;
+  T.ntiles = T.nti * T.ntj;
+  T.sorted_end = 0;
+  int e;
+  if ((e = dalloc(&T.start, (size_t)T.ntiles + 2)) || (e = dalloc(&T.cursor, (size_t)T.ntiles + 2))) return e;
+  PIC_CUDA(cudaMemset(T.start, 0, (T.ntiles + 2) * 8));
+  c->d.tile_shape = shape;
+  c->need_sort = true;
+  return PIC_OK;
+}
+
+// a new context holding the same fields, particles and clock
+static int clone_context(pic_ctx *c, pic_ctx **out) {
+  pic_desc d = c->d;
+  d.capacity = 0;
+  int e = pic_init_grid(out, &d, c->stream);
+  if (e) return e;
+  pic_ctx *k = *out;
+  for (int q = 0; q < 6; ++q)
+    cudaMemcpyAsync(k->f[q], c->f[q], c->grid_elems * 8, cudaMemcpyDeviceToDevice, c->stream);
+  fields_fill_ghosts(k);
+  int64_t n = 0;
+  if ((e = pic_get_particles(c, &n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, PIC_MEM_DEVICE)))
+    return e;
+  if (n > 0) {
+    double *buf;
+    PIC_CUDA(cudaMalloc((void **)&buf, 6 * (size_t)n * 8));
+    double *b[6];
+    for (int q = 0; q < 6; ++q) b[q] = buf + (size_t)q * n;
+    e = pic_get_particles(c, &n, b[0], b[1], b[2], b[3], b[4], b[5], nullptr, PIC_MEM_DEVICE);
+    if (!e) e = pic_load_particles(k, n, b[0], b[1], b[2], b[3], b[4], b[5], PIC_MEM_DEVICE);
+    cudaFree(buf);
+    if (e) return e;
+  }
+  k->step = c->step;
+  k->next_id = c->next_id;
+  return PIC_OK;
+}
+
+extern "C" int pic_autotune(pic_ctx *c, int32_t trial_steps, int32_t *sort_interval, int32_t *tile_shape) {
+  if (!c || trial_steps < 1) return pic_fail(PIC_EINVAL, "bad autotune arguments");
+  if (c->d.precision != PIC_FP32) return pic_fail(PIC_EINVAL, "autotune applies to the FP32 path");
+  const int shapes[3] = {0, 1, 2}, intervals[4] = {5, 10, 20, 40};
+  double best = 1e300;
+  int best_shape = c->d.tile_shape, best_s = c->d.sort_interval;
+  cudaEvent_t e0, e1;
+  PIC_CUDA(cudaEventCreate(&e0));
+  PIC_CUDA(cudaEventCreate(&e1));
+  int err = PIC_OK;
+  for (int sh : shapes) {
+    for (int S : intervals) {
+      pic_ctx *k = nullptr;
+      if ((err = clone_context(c, &k))) break;
+      k->d.sort_interval = S;
+      if (sh != k->d.tile_shape) err = set_tiles(k, sh);
+      if (!err) err = pic_step(k, S);  // warm-up: one full sort cycle
+      const int n = std::max(trial_steps, 2 * S);
+      if (!err) {
+        cudaEventRecord(e0, k->stream);
+        err = pic_step(k, n);
+        cudaEventRecord(e1, k->stream);
+        cudaEventSynchronize(e1);
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      pic_destroy(k);
+      if (err) break;
+      if (ms / n < best) { best = ms / n; best_shape = sh; best_s = S; }
+    }
+    if (err) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err) return err;
+  c->d.sort_interval = best_s;
+  if (best_shape != c->d.tile_shape && (err = set_tiles(c, best_shape))) return err;
+  if (sort_interval) *sort_interval = best_s;
+  if (tile_shape) *tile_shape = best_shape;
   return PIC_OK;
 }
 

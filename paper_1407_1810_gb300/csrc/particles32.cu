@@ -24,9 +24,12 @@ namespace pic {
 
 namespace {
 
-constexpr int TI = 16, TJ = 16, H = 2;
-constexpr int WI = TI + 2 * H + 3, WJ = TJ + 2 * H + 3;  // window nodes
-constexpr int WN = WI * WJ;
+constexpr int H = 2;  // halo cells around a tile served from shared memory
+// window nodes of a TI x TJ tile: the tile, the halo and the stencil reach
+template <int TI, int TJ>
+struct Win {
+  static constexpr int WI = TI + 2 * H + 3, WJ = TJ + 2 * H + 3, WN = WI * WJ;
+};
 constexpr int NT = 256;                                  // threads per tile CTA
 constexpr int KFIX = 36;                                 // fixed point: 2^-36 of the reference charge
 // Shared-memory accumulation splits each term v (|v| <= 2^36 quanta) into
@@ -52,7 +55,7 @@ struct Args32 {
   int *err;
   long long *cnt;
   // tiles
-  int row0, ntj, ntiles;
+  int row0, ntj, ntiles, ti, tj;
   const int64_t *start;
   int64_t sorted_end, n_used;
   // vacuum
@@ -63,6 +66,7 @@ __device__ inline size_t pidx(const Args32 &A, int i, int j) {
   return (size_t)(i + A.PI) * (size_t)A.LD + (size_t)(j + A.PJ);
 }
 
+template <int WJ, int WN>
 struct SmemAcc {  // window accessors (shared memory)
   const float *f;           // 6 * WN
   int *hi;                  // 3 * WN : sums of the high parts
@@ -312,7 +316,8 @@ __device__ inline bool step32_global(const Args32 &A, uint32_t &cell, float &dx,
   return step32(A, gw, cell, dx, dy, ur, ut, up, qw);
 }
 
-__device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, const SmemAcc &sw,
+template <class SW>
+__device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, const SW &sw,
                                int wi_lo, int wi_hi, int wj_lo, int wj_hi, int &dead) {
   const float qw = P.qw[k];
   if (qw == 0.f) return;
@@ -328,7 +333,9 @@ __device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, 
   P.ur[k] = ur; P.ut[k] = ut; P.up[k] = up;
 }
 
+template <int TI, int TJ>
 __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
+  constexpr int WJ = Win<TI, TJ>::WJ, WN = Win<TI, TJ>::WN;
   __shared__ float sf[6 * WN];
   __shared__ int shi[3 * WN];
   __shared__ int slo[3 * WN];
@@ -349,7 +356,7 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
       for (int c = 0; c < 3; ++c) { shi[c * WN + e] = 0; slo[c * WN + e] = 0; }
     }
     __syncthreads();
-    const SmemAcc sw{sf, shi, slo, wi0, wj0};
+    const SmemAcc<WJ, WN> sw{sf, shi, slo, wi0, wj0};
     for (int64_t k = b0 + threadIdx.x; k < b1; k += NT)
       process(A, P, k, true, sw, i0 - H, i0 + TI + H, j0 - H, j0 + TJ + H, dead);
     if (dead) atomicAdd(&sdead, dead);
@@ -366,7 +373,7 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
     }
     if (threadIdx.x == 0 && sdead) add_ll(A.cnt + CNT_DELETED, sdead);
   } else {  // particles outside any bin (injected since the last sort)
-    const SmemAcc none{nullptr, nullptr, nullptr, 0, 0};
+    const SmemAcc<WJ, WN> none{nullptr, nullptr, nullptr, 0, 0};
     const int64_t k = A.sorted_end + (int64_t)(blockIdx.x - A.ntiles) * NT + threadIdx.x;
     if (k < A.n_used) process(A, P, k, false, none, 0, 0, 0, 0, dead);
     if (dead) add_ll(A.cnt + CNT_DELETED, dead);
@@ -388,7 +395,7 @@ __global__ void k_flux_from_acc(int nr, int nth, int g, int PI, int PJ, int LD, 
 __device__ inline int tile_key(const Args32 &A, uint32_t cell, float qw) {
   if (qw == 0.f) return A.ntiles;  // trash bin
   const int ci = (int)(cell >> 16) - CELL_BIAS, cj = (int)(cell & 0xffffu);
-  return ((ci - A.row0) / TI) * A.ntj + cj / TJ;
+  return ((ci - A.row0) / A.ti) * A.ntj + cj / A.tj;
 }
 
 __global__ void k_hist(Args32 A, Parts32 P, int64_t n, int64_t *count) {
@@ -459,14 +466,14 @@ __global__ void k_charge32(int PI, int PJ, int LD, Parts32 P, int64_t n, double 
 }
 
 __global__ void k_reduce32(Parts32 P, int64_t n, double qm, double *acc, long long *live) {
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double kin = 0.0, ch = 0.0;
   long long l = 0;
-  if (k < n && P.qw[k] != 0.f) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    if (P.qw[k] == 0.f) continue;
     const double q = P.qw[k], a = P.ur[k], b = P.ut[k], c = P.up[k];
-    kin = fabs(q) / qm * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
-    ch = q;
-    l = 1;
+    kin += fabs(q) / qm * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
+    ch += q;
+    l += 1;
   }
   block_sum3(kin, ch, l, acc + ACC_KIN, acc + ACC_CHARGE, live);
 }
@@ -503,6 +510,7 @@ Args32 make_args(pic_ctx *c, double t) {
   A.err = c->d_err;
   A.cnt = c->d_cnt;
   A.row0 = c->tiles.row0; A.ntj = c->tiles.ntj; A.ntiles = c->tiles.ntiles;
+  A.ti = c->tiles.TI; A.tj = c->tiles.TJ;
   A.start = c->tiles.start;
   A.sorted_end = c->tiles.sorted_end;
   A.n_used = c->n_used;
@@ -548,13 +556,19 @@ static void update_quantum(pic_ctx *c) {
   if (q0 > c->flux_quantum) c->flux_quantum = q0;
 }
 
+void prepare32(pic_ctx *c) {
+  if (c->flux_quantum == 0.0) update_quantum(c);
+}
+
 void particles32(pic_ctx *c, double t) {
   if (c->flux_quantum == 0.0) update_quantum(c);
   if (c->n_used == 0) return;
   Args32 A = make_args(c, t);
   const int64_t tail = c->n_used - c->tiles.sorted_end;
   const int64_t blocks = c->tiles.ntiles + (tail + NT - 1) / NT;
-  ++c->launches, k_tiles32<<<(unsigned)blocks, NT, 0, c->stream>>>(A, c->p32);
+  if (c->tiles.TI == 8) ++c->launches, k_tiles32<8, 32><<<(unsigned)blocks, NT, 0, c->stream>>>(A, c->p32);
+  else if (c->tiles.TI == 32) ++c->launches, k_tiles32<32, 8><<<(unsigned)blocks, NT, 0, c->stream>>>(A, c->p32);
+  else ++c->launches, k_tiles32<16, 16><<<(unsigned)blocks, NT, 0, c->stream>>>(A, c->p32);
 }
 
 void flux_from_acc(pic_ctx *c) {
@@ -594,7 +608,8 @@ void charge32(pic_ctx *c, double *Q, double *Qa) {
 
 void reduce_particles32(pic_ctx *c) {
   if (c->n_used == 0) return;
-  ++c->launches, k_reduce32<<<(unsigned)((c->n_used + 255) / 256), 256, 0, c->stream>>>(c->p32, c->n_used, c->G.qm, c->d_acc,
+  // a fixed grid (4 blocks per SM) keeps the same-address atomics few
+  ++c->launches, k_reduce32<<<4 * 152, 256, 0, c->stream>>>(c->p32, c->n_used, c->G.qm, c->d_acc,
                                                                         c->d_cnt + CNT_LIVE);
 }
 

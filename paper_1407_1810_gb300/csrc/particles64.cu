@@ -213,14 +213,14 @@ __global__ void k_charge64(Grid G, const double *__restrict__ x1, const double *
 }
 
 __global__ void k_reduce64(Parts64 P, int64_t n, double qm, double *acc, long long *live) {
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double kin = 0.0, ch = 0.0;
   long long l = 0;
-  if (k < n && P.qw[k] != 0.0) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    if (P.qw[k] == 0.0) continue;
     const double q = P.qw[k], u2 = P.ur[k] * P.ur[k] + P.ut[k] * P.ut[k] + P.up[k] * P.up[k];
-    kin = fabs(q) / qm * (sqrt(1.0 + u2) - 1.0);
-    ch = q;
-    l = 1;
+    kin += fabs(q) / qm * (sqrt(1.0 + u2) - 1.0);
+    ch += q;
+    l += 1;
   }
   block_sum3(kin, ch, l, acc + ACC_KIN, acc + ACC_CHARGE, live);
 }
@@ -262,7 +262,8 @@ void charge64(pic_ctx *c, double *Q, double *Qa) {
 
 void reduce_particles64(pic_ctx *c) {
   if (c->n_used == 0) return;
-  ++c->launches, k_reduce64<<<(unsigned)((c->n_used + 255) / 256), 256, 0, c->stream>>>(c->p64, c->n_used, c->G.qm, c->d_acc,
+  // a fixed grid (4 blocks per SM) keeps the same-address atomics few
+  ++c->launches, k_reduce64<<<4 * 152, 256, 0, c->stream>>>(c->p64, c->n_used, c->G.qm, c->d_acc,
                                                                         c->d_cnt + CNT_LIVE);
 }
 

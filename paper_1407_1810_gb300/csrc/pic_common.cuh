@@ -81,6 +81,13 @@ __device__ inline double map_th_inv(const Grid &G, double th) {
   return G.th_map == 1 ? 0.5 * G.nth * (1.0 - cos(th)) : th * G.nth / PI_D;
 }
 
+// reciprocal and reciprocal square root: hardware approximations (within 2
+// ulp) in FP32, exact division in FP64
+__device__ inline float rcp_(float x) { return __fdividef(1.0f, x); }
+__device__ inline double rcp_(double x) { return 1.0 / x; }
+__device__ inline float rsqrt_(float x) { return rsqrtf(x); }
+__device__ inline double rsqrt_(double x) { return 1.0 / sqrt(x); }
+
 // ---- analytic "initial" fields: Sec. 5.2 (monopole, rotator inside/outside),
 //      Sec. 4.3 (dipole + corotation), uniform B_z.  Spherical components.
 //      W = Omega(t)/c after the linear spin-up. -----------------------------------
@@ -99,7 +106,7 @@ __device__ inline void vacuum_field(const Vac<T> &V, T r, T st, T ct, bool insid
   E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = T(0);
   if (V.kind == 0) return;
   const T b0 = V.b0, r0 = V.r0, W = V.W;
-  const T ir = T(1) / r, q = r0 * ir;
+  const T ir = rcp_(r), q = r0 * ir;
   switch (V.kind) {
     case 1:  // monopole
       B[0] = b0 * q * q;
@@ -130,13 +137,6 @@ __device__ inline void vacuum_field(const Vac<T> &V, T r, T st, T ct, bool insid
       break;
   }
 }
-
-// reciprocal and reciprocal square root: hardware approximations (a few ulp)
-// in FP32, exact division in FP64
-__device__ inline float rcp_(float x) { return __frcp_rn(x); }
-__device__ inline double rcp_(double x) { return 1.0 / x; }
-__device__ inline float rsqrt_(float x) { return rsqrtf(x); }
-__device__ inline double rsqrt_(double x) { return 1.0 / sqrt(x); }
 
 // ---- pushers, Sec. 2 (Boris 1970; Vay 2008).  Any right-handed orthonormal
 //      basis; qmdt = (q/m) dt.  u = gamma v updated in place. -------------------

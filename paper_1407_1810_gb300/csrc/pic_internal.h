@@ -106,6 +106,7 @@ void charge64(pic_ctx *c, double *Q, double *Qa);
 void reduce_particles64(pic_ctx *c);   // kinetic energy, live count, total charge
 // particles32.cu
 void particles32(pic_ctx *c, double t);
+void prepare32(pic_ctx *c);            // host-side set-up the FP32 step needs (fixed-point quantum)
 void flux_from_acc(pic_ctx *c);        // fixed point -> FP64 fluxes, clears the accumulators
 int64_t sort32(pic_ctx *c);            // tile sort + removal; returns live count
 void charge32(pic_ctx *c, double *Q, double *Qa);

@@ -25,7 +25,7 @@ PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 
 EXPORTS = ["pic_init_grid", "pic_load_particles", "pic_step", "pic_get_fields", "pic_set_fields", "pic_get_flux",
            "pic_get_particles", "pic_get_particles_noalloc", "pic_get_live", "pic_get_moments", "pic_gauss_snapshot", "pic_set_clock", "pic_profile",
-           "pic_get_profile", "pic_get_launches", "pic_ensemble_step", "pic_destroy", "pic_last_error"]
+           "pic_get_profile", "pic_get_launches", "pic_ensemble_step", "pic_autotune", "pic_destroy", "pic_last_error"]
 
 
 class pic_desc(C.Structure):
@@ -42,6 +42,7 @@ class pic_desc(C.Structure):
         ("q_over_m", C.c_double),
         ("sort_interval", C.c_int32), ("capacity", C.c_int64),
         ("flux_quantum", C.c_double),
+        ("tile_shape", C.c_int32),
     ]
 
 
@@ -83,6 +84,7 @@ def lib():
         "pic_get_profile": [P, D, C.POINTER(C.c_int64)],
         "pic_get_launches": [P, C.POINTER(C.c_int64)],
         "pic_ensemble_step": [C.POINTER(C.c_void_p), I32, I32],
+        "pic_autotune": [P, I32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
         "pic_destroy": [P],
     }
     for name, args in sig.items():
@@ -226,6 +228,12 @@ class Simulation:
 
     def profile(self, enable=True):
         check(self.L.pic_profile(self.h, 1 if enable else 0))
+
+    def autotune(self, trial_steps=40):
+        """Pick tile shape and sort interval by measurement (pic_autotune)."""
+        S, sh = C.c_int32(), C.c_int32()
+        check(self.L.pic_autotune(self.h, trial_steps, C.byref(S), C.byref(sh)))
+        return {"sort_interval": S.value, "tile_shape": sh.value}
 
     def launches(self):
         n = C.c_int64()

@@ -1,0 +1,110 @@
+"""Batched ensemble (pic_ensemble_step) and the tile/sort autotuner (pic_autotune).
+
+Members are independent simulations with uneven grids and particle counts
+(the ensemble workload's recipe).  The FP32 path's deposit sums are exact
+integers, so neither the batching (graph capture, parallel branches) nor the
+tile shape or sort interval may change a single bit of any member's result;
+FP64 members agree to rounding (atomic summation order).
+"""
+import numpy as np
+import pytest
+
+from paper_1407_1810_gb300 import configs, synthetic
+
+from gpu_common import setup
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1407_1810_gb300 import build
+
+    build.build()
+
+
+def _member_cfg(m, precision="fp32", scale=8):
+    r = synthetic.ensemble_member(m)
+    # the workload's grid shapes scaled down so the test stays small
+    nr, nth = max(16, r["nr"] // scale), max(16, r["nth"] // scale)
+    ppc = max(1, min(6, r["particles"] // (2 * nr * nth)))
+    return dict(configs.CONFIGS["monopole-64x64"], nr=nr, nth=nth, pairs_per_cell=ppc, T=r["T"],
+                seed=r["seed"], precision=precision)
+
+
+def _pairs(n, precision):
+    a, b = [], []
+    for m in range(n):
+        cfg = _member_cfg(m, precision)
+        s1, _, plasma, _ = setup(cfg)
+        s2, _, _, _ = setup(cfg, plasma=plasma)
+        a.append(s1)
+        b.append(s2)
+    return a, b
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_ensemble_equals_independent_steps(precision):
+    from paper_1407_1810_gb300 import picsar as P
+
+    ens, ref = _pairs(6, precision)
+    P.ensemble_step(ens, 45)  # crosses two sort intervals (20)
+    for s in ref:
+        s.step(45)
+    for k, (a, b) in enumerate(zip(ens, ref)):
+        fa, fb = a.fields(), b.fields()
+        if precision == "fp32":
+            assert np.array_equal(fa, fb), k
+        else:
+            assert np.max(np.abs(fa - fb)) <= 1e-13 * max(np.max(np.abs(fb)), 1e-300), k
+        assert a.moments()["live"] == b.moments()["live"], k
+
+
+def test_ensemble_with_injection_member():
+    from paper_1407_1810_gb300 import picsar as P
+
+    cfgs = [dict(configs.CONFIGS["rotator-1024x1024"], nr=24, nth=16, pairs_per_cell=1, absorb_cells=4, t_spin=0.5),
+            _member_cfg(3)]
+    ens, ref = [], []
+    for cfg in cfgs:
+        s1, _, plasma, _ = setup(cfg)
+        s2, _, _, _ = setup(cfg, plasma=plasma)
+        ens.append(s1)
+        ref.append(s2)
+    P.ensemble_step(ens, 70)
+    for s in ref:
+        s.step(70)
+    for a, b in zip(ens, ref):
+        assert np.array_equal(a.fields(), b.fields())
+        ma, mb = a.moments(), b.moments()
+        assert ma["injected"] == mb["injected"] and ma["live"] == mb["live"]
+
+
+def test_autotune_keeps_the_physics_bit_exact():
+    cfg = dict(_member_cfg(5), T=0.8)
+    s1, _, plasma, _ = setup(cfg)
+    s2, _, _, _ = setup(cfg, plasma=plasma)
+    s1.step(5)
+    s2.step(5)
+    choice = s1.autotune(trial_steps=20)
+    assert choice["sort_interval"] in (5, 10, 20, 40) and choice["tile_shape"] in (0, 1, 2)
+    # autotuning ran on clones: s1 has not advanced
+    assert s1.moments()["step"] == 5
+    s1.step(30)
+    s2.step(30)
+    assert np.array_equal(s1.fields(), s2.fields())
+    assert np.array_equal(s1.flux(), s2.flux())
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_tile_shapes_agree(shape):
+    cfg = _member_cfg(7)
+    s1, _, plasma, _ = setup(cfg)
+    s2, _, _, _ = setup(cfg, plasma=plasma, tile_shape=shape)
+    s1.step(25)
+    s2.step(25)
+    assert np.array_equal(s1.fields(), s2.fields())
