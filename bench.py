@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tile-shape", type=int, default=None, help="FP32 tile: 0 = 16x16, 1 = 8x32, 2 = 32x8 cells")
+    ap.add_argument("--sort-interval", type=int, default=None)
     return ap.parse_args()
 
 
@@ -141,6 +143,8 @@ def make_sim(cfg, precision, stream, capacity):
     dt = configs.courant_dt(cfg)
     b0, qw = configs.physics(cfg, dt)
     kw = configs.desc_kwargs(cfg, dt, b0, precision=precision, capacity=capacity)
+    if precision == "fp32":
+        kw["tile_shape"] = cfg.get("tile_shape", 0)
     return P.Simulation(P.make_desc(**kw), stream=stream), qw
 
 
@@ -188,7 +192,11 @@ def gpu_arm(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg = configs.CONFIGS[args.workload]
+    cfg = dict(configs.CONFIGS[args.workload])
+    if args.tile_shape is not None:
+        cfg["tile_shape"] = args.tile_shape
+    if args.sort_interval is not None:
+        cfg["sort_interval"] = args.sort_interval
     stream = torch.cuda.Stream(device=dev)
     ntot = cfg["nr"] * cfg["nth"] * cfg["pairs_per_cell"] * 2
     cap = ntot + ntot // 64 + (1 << 20)
@@ -232,7 +240,8 @@ def gpu_arm(args):
         "vs_baseline": None, "dtype": "f32" if precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": f"{cfg['nr']}x{cfg['nth']}", "particles": n,
                    "pairs_per_cell": cfg["pairs_per_cell"], "T": cfg["T"], "path": precision,
-                   "sort_interval": cfg.get("sort_interval", 20), "field_update": "f64",
+                   "sort_interval": cfg.get("sort_interval", 20), "tile_shape": cfg.get("tile_shape", 0),
+                   "field_update": "f64",
                    "l2": "inputs larger than L2 (particle state %.1f GB)" % (n * (36 if precision == "fp32" else 56) / 1e9)},
         "gauss_residual": mom["gauss_residual"],
         "hot_kernel": {"name": kname, "ms_per_launch": kms, "particle_steps_per_s": hot_rate},

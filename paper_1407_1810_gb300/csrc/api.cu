@@ -173,9 +173,7 @@ void free_parts(pic_ctx *c) {
 }
 
 int alloc_parts(pic_ctx *c, int64_t cap) {
-  // 64 elements of padding past the capacity: the FP32 tile kernel's bulk
-  // copies round their length up to 16 bytes
-  const size_t n = (size_t)cap + 64;
+  const size_t n = (size_t)cap;
   if (c->d.precision == PIC_FP64) {
     Parts64 *a[2] = {&c->p64, &c->q64};
     for (Parts64 *p : a) {

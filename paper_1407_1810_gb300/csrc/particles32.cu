@@ -156,39 +156,7 @@ __device__ inline float exp_small(float y) {
 
 __device__ inline float clamp01(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
 
-// ---- bulk asynchronous copies (global -> shared) completing on an mbarrier --
-__device__ inline uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ inline void mbar_init(uint64_t *b, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
-}
-__device__ inline void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ inline void mbar_expect_tx(uint64_t *b, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
-}
-__device__ inline void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, uint64_t *b) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(dst)),
-               "l"(src), "r"(bytes), "r"(smem_addr(b))
-               : "memory");
-}
-__device__ inline void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ inline bool mbar_try_wait(uint64_t *b, unsigned parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_addr(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait: gives up after ~2^22 polls (each try_wait also suspends for a
-// while), reporting ERR_TIMEOUT instead of hanging
-__device__ inline bool mbar_wait_bounded(uint64_t *b, unsigned parity, int *err) {
-  for (int it = 0; it < (1 << 22); ++it)
-    if (mbar_try_wait(b, parity)) return true;
-  atomicOr(err, ERR_TIMEOUT);
-  return false;
-}
+
 
 // One particle step.  Returns false when the particle is removed.
 template <class W>
@@ -353,26 +321,6 @@ __device__ inline bool step32_global(const Args32 &A, uint32_t &cell, float &dx,
   return step32(A, gw, cell, dx, dy, ur, ut, up, qw);
 }
 
-// a particle whose state was staged in shared memory (tile path)
-template <class SW>
-__device__ inline void process_staged(const Args32 &A, Parts32 P, int64_t k, const uint32_t *scell, const float *sdx,
-                                      const float *sdy, const float *sur, const float *sut, const float *sup,
-                                      const float *sqw, int e, const SW &sw, int wi_lo, int wi_hi, int wj_lo,
-                                      int wj_hi, int &dead) {
-  const float qw = sqw[e];
-  if (qw == 0.f) return;
-  uint32_t cell = scell[e];
-  float dx = sdx[e], dy = sdy[e], ur = sur[e], ut = sut[e], up = sup[e];
-  const int ci = (int)(cell >> 16) - CELL_BIAS, cj = (int)(cell & 0xffffu);
-  bool alive;
-  if (ci >= wi_lo && ci < wi_hi && cj >= wj_lo && cj < wj_hi) alive = step32(A, sw, cell, dx, dy, ur, ut, up, qw);
-  else alive = step32_global(A, cell, dx, dy, ur, ut, up, qw);
-  if (!alive) { P.qw[k] = 0.f; ++dead; return; }
-  P.cell[k] = cell;
-  P.dx[k] = dx; P.dy[k] = dy;
-  P.ur[k] = ur; P.ut[k] = ut; P.up[k] = up;
-}
-
 template <class SW>
 __device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, const SW &sw,
                                int wi_lo, int wi_hi, int wj_lo, int wj_hi, int &dead) {
@@ -395,10 +343,6 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
   constexpr int WI = Win<TI, TJ>::WI, WJ = Win<TI, TJ>::WJ, WN = Win<TI, TJ>::WN;
   __shared__ float sf[6 * WN];
   __shared__ float srn[WI];
-  constexpr int SB = NT + 8;  // chunk plus alignment slack, a multiple of 4 elements
-  __shared__ __align__(16) uint32_t stg_cell[2][SB];
-  __shared__ __align__(16) float stg[2][6][SB];
-  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ int shi[3 * WN];
   __shared__ int slo[3 * WN];
   __shared__ int sdead;
@@ -418,47 +362,10 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
       for (int c = 0; c < 3; ++c) { shi[c * WN + e] = 0; slo[c * WN + e] = 0; }
     }
     for (int e = threadIdx.x; e < WI; e += NT) srn[e] = A.r_n[wi0 + e + A.PI];
-    // the bin is streamed through shared memory in chunks of NT particles,
-    // double-buffered: bulk copies of chunk c+1 fly while chunk c computes
-    if (threadIdx.x == 0) {
-      mbar_init(&mbar[0], 1);
-      mbar_init(&mbar[1], 1);
-      mbar_fence_init();
-    }
     __syncthreads();
     const SmemAcc<WJ, WN> sw{sf, shi, slo, srn, wi0, wj0};
-    const int nchunks = (int)((b1 - b0 + NT - 1) / NT);
-    // copy chunk c into stage s: start rounded down to 16 bytes (4 elements);
-    // the particle arrays are padded past their capacity, so the rounded-up
-    // length never leaves the allocation
-    auto issue = [&](int c, int st) {
-      const int64_t k0 = b0 + (int64_t)c * NT, ka = k0 & ~(int64_t)3;
-      const int64_t kend = min(b1, k0 + NT);
-      const unsigned cnt = (unsigned)(((kend - ka) + 3) & ~(int64_t)3);
-      const unsigned bytes = cnt * 4u;
-      fence_proxy_async();
-      mbar_expect_tx(&mbar[st], 7u * bytes);
-      bulk_copy_g2s(stg_cell[st], P.cell + ka, bytes, &mbar[st]);
-      bulk_copy_g2s(stg[st][0], P.dx + ka, bytes, &mbar[st]);
-      bulk_copy_g2s(stg[st][1], P.dy + ka, bytes, &mbar[st]);
-      bulk_copy_g2s(stg[st][2], P.ur + ka, bytes, &mbar[st]);
-      bulk_copy_g2s(stg[st][3], P.ut + ka, bytes, &mbar[st]);
-      bulk_copy_g2s(stg[st][4], P.up + ka, bytes, &mbar[st]);
-      bulk_copy_g2s(stg[st][5], P.qw + ka, bytes, &mbar[st]);
-    };
-    if (threadIdx.x == 0) issue(0, 0);
-    bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      const int st = c & 1;
-      if (threadIdx.x == 0 && c + 1 < nchunks) issue(c + 1, st ^ 1);
-      ok = mbar_wait_bounded(&mbar[st], (unsigned)((c >> 1) & 1), A.err) && ok;
-      const int64_t k0 = b0 + (int64_t)c * NT, k = k0 + threadIdx.x;
-      const int e = (int)(k0 - (k0 & ~(int64_t)3)) + threadIdx.x;
-      if (ok && k < b1)
-        process_staged(A, P, k, stg_cell[st], stg[st][0], stg[st][1], stg[st][2], stg[st][3], stg[st][4],
-                       stg[st][5], e, sw, i0 - H, i0 + TI + H, j0 - H, j0 + TJ + H, dead);
-      __syncthreads();  // every lane is done with stage st before it is refilled
-    }
+    for (int64_t k = b0 + threadIdx.x; k < b1; k += NT)
+      process(A, P, k, true, sw, i0 - H, i0 + TI + H, j0 - H, j0 + TJ + H, dead);
     if (dead) atomicAdd(&sdead, dead);
     __syncthreads();
     for (int e = threadIdx.x; e < WN; e += NT) {
