@@ -17,6 +17,11 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpicsar_gb300.so")
 SOURCES = ["api.cu", "fields.cu", "particles64.cu", "particles32.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The FP32 particle kernel takes approximate division and square root (within
+# 2 ulp) and flushes denormals: 5% faster, and the FP32 parity tests against the
+# oracle hold unchanged.  Full --use_fast_math is not used: its sin/cos move
+# positions near the poles by ~1e-5 cell.
+EXTRA = {"particles32.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
 
 
 def _nvcc() -> str:
@@ -46,7 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src in SOURCES:
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [nvcc, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *flags, *EXTRA.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
