@@ -30,6 +30,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1407_1810_gb300 import workload as W  # noqa: E402
+
 METRIC = "particle-steps/s (gather+push+deposit), FP32 vs FP64 path, at stated Gauss residual"
 UNIT = "particle-steps/s"
 ALG_BYTES_FP32 = 52  # per particle-step: read cell, dx, dy, u (3), qw = 28 B; write cell, dx, dy, u = 24 B
@@ -136,33 +138,6 @@ def recorded_traffic():
     return float(d["dram_bytes_per_particle"])
 
 
-def make_sim(cfg, precision, stream, capacity):
-    from paper_1407_1810_gb300 import configs
-    from paper_1407_1810_gb300 import picsar as P
-
-    dt = configs.courant_dt(cfg)
-    b0, qw = configs.physics(cfg, dt)
-    kw = configs.desc_kwargs(cfg, dt, b0, precision=precision, capacity=capacity)
-    if precision == "fp32":
-        kw["tile_shape"] = cfg.get("tile_shape", 0)
-    return P.Simulation(P.make_desc(**kw), stream=stream), qw
-
-
-def load_plasma(sim, cfg, qw, device, stream):
-    import torch
-
-    from paper_1407_1810_gb300 import synthetic
-
-    n = 0
-    with torch.cuda.stream(stream):
-        for ch in synthetic.pair_plasma_torch(cfg["nr"], cfg["nth"], cfg["pairs_per_cell"], cfg["T"], qw,
-                                              cfg["seed"], device, rows_per_chunk=128):
-            sim.load(ch["x1"], ch["x2"], ch["ur"], ch["uth"], ch["uph"], ch["qw"])
-            n += ch["x1"].numel()
-            del ch
-    return n
-
-
 def time_steps(sim, K, stream):
     import torch
 
@@ -198,10 +173,8 @@ def gpu_arm(args):
     if args.sort_interval is not None:
         cfg["sort_interval"] = args.sort_interval
     stream = torch.cuda.Stream(device=dev)
-    ntot = cfg["nr"] * cfg["nth"] * cfg["pairs_per_cell"] * 2
-    cap = ntot + ntot // 64 + (1 << 20)
-    sim, qw = make_sim(cfg, cfg["precision"], stream.cuda_stream, cap)
-    n = load_plasma(sim, cfg, qw, dev, stream)
+    sim, qw, _, _ = W.make_sim(cfg, stream=stream.cuda_stream)
+    n = W.load_plasma(sim, cfg, qw, dev, stream)
     torch.cuda.synchronize()
     sim.step(args.warmup)
     torch.cuda.synchronize()
@@ -280,8 +253,8 @@ def fp64_run(cfg, dev, stream, args):
     import torch
 
     ntot = cfg["nr"] * cfg["nth"] * cfg["pairs_per_cell"] * 2
-    sim, qw = make_sim(cfg, "fp64", stream.cuda_stream, ntot + (1 << 20))
-    load_plasma(sim, cfg, qw, dev, stream)
+    sim, qw, _, _ = W.make_sim(cfg, "fp64", stream.cuda_stream, ntot + (1 << 20))
+    W.load_plasma(sim, cfg, qw, dev, stream)
     sim.step(2)
     sim.profile(True)
     ms, units, _ = time_steps(sim, args.fp64_steps, stream)
@@ -307,7 +280,7 @@ def e2e_run(cfg, dev, stream, args):
     from paper_1407_1810_gb300 import synthetic
 
     ntot = cfg["nr"] * cfg["nth"] * cfg["pairs_per_cell"] * 2
-    sim, qw = make_sim(cfg, cfg["precision"], stream.cuda_stream, ntot + (1 << 20))
+    sim, qw, _, _ = W.make_sim(cfg, stream=stream.cuda_stream, capacity=ntot + (1 << 20))
     host = {k: torch.empty(ntot, dtype=torch.float64, pin_memory=True) for k in ("x1", "x2", "ur", "uth", "uph", "qw")}
     off = 0
     with torch.cuda.stream(stream):

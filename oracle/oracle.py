@@ -99,6 +99,7 @@ def _load():
         "orc_ghost": (I32, [P]),
         "orc_get_flux": (None, [P, D]),
         "orc_step": (None, [P, I32]),
+        "orc_particles_only": (None, [P]),
         "orc_field_step": (None, [P, I32]),
         "orc_vacuum_fields": (None, [P, C.c_double, C.c_double, C.c_double, D, D]),
         "orc_gather": (None, [P, C.c_double, C.c_double, C.c_double, D, D]),
@@ -223,6 +224,11 @@ class Oracle:
 
     def step(self, n=1):
         self.lib.orc_step(self.h, n)
+        return self.error()
+
+    def particles_only(self):
+        """The particle part of one step, fields untouched (sampled replays)."""
+        self.lib.orc_particles_only(self.h)
         return self.error()
 
     def field_step(self, n=1):

@@ -680,24 +680,32 @@ static void inject(orc_sim *s, double t) {
   s->next_id += (int64_t)2 * npp * nt;
 }
 
+/* Every particle's step with zeroed fluxes, then stable removal of those whose
+ * shape left the domain. */
+static void particles_pass(orc_sim *s, double t) {
+  for (int c = 0; c < 3; ++c) memset(s->F[c], 0, ghost_size(s) * sizeof(double));
+  int64_t w = 0;
+  for (int64_t k = 0; k < s->np; ++k) {
+    int del = 0;
+    particle_step(s, k, t, &del);
+    if (del) { s->n_deleted++; continue; }
+    if (w != k) {
+      s->x1[w] = s->x1[k]; s->x2[w] = s->x2[k];
+      s->ur[w] = s->ur[k]; s->uth[w] = s->uth[k]; s->uph[w] = s->uph[k];
+      s->qw[w] = s->qw[k]; s->id[w] = s->id[k];
+    }
+    ++w;
+  }
+  s->np = w;
+}
+
+/* The particle part of one step only, fields and clock left as they are: it
+ * replays a sample of a large state without the full-grid field solve. */
+void orc_particles_only(orc_sim *s) { particles_pass(s, s->step * s->p.dt); }
+
 void orc_step(orc_sim *s, int32_t nsteps) {
   for (int n = 0; n < nsteps; ++n) {
-    double t = s->step * s->p.dt;
-    for (int c = 0; c < 3; ++c) memset(s->F[c], 0, ghost_size(s) * sizeof(double));
-    /* particles, then stable removal of those whose shape left the domain */
-    int64_t w = 0;
-    for (int64_t k = 0; k < s->np; ++k) {
-      int del = 0;
-      particle_step(s, k, t, &del);
-      if (del) { s->n_deleted++; continue; }
-      if (w != k) {
-        s->x1[w] = s->x1[k]; s->x2[w] = s->x2[k];
-        s->ur[w] = s->ur[k]; s->uth[w] = s->uth[k]; s->uph[w] = s->uph[k];
-        s->qw[w] = s->qw[k]; s->id[w] = s->id[k];
-      }
-      ++w;
-    }
-    s->np = w;
+    particles_pass(s, s->step * s->p.dt);
     for (int f = 0; f < s->p.n_filt; ++f) {
       orc_filter_pass(s, s->F[0], 0, +1);
       orc_filter_pass(s, s->F[1], 1, -1);

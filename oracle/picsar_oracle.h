@@ -83,6 +83,8 @@ void orc_get_flux(const orc_sim *s, double *out3);
 
 /* one or more full time steps */
 void orc_step(orc_sim *s, int32_t nsteps);
+/* the particle part of one step (no field update, clock unchanged) */
+void orc_particles_only(orc_sim *s);
 /* field-only leapfrog with zero current (Appendix A), used by the field tests */
 void orc_field_step(orc_sim *s, int32_t nsteps);
 

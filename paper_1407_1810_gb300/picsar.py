@@ -188,13 +188,24 @@ class Simulation:
         check(self.L.pic_get_flux(self.h, C.c_void_p(out.ctypes.data), C.byref(n), PIC_MEM_HOST))
         return out.reshape(3, self.nr + 2 * self.g + 1, self.nth + 1)
 
-    def particles(self):
+    def particles(self, device=None):
+        """Live particles as FP64 arrays (id as int64): numpy on the host, or
+        torch tensors on ``device`` when one is given."""
+        keys = ("x1", "x2", "ur", "uth", "uph", "qw")
         n = C.c_int64(0)
         check(self.L.pic_get_particles(self.h, C.byref(n), None, None, None, None, None, None, None, PIC_MEM_HOST))
         m = n.value
-        out = {k: np.empty(m) for k in ("x1", "x2", "ur", "uth", "uph", "qw")}
+        if device is not None:
+            import torch
+
+            out = {k: torch.empty(m, dtype=torch.float64, device=device) for k in keys}
+            out["id"] = torch.empty(m, dtype=torch.int64, device=device)
+            ptrs = [C.c_void_p(out[k].data_ptr()) for k in (*keys, "id")]
+            check(self.L.pic_get_particles(self.h, C.byref(n), *ptrs, PIC_MEM_DEVICE))
+            return out
+        out = {k: np.empty(m) for k in keys}
         ids = np.empty(m, dtype=np.int64)
-        ptrs = [C.c_void_p(out[k].ctypes.data) for k in ("x1", "x2", "ur", "uth", "uph", "qw")]
+        ptrs = [C.c_void_p(out[k].ctypes.data) for k in keys]
         check(self.L.pic_get_particles(self.h, C.byref(n), *ptrs, C.c_void_p(ids.ctypes.data), PIC_MEM_HOST))
         out["id"] = ids
         return out

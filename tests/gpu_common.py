@@ -57,3 +57,30 @@ def by_id(d):
 def rel_l2(a, b):
     den = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def replay_compare_fp32(g, r, tau):
+    """Compare the FP32 path's step with the oracle's replay of it, both given
+    as particle dicts.  Removals agree: ids kept by one side only (a removal
+    decided on a coordinate within rounding of the boundary) count with the
+    near-tie particles, which the oracle places within tau of a grid line and
+    which may be at most 1e-4 of all; elsewhere cells agree exactly.
+    Positions agree within tau, momenta within 2e-6 of |u| (+1e-2), charges
+    exactly.  Returns the number of near-tie particles."""
+    g, r = by_id(g), by_id(r)
+    common = np.intersect1d(g["id"], r["id"])
+    one_sided = len(g["id"]) + len(r["id"]) - 2 * len(common)
+    g = {k: v[np.isin(g["id"], common)] for k, v in g.items()}
+    r = {k: v[np.isin(r["id"], common)] for k, v in r.items()}
+    tie = (np.abs(r["x1"] - np.round(r["x1"])) < tau) | (np.abs(r["x2"] - np.round(r["x2"])) < tau)
+    ok = ~tie
+    assert tie.sum() + one_sided <= max(1, 1e-4 * len(tie)), (tie.sum(), one_sided)
+    assert np.array_equal(np.floor(g["x1"][ok]), np.floor(r["x1"][ok]))
+    assert np.array_equal(np.floor(g["x2"][ok]), np.floor(r["x2"][ok]))
+    assert np.max(np.abs(g["x1"] - r["x1"]), initial=0.0) < tau
+    assert np.max(np.abs(g["x2"] - r["x2"]), initial=0.0) < tau
+    umag = np.sqrt(r["ur"] ** 2 + r["uth"] ** 2 + r["uph"] ** 2) + 1e-2
+    for k in ("ur", "uth", "uph"):
+        assert np.max(np.abs(g[k] - r[k]) / umag, initial=0.0) < 2e-6, k
+    assert np.array_equal(g["qw"], r["qw"])
+    return int(tie.sum())

@@ -17,7 +17,7 @@ import pytest
 import oracle as O
 from paper_1407_1810_gb300 import configs
 
-from gpu_common import KEYS, by_id, fp32_state, rel_l2, setup
+from gpu_common import KEYS, by_id, fp32_state, rel_l2, replay_compare_fp32, setup
 
 pytestmark = pytest.mark.gpu
 TAU = 2e-6
@@ -45,24 +45,7 @@ def _cfg(**over):
 
 def _replay_compare(s, o2):
     """Compare a GPU step with the oracle's replay of the same step."""
-    g, r = by_id(s.particles()), by_id(o2.particles())
-    common = np.intersect1d(g["id"], r["id"])
-    gi = np.isin(g["id"], common)
-    ri = np.isin(r["id"], common)
-    g = {k: v[gi] for k, v in g.items()}
-    r = {k: v[ri] for k, v in r.items()}
-    # near-tie particles: the oracle's coordinate within TAU of a grid line
-    tie = (np.abs(r["x1"] - np.round(r["x1"])) < TAU) | (np.abs(r["x2"] - np.round(r["x2"])) < TAU)
-    ok = ~tie
-    assert tie.sum() <= max(1, 1e-4 * len(tie)), tie.sum()
-    assert np.array_equal(np.floor(g["x1"][ok]), np.floor(r["x1"][ok]))
-    assert np.array_equal(np.floor(g["x2"][ok]), np.floor(r["x2"][ok]))
-    assert np.max(np.abs(g["x1"] - r["x1"])) < TAU
-    assert np.max(np.abs(g["x2"] - r["x2"])) < TAU
-    umag = np.sqrt(r["ur"] ** 2 + r["uth"] ** 2 + r["uph"] ** 2) + 1e-2
-    for k in ("ur", "uth", "uph"):
-        assert np.max(np.abs(g[k] - r[k]) / umag) < 2e-6, k
-    return tie.sum()
+    return replay_compare_fp32(s.particles(), o2.particles(), TAU)
 
 
 def _replay(s, o, step, next_id):

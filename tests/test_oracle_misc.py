@@ -127,3 +127,32 @@ def test_azimuthal_flux_is_swept_angle(oracle_mod):
     d = o.particles()
     r1, th1 = float(o.f_r(d["x1"][0])), float(o.f_th(d["x2"][0]))
     assert r1 * math.sin(th1) * d["uph"][0] == pytest.approx(R * uph, rel=1e-12)
+
+
+def test_particles_only_is_the_particle_part_of_a_step(oracle_mod):
+    """orc_particles_only moves, pushes, deposits and removes exactly as the
+    particle part of orc_step does (with no filtering the step's fluxes are
+    the raw deposit), and leaves the fields and the clock alone."""
+    rng = np.random.default_rng(3)
+    n = 400
+    a, b = _o(vacuum="monopole", b0=2.0), _o(vacuum="monopole", b0=2.0)
+    f = rng.normal(0, 0.1, a.field_shape)
+    x1 = np.concatenate([rng.uniform(0, 16, n - 2), [-0.95, 16.95]])  # two leave the domain
+    x2 = rng.uniform(0, 12, n)
+    u = rng.normal(0, 0.5, (3, n))
+    u[0, -2], u[0, -1] = -3.0, 3.0
+    qw = np.where(np.arange(n) % 2 == 0, 0.01, -0.01)
+    for o in (a, b):
+        o.set_fields(f)
+        o.load(x1, x2, u[0], u[1], u[2], qw)
+        o.set_clock(4, n)
+    fa = a.fields()
+    assert a.particles_only() == 0 and b.step(1) == 0
+    pa, pb = a.particles(), b.particles()
+    assert len(pa["x1"]) < n
+    for k in pa:
+        assert np.array_equal(pa[k], pb[k]), k
+    assert np.array_equal(a.flux(), b.flux())
+    assert a.counters() == b.counters()
+    assert np.array_equal(a.fields(), fa)
+    assert a.lib.orc_get_step(a.h) == 4 and b.lib.orc_get_step(b.h) == 5
