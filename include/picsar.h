@@ -89,7 +89,10 @@ typedef struct pic_desc {
   int32_t sort_interval;     /* FP32 path: steps between tile sorts (0 = 20);
                                 FP64 path: steps between compactions */
   int64_t capacity;          /* particle slots to allocate (0 = 2x the first load + injection room) */
-  double flux_quantum;       /* FP32 path: charge of one fixed-point flux unit; 0 = automatic */
+  double flux_quantum;       /* FP32 path: least charge of one fixed-point flux unit; 0 = automatic.
+                                The unit is 2^(e - 36), e = ceil(log2 max |qw|) over every charge
+                                the context has held (loaded or injected, raised on the device),
+                                and at least this value rounded up to a power of two. */
   int32_t tile_shape;        /* FP32 path: tile of the shared-memory deposit, 0 = 16x16 cells,
                                 1 = 8 (r) x 32 (theta), 2 = 32 x 8 */
 } pic_desc;
@@ -120,7 +123,8 @@ int pic_init_grid(pic_ctx **out, const pic_desc *d, void *stream);
  * All arrays are FP64 of length n, host or device per mem.  Particle ids are
  * assigned consecutively from the context's id counter.  The FP32 path stores
  * x as (cell, FP32 offset) and u, qw in FP32.  Errors: PIC_EINVAL (x outside
- * [-g, nr+g] x [0, nth] with g = n_filt+2, qw == 0), PIC_ECAPACITY. */
+ * [-g, nr+g] x [0, nth] with g = n_filt+2, qw == 0, on the FP32 path |qw|
+ * outside [2^-100, 2^100]), PIC_ECAPACITY. */
 int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const double *x2,
                        const double *u_r, const double *u_th, const double *u_ph,
                        const double *qw, int32_t mem);

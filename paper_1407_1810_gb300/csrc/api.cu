@@ -65,6 +65,8 @@ int check_desc(const pic_desc &d) {
       return pic_fail(PIC_EINVAL, "linear r map: the ghost cells inside the inner conductor reach r <= 0");
   }
   if (d.tile_shape < 0 || d.tile_shape > 2) return pic_fail(PIC_EINVAL, "tile_shape must be 0, 1 or 2");
+  if (!(d.flux_quantum >= 0.0) || !std::isfinite(d.flux_quantum))
+    return pic_fail(PIC_EINVAL, "flux_quantum must be finite and >= 0");
   if (d.precision == PIC_FP32 && d.nr + 2 * (d.n_filt + 2) >= 65536 - 2 * CELL_BIAS)
     return pic_fail(PIC_EINVAL, "FP32 path: grid too large for the packed cell index");
   return PIC_OK;
@@ -295,24 +297,32 @@ __global__ void k_load64(Grid G, Parts64 P, int64_t base, int64_t n, const doubl
 
 __global__ void k_load32(Grid G, Parts32 P, int64_t base, int64_t n, const double *x1, const double *x2,
                          const double *ur, const double *ut, const double *up, const double *qw, int64_t id0,
-                         int *err) {
+                         int *err, long long *qexp) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const double a = x1[k], b = x2[k], q = qw[k];
-  const bool ok = a >= -(double)(G.n_filt + 1) && a < (double)(G.nr + G.n_filt + 1) && b >= 0.0 && b <= G.nth &&
-                  q != 0.0 && isfinite(q) && isfinite(ur[k]) && isfinite(ut[k]) && isfinite(up[k]);
-  const int64_t d = base + k;
-  if (!ok) { atomicOr(err, ERR_RANGE); P.qw[d] = 0.0; return; }
-  // cell = floor(x); offset rounded to FP32 and kept in [0, 1)
-  int ci = (int)floor(a), cj = (int)floor(b);
-  if (cj > G.nth - 1) cj = G.nth - 1;
-  float ox = (float)(a - ci), oy = (float)(b - cj);
-  if (ox >= 1.0f) { ox = 0.0f; ++ci; }
-  if (oy >= 1.0f && cj < G.nth - 1) { oy = 0.0f; ++cj; }
-  P.cell[d] = ((uint32_t)(ci + CELL_BIAS) << 16) | (uint32_t)cj;
-  P.dx[d] = ox; P.dy[d] = oy;
-  P.ur[d] = (float)ur[k]; P.ut[d] = (float)ut[k]; P.up[d] = (float)up[k]; P.qw[d] = (float)q;
-  P.id[d] = id0 + k;
+  int qe = (int)QEXP_NONE;
+  if (k < n) {
+    const double a = x1[k], b = x2[k], q = qw[k];
+    const bool ok = a >= -(double)(G.n_filt + 1) && a < (double)(G.nr + G.n_filt + 1) && b >= 0.0 && b <= G.nth &&
+                    fabs(q) >= 0x1p-100 && fabs(q) <= 0x1p100 && isfinite(ur[k]) && isfinite(ut[k]) && isfinite(up[k]);
+    const int64_t d = base + k;
+    if (!ok) {
+      atomicOr(err, ERR_RANGE);
+      P.qw[d] = 0.0;
+    } else {
+      // cell = floor(x); offset rounded to FP32 and kept in [0, 1)
+      int ci = (int)floor(a), cj = (int)floor(b);
+      if (cj > G.nth - 1) cj = G.nth - 1;
+      float ox = (float)(a - ci), oy = (float)(b - cj);
+      if (ox >= 1.0f) { ox = 0.0f; ++ci; }
+      if (oy >= 1.0f && cj < G.nth - 1) { oy = 0.0f; ++cj; }
+      P.cell[d] = ((uint32_t)(ci + CELL_BIAS) << 16) | (uint32_t)cj;
+      P.dx[d] = ox; P.dy[d] = oy;
+      P.ur[d] = (float)ur[k]; P.ut[d] = (float)ut[k]; P.up[d] = (float)up[k]; P.qw[d] = (float)q;
+      P.id[d] = id0 + k;
+      qe = charge_exp(fabsf((float)q));
+    }
+  }
+  raise_qexp(qexp, qe);  // every lane of the warp reaches this
 }
 
 __global__ void k_export32(Parts32 P, int64_t n, double *x1, double *x2, double *ur, double *ut, double *up, double *qw,
@@ -441,6 +451,12 @@ extern "C" int pic_init_grid(pic_ctx **out, const pic_desc *dd, void *stream) {
   if ((e = dalloc(&c->d_err, 1)) || (e = dalloc(&c->d_cnt, CNT_N)) || (e = dalloc(&c->d_acc, ACC_N))) return fail(e);
   cudaMemset(c->d_err, 0, sizeof(int));
   cudaMemset(c->d_cnt, 0, CNT_N * sizeof(long long));
+  {  // fixed-point exponent: raised on the device by the charges loaded or injected
+    long long q0 = QEXP_NONE;
+    if (d.flux_quantum > 0.0)
+      q0 = std::min<long long>(QEXP_MAX, std::max<long long>(QEXP_MIN, (long long)std::ceil(std::log2(d.flux_quantum)) + KFIX));
+    PIC_CUDA(cudaMemcpy(c->d_cnt + CNT_QEXP, &q0, sizeof q0, cudaMemcpyHostToDevice));
+  }
   PIC_CUDA(cudaMallocHost((void **)&c->h_pinned, 64));
   PIC_CUDA(cudaDeviceSynchronize());
   *out = c;
@@ -484,7 +500,7 @@ extern "C" int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const
                                              dv[5], c->next_id + off, c->d_err);
     else
       ++c->launches, k_load32<<<blocks, 256, 0, c->stream>>>(c->G, c->p32, c->n_used + off, m, dv[0], dv[1], dv[2], dv[3], dv[4],
-                                             dv[5], c->next_id + off, c->d_err);
+                                             dv[5], c->next_id + off, c->d_err, c->d_cnt + CNT_QEXP);
     if (mem != PIC_MEM_DEVICE) PIC_CUDA(cudaStreamSynchronize(c->stream));
   }
   PIC_CUDA(cudaGetLastError());
@@ -498,10 +514,7 @@ extern "C" int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const
     cudaMemset(c->d_err, 0, sizeof(int));
     return pic_fail(PIC_EINVAL, "particle outside the grid, zero charge or non-finite momentum (dropped)");
   }
-  if (c->d.precision == PIC_FP32) {
-    c->flux_quantum = 0.0;  // recomputed from the new charges at the next step
-    c->need_sort = true;    // binned by the next step (appended particles are valid unbinned)
-  }
+  if (c->d.precision == PIC_FP32) c->need_sort = true;  // binned by the next step (appended particles are valid unbinned)
   return PIC_OK;
 }
 
@@ -543,8 +556,7 @@ static void step_body(pic_ctx *c) {
 }
 
 // Work that needs the host before steps can be enqueued blindly: a pending
-// sort, the Gauss snapshot, the fixed-point quantum, and room for `steps`
-// steps of injection.
+// sort, the Gauss snapshot, and room for `steps` steps of injection.
 static int prepare_steps(pic_ctx *c, int steps) {
   if (c->need_sort) {
     int e = compact(c);
@@ -552,7 +564,6 @@ static int prepare_steps(pic_ctx *c, int steps) {
     c->need_sort = false;
   }
   if (!c->have_snap) moments(c, true, nullptr);
-  if (c->d.precision == PIC_FP32) prepare32(c);
   const int64_t need = c->n_used + inject_slots(c) * (int64_t)steps;
   if (c->d.inject && need > c->cap) {
     int e = compact(c);
@@ -889,8 +900,11 @@ static int clone_context(pic_ctx *c, pic_ctx **out) {
     cudaFree(buf);
     if (e) return e;
   }
+  // the same fixed-point quantum as the original (its charges may have left)
+  cudaMemcpyAsync(k->d_cnt + CNT_QEXP, c->d_cnt + CNT_QEXP, sizeof(long long), cudaMemcpyDeviceToDevice, c->stream);
   k->step = c->step;
   k->next_id = c->next_id;
+  PIC_CUDA(cudaStreamSynchronize(c->stream));
   return PIC_OK;
 }
 

@@ -158,33 +158,38 @@ __global__ void k_inject_sigma(Grid G, const double *__restrict__ Er, double t, 
 
 template <bool FP32>
 __global__ void k_inject_write(Grid G, const double *__restrict__ sig, const long long *smax, Parts64 P,
-                               Parts32 Q, int64_t base, int64_t id0, int npp, double finj, long long *cnt) {
+                               Parts32 Q, int64_t base, int64_t id0, int npp, double finj, long long *cnt,
+                               long long *qexp) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)G.nth * npp * 2) return;
-  const int j = (int)(idx / (2 * npp)), k = (int)((idx / 2) % npp), s = (int)(idx % 2);
-  const double sm = __longlong_as_double(*smax), sg = sig[j];
-  const double r0 = G.r_min;
-  const double dA = 2.0 * PI_D * r0 * r0 * (G.m.cos_t[j + G.PJ] - G.m.cos_t[j + 1 + G.PJ]);
-  const double w = finj * fabs(sg) * dA / npp;
-  const bool on = fabs(sg) > 1e-12 * sm && w > 0.0;
-  const int64_t slot = base + idx;
-  const double q = on ? (s == 0 ? w : -w) : 0.0;
-  const double oy = (k + 0.5) / npp;
-  if (FP32) {
-    Q.cell[slot] = ((uint32_t)(0 + CELL_BIAS) << 16) | (uint32_t)j;
-    Q.dx[slot] = 0.5f;
-    Q.dy[slot] = (float)oy;
-    Q.ur[slot] = Q.ut[slot] = Q.up[slot] = 0.0f;
-    Q.qw[slot] = (float)q;
-    Q.id[slot] = id0 + idx;
-  } else {
-    P.x1[slot] = 0.5;
-    P.x2[slot] = j + oy;
-    P.ur[slot] = P.ut[slot] = P.up[slot] = 0.0;
-    P.qw[slot] = q;
-    P.id[slot] = id0 + idx;
+  int qe = (int)QEXP_NONE;
+  if (idx < (int64_t)G.nth * npp * 2) {
+    const int j = (int)(idx / (2 * npp)), k = (int)((idx / 2) % npp), s = (int)(idx % 2);
+    const double sm = __longlong_as_double(*smax), sg = sig[j];
+    const double r0 = G.r_min;
+    const double dA = 2.0 * PI_D * r0 * r0 * (G.m.cos_t[j + G.PJ] - G.m.cos_t[j + 1 + G.PJ]);
+    const double w = finj * fabs(sg) * dA / npp;
+    const bool on = fabs(sg) > 1e-12 * sm && w > 0.0;
+    const int64_t slot = base + idx;
+    const double q = on ? (s == 0 ? w : -w) : 0.0;
+    const double oy = (k + 0.5) / npp;
+    if (FP32) {
+      Q.cell[slot] = ((uint32_t)(0 + CELL_BIAS) << 16) | (uint32_t)j;
+      Q.dx[slot] = 0.5f;
+      Q.dy[slot] = (float)oy;
+      Q.ur[slot] = Q.ut[slot] = Q.up[slot] = 0.0f;
+      Q.qw[slot] = (float)q;
+      Q.id[slot] = id0 + idx;
+      if (on) qe = charge_exp(fabsf((float)q));
+    } else {
+      P.x1[slot] = 0.5;
+      P.x2[slot] = j + oy;
+      P.ur[slot] = P.ut[slot] = P.up[slot] = 0.0;
+      P.qw[slot] = q;
+      P.id[slot] = id0 + idx;
+    }
+    if (on) add_ll(cnt, 1LL);
   }
-  if (on) add_ll(cnt, 1LL);
+  if (FP32) raise_qexp(qexp, qe);  // every lane of the warp reaches this
 }
 
 __device__ inline double warp_max(double v) {
@@ -317,10 +322,10 @@ void inject(pic_ctx *c, double t) {
   const int blocks = (int)((nslots + 255) / 256);
   if (c->d.precision == PIC_FP32)
     ++c->launches, k_inject_write<true><<<blocks, 256, 0, c->stream>>>(G, c->sig, smax, c->p64, c->p32, c->n_used, c->next_id, npp,
-                                                        c->d.f_inj, c->d_cnt + CNT_INJECTED);
+                                                        c->d.f_inj, c->d_cnt + CNT_INJECTED, c->d_cnt + CNT_QEXP);
   else
     ++c->launches, k_inject_write<false><<<blocks, 256, 0, c->stream>>>(G, c->sig, smax, c->p64, c->p32, c->n_used, c->next_id, npp,
-                                                         c->d.f_inj, c->d_cnt + CNT_INJECTED);
+                                                         c->d.f_inj, c->d_cnt + CNT_INJECTED, c->d_cnt + CNT_QEXP);
   c->n_used += nslots;
   c->next_id += nslots;
 }

@@ -31,7 +31,6 @@ struct Win {
   static constexpr int WI = TI + 2 * H + 3, WJ = TJ + 2 * H + 3, WN = WI * WJ;
 };
 constexpr int NT = 256;                                  // threads per tile CTA
-constexpr int KFIX = 36;                                 // fixed point: 2^-36 of the reference charge
 // Shared-memory accumulation splits each term v (|v| <= 2^36 quanta) into
 // v = h 2^SPLIT + l with |h| <= 2^18, |l| <= 2^17 and sums h and l with
 // native 32-bit shared atomics: both sums stay exact below 2^31 / 2^18 = 8192
@@ -48,7 +47,7 @@ struct Args32 {
   // grows linearly with the step count)
   float dt_lo, inv_dxi_lo, k2_hi, k2_lo;  // k2 = nth / pi (linear theta map)
   float b0_lo, qmdt;     // qmdt = (q/m) dt rounded once
-  float fscale;             // 2^KFIX / qref: float contribution -> int64 units
+  const long long *qexp;    // fixed-point exponent e: one flux unit is 2^(e - KFIX)
   const float *r_n;         // f_r(i) per padded row (FP32)
   const float *f[6];        // FP32 field copies (padded)
   long long *acc[3];        // global fixed-point flux accumulators (padded)
@@ -73,6 +72,7 @@ struct SmemAcc {  // window accessors (shared memory)
   int *lo;                  // 3 * WN : sums of the low parts
   const float *rn;          // f_r(i) of the window's rows
   int wi0, wj0;
+  float fs;                 // flux units per unit charge, 2^(KFIX - e)
   __device__ float fld(int c, int i, int j) const { return f[c * WN + (i - wi0) * WJ + (j - wj0)]; }
   __device__ float rad(int i) const { return rn[i - wi0]; }
   __device__ void add(int k, int i, int j, int h, int l) const {
@@ -84,6 +84,7 @@ struct SmemAcc {  // window accessors (shared memory)
 
 struct GlobAcc {  // global-memory accessors (particles outside the window)
   const Args32 *A;
+  float fs;
   __device__ float fld(int c, int i, int j) const { return A->f[c][pidx(*A, i, j)]; }
   __device__ float rad(int i) const { return A->r_n[i + A->PI]; }
   __device__ void add(int k, int i, int j, int h, int l) const {
@@ -255,7 +256,7 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   // lines in the order it meets them; a line not crossed puts its segment at
   // zero length (zero terms are skipped).  Branch-free, so lanes that cross
   // and lanes that do not run the same instructions.
-  const float scale = qw * A.fscale;
+  const float scale = qw * w.fs;  // exact: fs is a power of two
   const float Dxs = kx == 0 ? nx - dx : (kx > 0 ? (1.f - dx) + nx : -(dx + (1.f - nx)));
   const float Dys = ky == 0 ? ny - dy : (ky > 0 ? (1.f - dy) + ny : -(dy + (1.f - ny)));
   // crossing parameters: any point on the crossed grid line keeps charge
@@ -315,9 +316,9 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
 
 // the rare path: a particle outside its tile's window (inlined: an
 // out-of-line call costs register spills around it in the hot loop)
-__device__ inline bool step32_global(const Args32 &A, uint32_t &cell, float &dx, float &dy, float &ur,
-                                           float &ut, float &up, const float qw) {
-  const GlobAcc gw{&A};
+__device__ inline bool step32_global(const Args32 &A, float fs, uint32_t &cell, float &dx, float &dy, float &ur,
+                                     float &ut, float &up, const float qw) {
+  const GlobAcc gw{&A, fs};
   return step32(A, gw, cell, dx, dy, ur, ut, up, qw);
 }
 
@@ -331,7 +332,7 @@ __device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, 
   const int ci = (int)(cell >> 16) - CELL_BIAS, cj = (int)(cell & 0xffffu);
   bool alive;
   if (win && ci >= wi_lo && ci < wi_hi && cj >= wj_lo && cj < wj_hi) alive = step32(A, sw, cell, dx, dy, ur, ut, up, qw);
-  else alive = step32_global(A, cell, dx, dy, ur, ut, up, qw);
+  else alive = step32_global(A, sw.fs, cell, dx, dy, ur, ut, up, qw);
   if (!alive) { P.qw[k] = 0.f; ++dead; return; }
   P.cell[k] = cell;
   P.dx[k] = dx; P.dy[k] = dy;
@@ -347,6 +348,7 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
   __shared__ int slo[3 * WN];
   __shared__ int sdead;
   int dead = 0;
+  const float fs = __int_as_float((127 + KFIX - qexp_value(A.qexp)) << 23);  // 2^(KFIX - e)
   if (blockIdx.x < (unsigned)A.ntiles) {
     const int t = blockIdx.x;
     const int64_t b0 = A.start[t], b1 = A.start[t + 1];
@@ -363,7 +365,7 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
     }
     for (int e = threadIdx.x; e < WI; e += NT) srn[e] = A.r_n[wi0 + e + A.PI];
     __syncthreads();
-    const SmemAcc<WJ, WN> sw{sf, shi, slo, srn, wi0, wj0};
+    const SmemAcc<WJ, WN> sw{sf, shi, slo, srn, wi0, wj0, fs};
     for (int64_t k = b0 + threadIdx.x; k < b1; k += NT)
       process(A, P, k, true, sw, i0 - H, i0 + TI + H, j0 - H, j0 + TJ + H, dead);
     if (dead) atomicAdd(&sdead, dead);
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
     }
     if (threadIdx.x == 0 && sdead) add_ll(A.cnt + CNT_DELETED, sdead);
   } else {  // particles outside any bin (injected since the last sort)
-    const SmemAcc<WJ, WN> none{nullptr, nullptr, nullptr, nullptr, 0, 0};
+    const SmemAcc<WJ, WN> none{nullptr, nullptr, nullptr, nullptr, 0, 0, fs};
     const int64_t k = A.sorted_end + (int64_t)(blockIdx.x - A.ntiles) * NT + threadIdx.x;
     if (k < A.n_used) process(A, P, k, false, none, 0, 0, 0, 0, dead);
     if (dead) add_ll(A.cnt + CNT_DELETED, dead);
@@ -388,10 +390,11 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
 }
 
 // fixed point -> FP64 fluxes over the ghost band; clears the accumulators
-__global__ void k_flux_from_acc(int nr, int nth, int g, int PI, int PJ, int LD, double q0, long long *a0,
-                                long long *a1, long long *a2, double *F0, double *F1, double *F2) {
+__global__ void k_flux_from_acc(int nr, int nth, int g, int PI, int PJ, int LD, const long long *qexp,
+                                long long *a0, long long *a1, long long *a2, double *F0, double *F1, double *F2) {
   const int j = blockIdx.x * 32 + threadIdx.x, i = -g + (int)(blockIdx.y * 8 + threadIdx.y);
   if (i > nr + g || j > nth) return;
+  const double q0 = ldexp(1.0, qexp_value(qexp) - KFIX);  // charge of one flux unit
   const size_t o = (size_t)(i + PI) * LD + (size_t)(j + PJ);
   F0[o] = (double)a0[o] * q0; a0[o] = 0;
   F1[o] = (double)a1[o] * q0; a1[o] = 0;
@@ -485,19 +488,6 @@ __global__ void k_reduce32(Parts32 P, int64_t n, double qm, double *acc, long lo
   block_sum3(kin, ch, l, acc + ACC_KIN, acc + ACC_CHARGE, live);
 }
 
-__global__ void k_max_abs_qw(const float *qw, int64_t n, unsigned *out) {
-  __shared__ float sm[32];
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  float v = k < n ? fabsf(qw[k]) : 0.f;
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, sm[w]);
-    atomicMax(out, __float_as_uint(v));
-  }
-}
-
 Args32 make_args(pic_ctx *c, double t) {
   const Grid &G = c->G;
   Args32 A;
@@ -510,7 +500,7 @@ Args32 make_args(pic_ctx *c, double t) {
   A.k2_hi = (float)(G.nth / M_PI);
   A.k2_lo = (float)(G.nth / M_PI - (double)A.k2_hi);
   A.inv_nth = (float)(1.0 / G.nth); A.nth_f = (float)G.nth;
-  A.fscale = (float)(1.0 / c->flux_quantum);  // a power of two: the scaling is exact
+  A.qexp = c->d_cnt + CNT_QEXP;
   A.r_n = c->r_n32;
   for (int k = 0; k < 6; ++k) A.f[k] = c->f32[k];
   for (int k = 0; k < 3; ++k) A.acc[k] = c->acc[k];
@@ -530,45 +520,7 @@ Args32 make_args(pic_ctx *c, double t) {
 
 }  // namespace
 
-// fixed-point quantum: 2^-KFIX of the smallest power of two above the largest
-// charge a particle can carry (loaded charges, and for surface injection 16x
-// the vacuum surface charge of one cell)
-static void update_quantum(pic_ctx *c) {
-  double qref = 0.0;
-  if (c->n_used > 0) {
-    unsigned *d;
-    cudaMalloc(&d, sizeof(unsigned));
-    cudaMemsetAsync(d, 0, sizeof(unsigned), c->stream);
-    ++c->launches, k_max_abs_qw<<<(unsigned)((c->n_used + 255) / 256), 256, 0, c->stream>>>(c->p32.qw, c->n_used, d);
-    unsigned h = 0;
-    cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, c->stream);
-    cudaStreamSynchronize(c->stream);
-    cudaFree(d);
-    float f;
-    memcpy(&f, &h, sizeof f);
-    qref = f;
-  }
-  if (c->d.inject) {
-    const pic_desc &d = c->d;
-    const double r0 = d.r_min, rb = c->G.r_min * (d.r_map == PIC_R_LOG ? std::exp(0.5 * c->G.dxi) : 1.0) +
-                                   (d.r_map == PIC_R_LOG ? 0.0 : 0.5 * c->G.dxi);
-    const double sig = 2.0 * std::fabs(d.b0) * d.omega * std::pow(r0, 4) / std::pow(rb, 3) + 1e-300;
-    const double dA = 2.0 * M_PI * r0 * r0 * 2.0;  // whole sphere bounds any cell
-    qref = std::fmax(qref, 16.0 * d.f_inj * sig * dA / d.pairs_per_cell);
-  }
-  if (c->d.flux_quantum > 0.0) { c->flux_quantum = c->d.flux_quantum; return; }
-  if (!(qref > 0.0)) qref = 1.0;
-  const int e = (int)std::ceil(std::log2(qref));
-  const double q0 = std::ldexp(1.0, e - KFIX);
-  if (q0 > c->flux_quantum) c->flux_quantum = q0;
-}
-
-void prepare32(pic_ctx *c) {
-  if (c->flux_quantum == 0.0) update_quantum(c);
-}
-
 void particles32(pic_ctx *c, double t) {
-  if (c->flux_quantum == 0.0) update_quantum(c);
   if (c->n_used == 0) return;
   Args32 A = make_args(c, t);
   const int64_t tail = c->n_used - c->tiles.sorted_end;
@@ -581,7 +533,7 @@ void particles32(pic_ctx *c, double t) {
 void flux_from_acc(pic_ctx *c) {
   const Grid &G = c->G;
   dim3 gr((G.nth + 1 + 31) / 32, (G.nr + 2 * G.g + 1 + 7) / 8);
-  ++c->launches, k_flux_from_acc<<<gr, dim3(32, 8), 0, c->stream>>>(G.nr, G.nth, G.g, G.PI, G.PJ, G.LD, c->flux_quantum,
+  ++c->launches, k_flux_from_acc<<<gr, dim3(32, 8), 0, c->stream>>>(G.nr, G.nth, G.g, G.PI, G.PJ, G.LD, c->d_cnt + CNT_QEXP,
                                                      c->acc[0], c->acc[1], c->acc[2], c->F[0], c->F[1], c->F[2]);
 }
 

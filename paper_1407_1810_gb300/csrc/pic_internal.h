@@ -28,7 +28,40 @@ constexpr int CELL_BIAS = 1024;
 
 // device counters (one int64 array)
 enum Counter { CNT_DELETED = 0, CNT_INJECTED = 1, CNT_LIVE = 2, CNT_SMAX = 3, CNT_GMAX = 4,
-               CNT_QMAX = 5, CNT_SORTED = 6, CNT_N };
+               CNT_QMAX = 5, CNT_SORTED = 6, CNT_QEXP = 7, CNT_N };
+
+// FP32 path fixed-point deposit.  One flux unit is 2^(e - KFIX) with e =
+// ceil(log2 max |qw|) over every charge the context has held (loaded or
+// injected), kept on the device in d_cnt[CNT_QEXP]: the loading and
+// injection kernels raise it with atomicMax, the deposit and the conversion
+// to FP64 read it, so no flux term exceeds 2^KFIX units and the quantum
+// follows the charges without any host round trip.  e is clamped to
+// [QEXP_MIN, QEXP_MAX]; QEXP_NONE marks a context that has held no charge.
+constexpr int KFIX = 36;
+constexpr int QEXP_MIN = -90, QEXP_MAX = 100;
+constexpr long long QEXP_NONE = -1000000;
+
+// ceil(log2 a) of a charge magnitude a > 0, clamped to [QEXP_MIN, QEXP_MAX]
+__device__ inline int charge_exp(float a) {
+  int e;
+  const float m = frexpf(a, &e);  // a = m 2^e, 0.5 <= m < 1
+  if (m == 0.5f) --e;             // a power of two: log2 a = e - 1 exactly
+  return e < QEXP_MIN ? QEXP_MIN : (e > QEXP_MAX ? QEXP_MAX : e);
+}
+
+// Raise the context's exponent to the warp's largest e (QEXP_NONE: no
+// charge).  Every lane of the warp must call it.  The plain read first
+// skips the atomic in the common case of a bound already reached.
+__device__ inline void raise_qexp(long long *qexp, int e) {
+  e = __reduce_max_sync(0xffffffffu, e);
+  if ((threadIdx.x & 31) == 0 && e > *(volatile long long *)qexp) atomicMax(qexp, (long long)e);
+}
+
+// the exponent as the kernels use it (a context with no charge yet: 0)
+__device__ inline int qexp_value(const long long *qexp) {
+  const long long e = *qexp;
+  return e < QEXP_MIN ? 0 : (int)e;
+}
 // device double accumulators
 enum Accum { ACC_KIN = 0, ACC_FIELD = 1, ACC_CHARGE = 2, ACC_N };
 
@@ -59,7 +92,6 @@ struct pic_ctx {
   float *f32[6] = {};     // FP32 gather copies (FP32 path)
   float *r_n32 = nullptr; // f_r(i) per padded row, FP32 (FP32 path)
   long long *acc[3] = {}; // fixed-point flux accumulators (FP32 path)
-  double flux_quantum = 0.0;
   double *Q = nullptr, *Qa = nullptr, *Qt = nullptr, *gsnap = nullptr;
   bool have_snap = false;
   double *sig = nullptr;  // injection: surface charge per cell
@@ -106,7 +138,6 @@ void charge64(pic_ctx *c, double *Q, double *Qa);
 void reduce_particles64(pic_ctx *c);   // kinetic energy, live count, total charge
 // particles32.cu
 void particles32(pic_ctx *c, double t);
-void prepare32(pic_ctx *c);            // host-side set-up the FP32 step needs (fixed-point quantum)
 void flux_from_acc(pic_ctx *c);        // fixed point -> FP64 fluxes, clears the accumulators
 int64_t sort32(pic_ctx *c);            // tile sort + removal; returns live count
 void charge32(pic_ctx *c, double *Q, double *Qa);

@@ -131,3 +131,27 @@ def test_fp32_against_fp64_gpu_path():
     s32.step(100)
     s64.step(100)
     assert rel_l2(s32.fields(), s64.fields()) < FIELD_TOL_NOISY
+
+
+def test_fixed_point_unit_follows_the_charges():
+    """The deposit's unit is 2^(e - 36), e = ceil(log2 max |qw|) over the
+    charges the context has held, raised on the device as charges are
+    loaded and injected: every flux is an integer multiple of that unit and
+    some are odd multiples (any coarser unit would make them all even).
+    A slow spin-up keeps the injected charges growing, so the largest charge
+    ever held is a live one."""
+    cfg = dict(configs.CONFIGS["rotator-1024x1024"], nr=40, nth=32, pairs_per_cell=2, absorb_cells=8, t_spin=1000.0,
+               n_filt=0)
+    s, o, plasma, dt = setup(cfg)
+    for steps in (1, 30):
+        if steps > 1:
+            s.step(steps - 1)
+        qmax = np.max(np.abs(s.particles()["qw"]))  # the charges the next deposit moves
+        s.step(1)
+        unit = 2.0 ** (int(np.ceil(np.log2(qmax))) - 36)
+        F = s.flux()
+        k = F / unit
+        assert np.array_equal(k, np.round(k))
+        assert np.any(np.mod(k, 2) == 1)
+    assert s.moments()["injected"] > 0
+    assert s.moments()["gauss_residual"] < 1e-6
