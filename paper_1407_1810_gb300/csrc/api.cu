@@ -196,10 +196,8 @@ int alloc_parts(pic_ctx *c, int64_t cap) {
     }
     PIC_CUDA(cudaMemset(c->p32.qw, 0, n * sizeof(float)));
   }
-  // scratch: block counts of the compaction / tile bins of the sort
-  size_t sb = ((size_t)cap / 256 + 2) * sizeof(long long);
-  size_t tb = ((size_t)c->tiles.ntiles + 2) * 2 * sizeof(int64_t);
-  c->scratch_bytes = sb > tb ? sb : tb;
+  // scratch: block counts of the FP64 path's stable compaction
+  c->scratch_bytes = ((size_t)cap / 256 + 2) * sizeof(long long);
   PIC_CUDA(cudaMalloc(&c->scratch, c->scratch_bytes));
   c->cap = cap;
   return PIC_OK;
@@ -383,6 +381,26 @@ void prof_drain(pic_ctx *c) {
 }  // namespace
 
 // =============================================================================
+// tile geometry and cell bins of the FP32 path for a tile shape (0: 16 x 16,
+// 1: 8 x 32, 2: 32 x 8 cells)
+static int alloc_bins(pic_ctx *c, int shape) {
+  Tiles &T = c->tiles;
+  T.TI = shape == 1 ? 8 : (shape == 2 ? 32 : 16);
+  T.TJ = shape == 1 ? 32 : (shape == 2 ? 8 : 16);
+  T.tc = T.TI * T.TJ;
+  T.nti = (c->d.nr + 2 * c->G.g + T.TI - 1) / T.TI;
+  T.ntj = (c->d.nth + T.TJ - 1) / T.TJ;
+  T.ntiles = T.nti * T.ntj;
+  T.nbins = (int64_t)T.ntiles * T.tc + 1;
+  const int64_t nblk = T.nbins / SCAN_CHUNK + 2;
+  int e;
+  if ((e = dalloc(&T.start, (size_t)T.nbins + 1)) || (e = dalloc(&T.cursor, (size_t)T.nbins + 1)) ||
+      (e = dalloc(&T.bsum, 2 * (size_t)nblk)))
+    return e;
+  PIC_CUDA(cudaMemset(T.start, 0, (T.nbins + 1) * sizeof(int64_t)));
+  return PIC_OK;
+}
+
 extern "C" int pic_init_grid(pic_ctx **out, const pic_desc *dd, void *stream) {
   if (!out || !dd) return pic_fail(PIC_EINVAL, "null argument");
   *out = nullptr;
@@ -436,16 +454,8 @@ extern "C" int pic_init_grid(pic_ctx **out, const pic_desc *dd, void *stream) {
       if ((e = dalloc(&c->r_n32, rn.size()))) return fail(e);
       PIC_CUDA(cudaMemcpy(c->r_n32, rn.data(), rn.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
-    Tiles &T = c->tiles;
-    T.TI = d.tile_shape == 1 ? 8 : (d.tile_shape == 2 ? 32 : 16);
-    T.TJ = d.tile_shape == 1 ? 32 : (d.tile_shape == 2 ? 8 : 16);
-    T.row0 = -G.g;
-    T.nti = (d.nr + 2 * G.g + T.TI - 1) / T.TI;
-    T.ntj = (d.nth + T.TJ - 1) / T.TJ;
-    T.ntiles = T.nti * T.ntj;
-    if ((e = dalloc(&T.start, (size_t)T.ntiles + 2)) || (e = dalloc(&T.cursor, (size_t)T.ntiles + 2)))
-      return fail(e);
-    cudaMemset(T.start, 0, (T.ntiles + 2) * 8);
+    c->tiles.row0 = -G.g;
+    if ((e = alloc_bins(c, d.tile_shape))) return fail(e);
   }
   if ((e = dalloc(&c->sig, (size_t)d.nth + 1))) return fail(e);
   if ((e = dalloc(&c->d_err, 1)) || (e = dalloc(&c->d_cnt, CNT_N)) || (e = dalloc(&c->d_acc, ACC_N))) return fail(e);
@@ -514,7 +524,10 @@ extern "C" int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const
     cudaMemset(c->d_err, 0, sizeof(int));
     return pic_fail(PIC_EINVAL, "particle outside the grid, zero charge or non-finite momentum (dropped)");
   }
-  if (c->d.precision == PIC_FP32) c->need_sort = true;  // binned by the next step (appended particles are valid unbinned)
+  if (c->d.precision == PIC_FP32) {
+    c->need_sort = true;  // binned by the next step (appended particles are valid unbinned)
+    c->mix_sort = true;
+  }
   return PIC_OK;
 }
 
@@ -862,18 +875,14 @@ static int set_tiles(pic_ctx *c, int shape) {
   cudaStreamSynchronize(c->stream);
   cudaFree(T.start);
   cudaFree(T.cursor);
-  T.start = T.cursor = nullptr;
-  T.TI = shape == 1 ? 8 : (shape == 2 ? 32 : 16);
-  T.TJ = shape == 1 ? 32 : (shape == 2 ? 8 : 16);
-  T.nti = (c->d.nr + 2 * c->G.g + T.TI - 1) / T.TI;
-  T.ntj = (c->d.nth + T.TJ - 1) / T.TJ;
-  T.ntiles = T.nti * T.ntj;
+  cudaFree(T.bsum);
+  T.start = T.cursor = T.bsum = nullptr;
   T.sorted_end = 0;
   int e;
-  if ((e = dalloc(&T.start, (size_t)T.ntiles + 2)) || (e = dalloc(&T.cursor, (size_t)T.ntiles + 2))) return e;
-  PIC_CUDA(cudaMemset(T.start, 0, (T.ntiles + 2) * 8));
+  if ((e = alloc_bins(c, shape))) return e;
   c->d.tile_shape = shape;
   c->need_sort = true;
+  c->mix_sort = true;
   return PIC_OK;
 }
 
@@ -961,7 +970,7 @@ extern "C" int pic_destroy(pic_ctx *c) {
   for (int k = 0; k < 3; ++k) { cudaFree(c->F[k]); cudaFree(c->Ft[k]); cudaFree(c->acc[k]); }
   cudaFree(c->Q); cudaFree(c->Qa); cudaFree(c->Qt); cudaFree(c->gsnap); cudaFree(c->sig);
   cudaFree(c->d_err); cudaFree(c->d_cnt); cudaFree(c->d_acc);
-  cudaFree(c->tiles.start); cudaFree(c->tiles.cursor);
+  cudaFree(c->tiles.start); cudaFree(c->tiles.cursor); cudaFree(c->tiles.bsum);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;

@@ -54,7 +54,8 @@ struct Args32 {
   int *err;
   long long *cnt;
   // tiles
-  int row0, ntj, ntiles, ti, tj;
+  int row0, ntj, ntiles, ti, tj, tc;
+  int mix;                  // sort: 1 = by cell, bins stored transposed; 0 = by tile, order kept
   const int64_t *start;
   int64_t sorted_end, n_used;
   // vacuum
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
   const float fs = __int_as_float((127 + KFIX - qexp_value(A.qexp)) << 23);  // 2^(KFIX - e)
   if (blockIdx.x < (unsigned)A.ntiles) {
     const int t = blockIdx.x;
-    const int64_t b0 = A.start[t], b1 = A.start[t + 1];
+    const int64_t b0 = A.start[(int64_t)t * A.tc], b1 = A.start[(int64_t)(t + 1) * A.tc];
     if (b1 <= b0) return;
     const int i0 = A.row0 + (t / A.ntj) * TI, j0 = (t % A.ntj) * TJ;
     const int wi0 = i0 - H - 1, wj0 = j0 - H - 1;
@@ -401,24 +402,36 @@ __global__ void k_flux_from_acc(int nr, int nth, int g, int PI, int PJ, int LD, 
   F2[o] = (double)a2[o] * q0; a2[o] = 0;
 }
 
-// ---- tile counting sort (drops deleted particles) --------------------------
-__device__ inline int tile_key(const Args32 &A, uint32_t cell, float qw) {
-  if (qw == 0.f) return A.ntiles;  // trash bin
-  const int ci = (int)(cell >> 16) - CELL_BIAS, cj = (int)(cell & 0xffffu);
-  return ((ci - A.row0) / A.ti) * A.ntj + cj / A.tj;
+// ---- counting sort into tile bins (drops removed particles) ---------------
+// Bins are numbered cell by cell, tile-major: key = tile * tc + cell index
+// inside the tile; removed particles go to the last bin, ntiles * tc.  Keys
+// fit in 32 bits: at most (nr + 2g + TI) (nth + TJ) cells with nr, nth <= 32000.
+// Two kinds of sort share the bins:
+//  - mixing (after particles are loaded or the tile shape changes): by cell,
+//    each tile's bin stored transposed (transposed_slot below), so the lanes
+//    of a warp step particles of different cells;
+//  - keeping (every later sort): by tile only (all of a tile's particles in
+//    bin tile * tc), each tile's particles in their previous relative order,
+//    which keeps them mixed: particles move a few cells between sorts.
+__device__ inline int cell_key(const Args32 &A, uint32_t cell, float qw) {
+  if (qw == 0.f) return A.ntiles * A.tc;
+  const int ci = (int)(cell >> 16) - CELL_BIAS - A.row0, cj = (int)(cell & 0xffffu);
+  const int tile = ((ci / A.ti) * A.ntj + cj / A.tj) * A.tc;
+  return A.mix ? tile + (ci % A.ti) * A.tj + cj % A.tj : tile;
 }
 
 __global__ void k_hist(Args32 A, Parts32 P, int64_t n, int64_t *count) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int key = k < n ? tile_key(A, P.cell[k], P.qw[k]) : -1;
+  const int key = k < n ? cell_key(A, P.cell[k], P.qw[k]) : -1;
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   const int lane = threadIdx.x & 31;
   if (key >= 0 && lane == __ffs(peers) - 1)
     atomicAdd(reinterpret_cast<unsigned long long *>(count + key), (unsigned long long)__popc(peers));
 }
 
+// exclusive scan of nb counts by one block (the top level of the scan below);
+// count becomes the cursor and start[nb] the total
 __global__ void k_scan_bins(int64_t *count, int64_t *start, int nb) {
-  // exclusive scan of nb = ntiles + 1 bin counts by one block; count becomes the cursor
   __shared__ int64_t part[1024];
   const int t = threadIdx.x;
   const int per = (nb + 1023) / 1024, a = t * per, b = min(nb, a + per);
@@ -442,17 +455,91 @@ __global__ void k_scan_bins(int64_t *count, int64_t *start, int nb) {
   if (t == 1023) start[nb] = part[1023];
 }
 
-__global__ void k_scatter_tiles(Args32 A, Parts32 S, Parts32 D, int64_t n, int64_t *cursor) {
+// block sum of 256 values (all threads get it)
+__device__ inline int64_t block_sum256(int64_t v, int64_t *sm) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int64_t t = 0;
+  for (int w = 0; w < 8; ++w) t += sm[w];
+  __syncthreads();
+  return t;
+}
+
+// multi-block exclusive scan over nb bins, SCAN_CHUNK bins per block of 256
+// threads: sums of each chunk, a one-block scan of the sums, then each chunk
+// scanned from its offset (16 consecutive bins per thread)
+__global__ void k_scan_sums(const int64_t *count, int64_t nb, int64_t *sums) {
+  __shared__ int64_t sm[8];
+  const int64_t a = blockIdx.x * (int64_t)SCAN_CHUNK;
+  int64_t s = 0;
+  for (int k = threadIdx.x; k < SCAN_CHUNK; k += 256)
+    if (a + k < nb) s += count[a + k];
+  s = block_sum256(s, sm);
+  if (threadIdx.x == 0) sums[blockIdx.x] = s;
+}
+
+__global__ void k_scan_apply(int64_t *count, int64_t *start, int64_t nb, const int64_t *offs, int nblk) {
+  __shared__ int64_t sm[8];
+  const int64_t a = blockIdx.x * (int64_t)SCAN_CHUNK + threadIdx.x * 16;
+  int64_t v[16], s = 0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) { v[i] = a + i < nb ? count[a + i] : 0; s += v[i]; }
+  // exclusive scan of the 256 thread sums
+  int64_t x = s;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sm[w] = x;
+  __syncthreads();
+  int64_t base = offs[blockIdx.x];
+  for (int k = 0; k < w; ++k) base += sm[k];
+  int64_t run = base + x - s;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    if (a + i < nb) { start[a + i] = run; count[a + i] = run; }
+    run += v[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) start[nb] = offs[nblk];
+}
+
+// Order inside a tile's bin.  The counting sort yields the tile's particles
+// cell by cell; they are stored transposed: the cell-ordered sequence fills
+// the columns of a matrix with TRW columns, and the bin holds its rows.  The
+// 32 lanes of a warp, which step consecutive slots, then hold particles about
+// n / TRW apart in cell order: different cells, so their deposits rarely hit
+// the same shared-memory address in one instruction.  (The results do not
+// depend on the order: the deposit sums are exact.)  q: position in cell
+// order, n: particles in the bin; returns the slot.
+constexpr int TRW = 16;
+__device__ inline int64_t transposed_slot(int64_t q, int64_t n) {
+  const int64_t R = (n + TRW - 1) / TRW;  // rows
+  const int64_t L = n - (R - 1) * TRW;    // columns of R elements; the others hold R - 1
+  int64_t c, r;
+  if (q < L * R) { c = q / R; r = q - c * R; }
+  else { const int64_t u = q - L * R; c = L + u / (R - 1); r = u - (c - L) * (R - 1); }
+  return r * TRW + c;
+}
+
+__global__ void k_scatter_cells(Args32 A, Parts32 S, Parts32 D, int64_t n, int64_t *cursor) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int key = k < n ? tile_key(A, S.cell[k], S.qw[k]) : -1;
+  const int trash = A.ntiles * A.tc;
+  const int key = k < n ? cell_key(A, S.cell[k], S.qw[k]) : -1;
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
   unsigned long long base = 0;
-  if (key >= 0 && key < A.ntiles && lane == leader)
+  if (key >= 0 && key < trash && lane == leader)
     base = atomicAdd(reinterpret_cast<unsigned long long *>(cursor + key), (unsigned long long)__popc(peers));
   base = __shfl_sync(0xffffffffu, base, leader);
-  if (key < 0 || key >= A.ntiles) return;
-  const int64_t d = (int64_t)base + __popc(peers & ((1u << lane) - 1u));
+  if (key < 0 || key >= trash) return;
+  int64_t d = (int64_t)base + __popc(peers & ((1u << lane) - 1u));
+  if (A.mix) {
+    const int t = key / A.tc;
+    const int64_t t0 = A.start[(int64_t)t * A.tc], t1 = A.start[(int64_t)(t + 1) * A.tc];
+    d = t0 + transposed_slot(d - t0, t1 - t0);
+  }
   D.cell[d] = S.cell[k]; D.dx[d] = S.dx[k]; D.dy[d] = S.dy[k];
   D.ur[d] = S.ur[k]; D.ut[d] = S.ut[k]; D.up[d] = S.up[k];
   D.qw[d] = S.qw[k]; D.id[d] = S.id[k];
@@ -507,7 +594,8 @@ Args32 make_args(pic_ctx *c, double t) {
   A.err = c->d_err;
   A.cnt = c->d_cnt;
   A.row0 = c->tiles.row0; A.ntj = c->tiles.ntj; A.ntiles = c->tiles.ntiles;
-  A.ti = c->tiles.TI; A.tj = c->tiles.TJ;
+  A.ti = c->tiles.TI; A.tj = c->tiles.TJ; A.tc = c->tiles.tc;
+  A.mix = 0;
   A.start = c->tiles.start;
   A.sorted_end = c->tiles.sorted_end;
   A.n_used = c->n_used;
@@ -540,15 +628,25 @@ void flux_from_acc(pic_ctx *c) {
 int64_t sort32(pic_ctx *c) {
   Tiles &T = c->tiles;
   const int64_t n = c->n_used;
-  if (n == 0) { T.sorted_end = 0; cudaMemsetAsync(T.start, 0, (T.ntiles + 2) * 8, c->stream); return 0; }
+  if (n == 0) {
+    T.sorted_end = 0;
+    cudaMemsetAsync(T.start, 0, (T.nbins + 1) * sizeof(int64_t), c->stream);
+    return 0;
+  }
   Args32 A = make_args(c, 0.0);
+  A.mix = c->mix_sort ? 1 : 0;
+  c->mix_sort = false;
   int64_t *count = T.cursor;
-  cudaMemsetAsync(count, 0, (T.ntiles + 2) * sizeof(int64_t), c->stream);
+  cudaMemsetAsync(count, 0, (T.nbins + 1) * sizeof(int64_t), c->stream);
   const unsigned blocks = (unsigned)((n + 255) / 256);
+  const int nblk = (int)((T.nbins + SCAN_CHUNK - 1) / SCAN_CHUNK);
   ++c->launches, k_hist<<<blocks, 256, 0, c->stream>>>(A, c->p32, n, count);
-  ++c->launches, k_scan_bins<<<1, 1024, 0, c->stream>>>(count, T.start, T.ntiles + 1);
-  ++c->launches, k_scatter_tiles<<<blocks, 256, 0, c->stream>>>(A, c->p32, c->q32, n, count);
-  cudaMemcpyAsync(c->h_pinned, T.start + T.ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+  ++c->launches, k_scan_sums<<<nblk, 256, 0, c->stream>>>(count, T.nbins, T.bsum);
+  ++c->launches, k_scan_bins<<<1, 1024, 0, c->stream>>>(T.bsum, T.bsum + nblk + 1, nblk);
+  ++c->launches, k_scan_apply<<<nblk, 256, 0, c->stream>>>(count, T.start, T.nbins, T.bsum + nblk + 1, nblk);
+  ++c->launches, k_scatter_cells<<<blocks, 256, 0, c->stream>>>(A, c->p32, c->q32, n, count);
+  // particles in cell bins: everything before the bin of removed ones
+  cudaMemcpyAsync(c->h_pinned, T.start + (int64_t)T.ntiles * T.tc, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
   cudaStreamSynchronize(c->stream);
   const int64_t live = *c->h_pinned;
   Parts32 tmp = c->p32;

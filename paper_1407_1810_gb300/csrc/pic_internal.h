@@ -65,14 +65,21 @@ __device__ inline int qexp_value(const long long *qexp) {
 // device double accumulators
 enum Accum { ACC_KIN = 0, ACC_FIELD = 1, ACC_CHARGE = 2, ACC_N };
 
-struct Tiles {  // FP32 path: tile bins after the last sort
+// FP32 path: particles are counting-sorted by cell, cells numbered tile by
+// tile (tile-major, row-major inside a tile), so each tile's particles form
+// one contiguous range ordered by cell
+struct Tiles {
   int TI = 16, TJ = 16, H = 2;  // tile size in cells and halo
   int nti = 0, ntj = 0, ntiles = 0;
   int row0 = 0;                   // first tile row (cell index)
-  int64_t *start = nullptr;       // ntiles + 1 bin starts
-  int64_t *cursor = nullptr;      // scatter cursors
+  int tc = 256;                   // cells per tile, TI * TJ
+  int64_t nbins = 0;              // ntiles * tc cell bins + 1 bin of removed particles
+  int64_t *start = nullptr;       // nbins + 1 bin starts: tile t is [start[t tc], start[(t+1) tc])
+  int64_t *cursor = nullptr;      // nbins + 1 counts, then scatter cursors
+  int64_t *bsum = nullptr;        // 2 (nbins / SCAN_CHUNK + 2) partial sums of the scan
   int64_t sorted_end = 0;         // particles [0, sorted_end) are binned
 };
+constexpr int SCAN_CHUNK = 4096;  // bins per block of the multi-block scan
 
 enum ProfSlot { PROF_PARTICLES = 0, PROF_REDUCE = 1, PROF_FILTER = 2, PROF_FIELDS = 3, PROF_INJECT = 4,
                 PROF_SORT = 5, PROF_N };
@@ -111,6 +118,7 @@ struct pic_ctx {
   int host_err = 0;
   int steps_since_sort = 0;
   bool need_sort = false;
+  bool mix_sort = true;    // FP32: the next sort orders by cell and mixes each tile's bin
   // profiling: one start/stop event pair per phase per step, read back lazily
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;           // recorded events, pairs per phase
