@@ -76,10 +76,12 @@ struct SmemAcc {  // window accessors (shared memory)
   float fs;                 // flux units per unit charge, 2^(KFIX - e)
   __device__ float fld(int c, int i, int j) const { return f[c * WN + (i - wi0) * WJ + (j - wj0)]; }
   __device__ float rad(int i) const { return rn[i - wi0]; }
+  // unconditional: a test for zero terms would branch around every atomic,
+  // which costs more than adding the rare zero
   __device__ void add(int k, int i, int j, int h, int l) const {
     const int e = k * WN + (i - wi0) * WJ + (j - wj0);
-    if (h) atomicAdd(&hi[e], h);
-    if (l) atomicAdd(&lo[e], l);
+    atomicAdd(&hi[e], h);
+    atomicAdd(&lo[e], l);
   }
 };
 
@@ -295,7 +297,7 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
     const float fx = floorf(mx), fy = floorf(my);
     const float wx = mx - fx, wy = my - fy;
     const int i0 = ci + (int)fx, j0 = cj + (int)fy;
-    if (v != 0.f) {
+    {  // v is nonzero for nearly every particle: no test
       int h, l;
       split_fix(v * (1.f - wx) * (1.f - wy), h, l);
       w.add(2, i0, j0, h, l);
