@@ -24,7 +24,12 @@ namespace pic {
 
 namespace {
 
-constexpr int H = 2;  // halo cells around a tile served from shared memory
+// halo cells around a tile served from shared memory.  A particle that
+// drifts beyond it between sorts takes the global-memory path, and one such
+// lane makes its whole warp run that path: with 4 cells (0.003 % of
+// particle-steps at 20 steps per sort, against 0.14 % with 2) the window of
+// 27 x 27 nodes still leaves room for 4 CTAs per SM.
+constexpr int H = 4;
 // window nodes of a TI x TJ tile: the tile, the halo and the stencil reach
 template <int TI, int TJ>
 struct Win {

@@ -69,7 +69,7 @@ enum Accum { ACC_KIN = 0, ACC_FIELD = 1, ACC_CHARGE = 2, ACC_N };
 // tile (tile-major, row-major inside a tile), so each tile's particles form
 // one contiguous range ordered by cell
 struct Tiles {
-  int TI = 16, TJ = 16, H = 2;  // tile size in cells and halo
+  int TI = 16, TJ = 16;          // tile size in cells
   int nti = 0, ntj = 0, ntiles = 0;
   int row0 = 0;                   // first tile row (cell index)
   int tc = 256;                   // cells per tile, TI * TJ
