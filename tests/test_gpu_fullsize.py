@@ -129,13 +129,15 @@ def test_rotator_1024_fp32_full_step_replay():
     assert m["injected"] - m0["injected"] == c["injected"] > 0
     g, r = sim.particles(), o.particles()
     replay_compare_fp32(_every(g, 64, nid), _every(r, 64, nid), TAU)
-    # injected this step: same ids, positions and signs; FP32 charges
+    # injected this step: same ids, positions and signs; the charges follow
+    # the surface E_r, which on the FP32 path carries the deposit's rounding:
+    # held to the FP32 field bar
     gi, ri = by_id(_every(g, 1, None)), by_id(_every(r, 1, None))
     gi = {k: v[gi["id"] >= nid] for k, v in gi.items()}
     ri = {k: v[ri["id"] >= nid] for k, v in ri.items()}
     assert np.array_equal(gi["id"], ri["id"])
     assert np.array_equal(gi["x2"], ri["x2"])
-    assert np.max(np.abs(gi["qw"] - ri["qw"]) / np.abs(ri["qw"])) < 1e-6
+    assert np.max(np.abs(gi["qw"] - ri["qw"]) / np.abs(ri["qw"])) < 1e-5
     assert m["gauss_residual"] <= GAUSS_FP32, m["gauss_residual"]
     sim.close()
 
