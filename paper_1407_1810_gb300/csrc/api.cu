@@ -451,6 +451,10 @@ extern "C" int pic_init_grid(pic_ctx **out, const pic_desc *dd, void *stream) {
     {
       std::vector<float> rn(d.nr + 2 * G.PI + 1);
       for (size_t ii = 0; ii < rn.size(); ++ii) rn[ii] = (float)h_fr(d, G.dxi, (double)ii - G.PI);
+      // displacements per step relative to r stay below dt / r(-g) (speed < c)
+      // and one cell spans dxi in log r: both below 1/64 let the step use
+      // its short series without the general fallback
+      c->small_steps = d.r_map == PIC_R_LOG && G.dxi <= 1.0 / 64 && G.dt / h_fr(d, G.dxi, -G.g) <= 1.0 / 64;
       if ((e = dalloc(&c->r_n32, rn.size()))) return fail(e);
       PIC_CUDA(cudaMemcpy(c->r_n32, rn.data(), rn.size() * sizeof(float), cudaMemcpyHostToDevice));
     }

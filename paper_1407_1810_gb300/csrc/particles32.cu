@@ -146,22 +146,22 @@ __device__ inline void vb_seg(const W &w, float scale, int i, int j, float p1, f
 // log1p, atan and expm1 for the small arguments of a single step: truncated
 // Taylor series (remainders below 1e-11 relative for |x| < 1/32), otherwise
 // the library functions
-__device__ inline float log1p_small(float s) {
-  if (fabsf(s) < 0.03125f)
-    return s * (1.f - s * (0.5f - s * (0.33333334f - s * (0.25f - s * (0.2f - s * 0.16666667f)))));
-  return log1pf(s);
+// (the _series forms alone when the arguments are known to be small)
+__device__ inline float log1p_series(float s) {
+  return s * (1.f - s * (0.5f - s * (0.33333334f - s * (0.25f - s * (0.2f - s * 0.16666667f)))));
 }
+__device__ inline float atan_series(float y, float x) {
+  const float t = y * rcp_(x), t2 = t * t;
+  return t * (1.f - t2 * (0.33333334f - t2 * (0.2f - t2 * 0.14285715f)));
+}
+__device__ inline float exp_series(float y) {
+  return 1.f + y * (1.f + y * (0.5f + y * (0.16666667f + y * (0.041666668f + y * 0.008333334f))));
+}
+__device__ inline float log1p_small(float s) { return fabsf(s) < 0.03125f ? log1p_series(s) : log1pf(s); }
 __device__ inline float atan2_small(float y, float x) {
-  if (x > 0.f && fabsf(y) < 0.03125f * x) {
-    const float t = y * rcp_(x), t2 = t * t;
-    return t * (1.f - t2 * (0.33333334f - t2 * (0.2f - t2 * 0.14285715f)));
-  }
-  return atan2f(y, x);
+  return x > 0.f && fabsf(y) < 0.03125f * x ? atan_series(y, x) : atan2f(y, x);
 }
-__device__ inline float exp_small(float y) {
-  if (fabsf(y) < 0.03125f) return 1.f + y * (1.f + y * (0.5f + y * (0.16666667f + y * (0.041666668f + y * 0.008333334f))));
-  return expf(y);
-}
+__device__ inline float exp_small(float y) { return fabsf(y) < 0.03125f ? exp_series(y) : expf(y); }
 
 __device__ inline float clamp01(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
 
@@ -169,8 +169,9 @@ __device__ inline float clamp01(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
 
 // Specialisations of the step: the grid maps, pusher and analytic field kind
 // fixed at compile time for the two common configurations, so their branches
-// fold away (8 % faster than reading them from the arguments); SPEC_GENERIC
-// reads them at run time.
+// fold away (8 % faster than reading them from the arguments), on grids fine
+// enough that the radial and meridional series need no general fallback
+// (pic_ctx::small_steps); SPEC_GENERIC reads them at run time.
 enum Spec { SPEC_GENERIC = 0, SPEC_MONOPOLE = 1, SPEC_ROTATOR = 2 };
 template <int SPEC>
 struct Flags {
@@ -191,7 +192,8 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   const int ci = (int)(cell >> 16) - CELL_BIAS, cj = (int)(cell & 0xffffu);
   // ---- geometry of the particle's position (Sec. 3.2) -----------------------
   const float rn = w.rad(ci);
-  const float r = F.r_log ? rn * exp_small(dx * A.dxi) : rn + dx * A.dxi;
+  constexpr bool series = SPEC != SPEC_GENERIC;  // arguments below 1/32: no fallback
+  const float r = F.r_log ? rn * (series ? exp_series(dx * A.dxi) : exp_small(dx * A.dxi)) : rn + dx * A.dxi;
   // sin and cos of theta from the distance to the nearer pole, which both
   // offsets resolve to FP32 relative precision (1 - x2/nth would cancel)
   const float x2 = (float)cj + dy;                 // distance to the north pole
@@ -239,13 +241,13 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   const float ir = rcp_(r);
   const float a = Dr * ir, b = Dt * ir, c = Dp * ir;
   const float s = a * (2.f + a) + b * b + c * c;  // (r'/r)^2 - 1
-  const float L1 = F.r_log ? 0.5f * log1p_small(s) : r * s * rcp_(1.f + sqrtf(1.f + s));
+  const float L1 = F.r_log ? 0.5f * (series ? log1p_series(s) : log1p_small(s)) : r * s * rcp_(1.f + sqrtf(1.f + s));
   const float D1 = fmaf(L1, A.inv_dxi, L1 * A.inv_dxi_lo);
   const float p = r + Dr, q = Dt;
   const float Px = p * st + q * ct, Pz = p * ct - q * st;  // displaced point, (R, z) before rotating back
   const float Rn = sqrtf(Px * Px + Dp * Dp);
   const float kap = Px >= 0.f ? (Rn + Px > 0.f ? Dp * Dp * rcp_(Rn + Px) : 0.f) : Rn - Px;  // R' - Px
-  const float dth = atan2_small(q + ct * kap, p + st * kap);                                 // theta' - theta
+  const float dth = series ? atan_series(q + ct * kap, p + st * kap) : atan2_small(q + ct * kap, p + st * kap);
   float D2;
   if (F.th_ea) {
     float sh, ch;
@@ -648,7 +650,7 @@ void particles32(pic_ctx *c, double t) {
   const int64_t tail = c->n_used - c->tiles.sorted_end;
   const int64_t blocks = c->tiles.ntiles + (tail + NT - 1) / NT;
   const pic_desc &d = c->d;
-  const int spec = d.r_map == PIC_R_LOG && d.pusher == PIC_VAY
+  const int spec = c->small_steps && d.r_map == PIC_R_LOG && d.pusher == PIC_VAY
                        ? (d.th_map == PIC_TH_LINEAR && d.vacuum == PIC_VAC_MONOPOLE ? SPEC_MONOPOLE
                           : d.th_map == PIC_TH_EQUAL_AREA && d.vacuum == PIC_VAC_MONOPOLE_ROTATOR ? SPEC_ROTATOR
                                                                                                    : SPEC_GENERIC)
