@@ -120,7 +120,9 @@ int pic_init_grid(pic_ctx **out, const pic_desc *d, void *stream);
 
 /* Append n particles (Sec. 3.3 state).  x1, x2: grid coordinates; u_r, u_th,
  * u_ph: gamma v in the local spherical basis; qw: signed macro-charge (nonzero).
- * All arrays are FP64 of length n, host or device per mem.  Particle ids are
+ * All arrays are FP64 of length n, host or device per mem; page-locked
+ * (pinned) host arrays are read in place by the GPU, pageable ones are staged
+ * through device memory in chunks.  Particle ids are
  * assigned consecutively from the context's id counter.  The FP32 path stores
  * x as (cell, FP32 offset) and u, qw in FP32.  Errors: PIC_EINVAL (x outside
  * [-g, nr+g] x [0, nth] with g = n_filt+2, qw == 0, on the FP32 path |qw|

@@ -477,6 +477,22 @@ extern "C" int pic_init_grid(pic_ctx **out, const pic_desc *dd, void *stream) {
   return PIC_OK;
 }
 
+// Device-visible addresses of six host arrays that are page-locked (pinned):
+// the load kernel then reads them in place -- on a Grace host over
+// NVLink-C2C -- with no staging copy.  False for pageable memory.
+static bool pinned_views(const double *const src[6], const double *dv[6]) {
+  for (int k = 0; k < 6; ++k) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, src[k]) != cudaSuccess) {
+      cudaGetLastError();  // clear the sticky-free error of the query
+      return false;
+    }
+    if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return false;
+    dv[k] = static_cast<const double *>(a.devicePointer);
+  }
+  return true;
+}
+
 extern "C" int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const double *x2, const double *u_r,
                                   const double *u_th, const double *u_ph, const double *qw, int32_t mem) {
   if (!c) return pic_fail(PIC_EINVAL, "null context");
@@ -492,16 +508,22 @@ extern "C" int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const
   } else if (c->n_used + n + room > c->cap) {
     if ((e = grow_parts(c, (c->n_used + n + room) * 3 / 2 + 1024))) return e;
   }
-  // device views of the input (host input is staged in chunks)
-  const int64_t chunk = mem == PIC_MEM_DEVICE ? n : ((int64_t)1 << 22);
+  // device views of the input: device arrays and pinned host arrays are read
+  // in place, pageable host arrays are staged in chunks
+  const double *const all[6] = {x1, x2, u_r, u_th, u_ph, qw};
+  const double *pv[6];
+  const bool direct = mem == PIC_MEM_DEVICE || pinned_views(all, pv);
+  if (mem == PIC_MEM_DEVICE)
+    for (int k = 0; k < 6; ++k) pv[k] = all[k];
+  const int64_t chunk = direct ? n : ((int64_t)1 << 22);
   double *stage = nullptr;
-  if (mem != PIC_MEM_DEVICE) PIC_CUDA(cudaMalloc((void **)&stage, 6 * (size_t)chunk * sizeof(double)));
+  if (!direct) PIC_CUDA(cudaMalloc((void **)&stage, 6 * (size_t)chunk * sizeof(double)));
   for (int64_t off = 0; off < n; off += chunk) {
     const int64_t m = std::min(chunk, n - off);
     const double *src[6] = {x1 + off, x2 + off, u_r + off, u_th + off, u_ph + off, qw + off};
     const double *dv[6];
     for (int k = 0; k < 6; ++k) {
-      if (mem == PIC_MEM_DEVICE) dv[k] = src[k];
+      if (direct) dv[k] = pv[k] + off;
       else {
         double *s = stage + (size_t)k * chunk;
         cudaMemcpyAsync(s, src[k], m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
@@ -515,7 +537,7 @@ extern "C" int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const
     else
       ++c->launches, k_load32<<<blocks, 256, 0, c->stream>>>(c->G, c->p32, c->n_used + off, m, dv[0], dv[1], dv[2], dv[3], dv[4],
                                              dv[5], c->next_id + off, c->d_err, c->d_cnt + CNT_QEXP);
-    if (mem != PIC_MEM_DEVICE) PIC_CUDA(cudaStreamSynchronize(c->stream));
+    if (!direct) PIC_CUDA(cudaStreamSynchronize(c->stream));
   }
   PIC_CUDA(cudaGetLastError());
   PIC_CUDA(cudaStreamSynchronize(c->stream));

@@ -198,3 +198,22 @@ def test_capacity_grows_under_injection():
     # differences step by step: 1e-12 at 40 steps, growing smoothly afterwards
     assert errs[0] < TOL, errs
     assert errs[-1] < 1e-8, errs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_pinned_and_pageable_host_loads_agree(precision):
+    """Pinned host arrays are read in place by the load kernel, pageable ones
+    are staged through device memory: both give the same particle state."""
+    import torch
+
+    from paper_1407_1810_gb300 import picsar as P
+
+    cfg = dict(configs.CONFIGS["monopole-64x64"], nr=24, nth=16, pairs_per_cell=2, precision=precision)
+    s1, _, plasma, dt = setup(cfg)  # numpy arrays: pageable
+    b0, _ = configs.physics(cfg, dt)
+    s2 = P.Simulation(P.make_desc(**configs.desc_kwargs(cfg, dt, b0, precision=precision)))
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(plasma[k])).pin_memory() for k in KEYS}
+    s2.load(*(pinned[k] for k in KEYS))
+    a, b = by_id(s1.particles()), by_id(s2.particles())
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
