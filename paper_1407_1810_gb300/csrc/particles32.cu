@@ -595,13 +595,17 @@ __global__ void k_reduce32(Parts32 P, int64_t n, double qm, double *acc, long lo
   double kin = 0.0, ch = 0.0;
   long long l = 0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    if (P.qw[k] == 0.f) continue;
-    const double q = P.qw[k], a = P.ur[k], b = P.ut[k], c = P.up[k];
-    kin += fabs(q) / qm * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
+    const float q = P.qw[k];
+    if (q == 0.f) continue;
+    const float a = P.ur[k], b = P.ut[k], c = P.up[k], u2 = a * a + b * b + c * c;
+    // each particle's (gamma - 1) |qw| in FP32 (gamma - 1 = u^2 / (1 + gamma): no
+    // cancellation), summed in FP64; FP64 square roots would make this diagnostic
+    // FP64-bound on this part
+    kin += (double)(fabsf(q) * (u2 / (1.f + sqrtf(1.f + u2))));
     ch += q;
     l += 1;
   }
-  block_sum3(kin, ch, l, acc + ACC_KIN, acc + ACC_CHARGE, live);
+  block_sum3(kin / qm, ch, l, acc + ACC_KIN, acc + ACC_CHARGE, live);
 }
 
 Args32 make_args(pic_ctx *c, double t) {
