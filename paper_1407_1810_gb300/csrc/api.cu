@@ -95,8 +95,10 @@ int build_metric(pic_ctx *c) {
   const pic_desc &d = c->d;
   Grid &G = c->G;
   const int NRr = d.nr + 2 * G.PI + 1, NC = G.LD;
-  // 16 row tables, 12 column tables
-  const int nrow = 14, ncol = 12;
+  // row tables 0-12 (geometry) and 13-20 (update coefficients); column
+  // tables 0-11 (geometry) and 12-16 (update coefficients)
+  const int nrow = 21, ncol = 17;
+  const double hh = 0.5 * G.dt, dt = G.dt;
   std::vector<double> h((size_t)nrow * NRr + (size_t)ncol * NC, 0.0);
   auto row = [&](int t) { return h.data() + (size_t)t * NRr; };
   auto col = [&](int t) { return h.data() + (size_t)nrow * NRr + (size_t)t * NC; };
@@ -116,6 +118,15 @@ int build_metric(pic_ctx *c) {
     row(8)[ii] = rh - rhm;
     row(9)[ii] = 1.0 - sigma_star(d, i);
     row(10)[ii] = 1.0 - sigma_star(d, i + 0.5);
+    const double id2n = 2.0 / (rn1 * rn1 - rn * rn), id2h = 2.0 / (rh * rh - rhm * rhm);
+    row(13)[ii] = hh / rn;
+    row(14)[ii] = hh * id2n * rn;
+    row(15)[ii] = hh * id2n * rn1;
+    row(16)[ii] = hh * id2n * (rn1 - rn);
+    row(17)[ii] = dt / rh;
+    row(18)[ii] = dt * id2h * rhm;
+    row(19)[ii] = dt * id2h * rh;
+    row(20)[ii] = dt * id2h * (rh - rhm);
     if (i >= 0 && i <= d.nr) {
       double a = std::fmax(i - 0.5, 0.0), b = std::fmin(i + 0.5, (double)d.nr);
       row(11)[ii] = 2.0 * M_PI / 3.0 * (std::pow(fr(b), 3) - std::pow(fr(a), 3));
@@ -141,6 +152,19 @@ int build_metric(pic_ctx *c) {
     }
     if (j >= 1 && j < d.nth) col(6)[cc] = 1.0 / (th(j + 0.5) - th(j - 0.5));
   }
+  for (int cc = 0; cc < NC; ++cc) {  // products of the geometry columns (zero where a factor is)
+    const int j = cc - G.PJ;
+    const double stb = j >= 0 && j < d.nth ? col(4)[cc] : 0.0, stbm = cc >= 1 && j >= 1 && j <= d.nth ? col(4)[cc - 1] : 0.0;
+    if (j >= 0 && j < d.nth) {
+      col(12)[cc] = col(0)[cc] * col(2)[cc];
+      col(13)[cc] = col(0)[cc + 1] * col(2)[cc];
+      col(16)[cc] = col(5)[cc] * (0.5 / M_PI);
+    }
+    if (j >= 0 && j <= d.nth) {
+      col(14)[cc] = stb * col(9)[cc];
+      col(15)[cc] = stbm * col(9)[cc];
+    }
+  }
   PIC_CUDA(cudaMalloc((void **)&c->metric_buf, h.size() * sizeof(double)));
   PIC_CUDA(cudaMemcpy(c->metric_buf, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
   const double *R = c->metric_buf, *C = c->metric_buf + (size_t)nrow * NRr;
@@ -153,6 +177,9 @@ int build_metric(pic_ctx *c) {
   m.sin_t = dc(0); m.cos_t = dc(1); m.inv_dcos_t = dc(2); m.inv_dth_t = dc(3);
   m.sin_tb = dc(4); m.inv_sin_tb = dc(5); m.inv_dtb = dc(6);
   m.inv_dcos_tb = dc(9); m.vol_t_n = dc(10); m.vol_t_h = dc(11);
+  m.bR = dr(13); m.bT0 = dr(14); m.bT1 = dr(15); m.bP = dr(16);
+  m.eR = dr(17); m.eT0 = dr(18); m.eT1 = dr(19); m.eP = dr(20);
+  m.cB1 = dc(12); m.cB2 = dc(13); m.cE1 = dc(14); m.cE2 = dc(15); m.cF = dc(16);
   return PIC_OK;
 }
 

@@ -21,28 +21,25 @@ inline dim3 grid2(int ni, int nj) { return dim3((nj + BX - 1) / BX, (ni + BY - 1
 
 // B <- B - h c curl E over the faces of the primary grid (first three lines of
 // Eq. discreteeq).  One thread per node (i, j), 0 <= i <= nr, 0 <= j <= nth.
+// (the factors of dt / 2 and the metric are folded into the row and column
+// coefficient tables of Metric: a few FP64 FMAs per node, the rate that
+// limits this kernel)
 __global__ void k_b_half(Grid G, const double *__restrict__ Er, const double *__restrict__ Et,
                          const double *__restrict__ Ep, double *__restrict__ Br, double *__restrict__ Bt,
-                         double *__restrict__ Bp, double h) {
+                         double *__restrict__ Bp) {
   const int j = blockIdx.x * BX + threadIdx.x, i = blockIdx.y * BY + threadIdx.y;
   if (i > G.nr || j > G.nth) return;
   const Metric &m = G.m;
   const int ri = i + G.PI, cj = j + G.PJ;
   const size_t o = gidx(G, i, j);
-  if (j < G.nth) {  // B_r at (i, j+1/2)
-    double rhs = Ep[o] * m.sin_t[cj] - Ep[o + 1] * m.sin_t[cj + 1];
-    Br[o] += h * m.inv_r_n[ri] * rhs * m.inv_dcos_t[cj];
-  }
+  if (j < G.nth)  // B_r at (i, j+1/2)
+    Br[o] += m.bR[ri] * (Ep[o] * m.cB1[cj] - Ep[o + 1] * m.cB2[cj]);
   if (i < G.nr) {
-    if (j >= 1 && j < G.nth) {  // B_th at (i+1/2, j); zero on the axis
-      double rhs = m.r_n[ri + 1] * Ep[o + G.LD] - m.r_n[ri] * Ep[o];
-      Bt[o] += h * rhs * m.inv_dr2_n[ri];
-    }
-    if (j < G.nth) {  // B_ph at (i+1/2, j+1/2)
-      double rhs = (m.r_n[ri] * Et[o] - m.r_n[ri + 1] * Et[o + G.LD]) -
-                   (Er[o] - Er[o + 1]) * m.dr_n[ri] * m.inv_dth_t[cj];
-      Bp[o] += h * rhs * m.inv_dr2_n[ri];
-    }
+    const double t0 = m.bT0[ri], t1 = m.bT1[ri];
+    if (j >= 1 && j < G.nth)  // B_th at (i+1/2, j); zero on the axis
+      Bt[o] += t1 * Ep[o + G.LD] - t0 * Ep[o];
+    if (j < G.nth)  // B_ph at (i+1/2, j+1/2)
+      Bp[o] += (t0 * Et[o] - t1 * Et[o + G.LD]) - (Er[o] - Er[o + 1]) * (m.bP[ri] * m.inv_dth_t[cj]);
   }
 }
 
@@ -54,24 +51,21 @@ __global__ void k_b_half(Grid G, const double *__restrict__ Er, const double *__
 __global__ void k_e_full(Grid G, double *__restrict__ Er, double *__restrict__ Et, double *__restrict__ Ep,
                          const double *__restrict__ Br, const double *__restrict__ Bt,
                          const double *__restrict__ Bp, const double *__restrict__ Fr,
-                         const double *__restrict__ Ft, const double *__restrict__ Fp, double dt) {
+                         const double *__restrict__ Ft, const double *__restrict__ Fp) {
   const int j = blockIdx.x * BX + threadIdx.x, i = blockIdx.y * BY + threadIdx.y;
   if (i > G.nr || j > G.nth) return;
   const Metric &m = G.m;
   const int ri = i + G.PI, cj = j + G.PJ;
   const size_t o = gidx(G, i, j);
-  if (i < G.nr) {  // E_r at (i+1/2, j)
-    double circ = Bp[o] * m.sin_tb[cj] - Bp[o - 1] * m.sin_tb[cj - 1];
-    Er[o] += (dt * m.inv_r_h[ri] * circ - Fr[o] * m.inv_area_h[ri]) * m.inv_dcos_tb[cj];
-  }
+  if (i < G.nr)  // E_r at (i+1/2, j)
+    Er[o] += m.eR[ri] * (Bp[o] * m.cE1[cj] - Bp[o - 1] * m.cE2[cj]) - Fr[o] * (m.inv_area_h[ri] * m.inv_dcos_tb[cj]);
   if (i >= 1 && i < G.nr) {
-    if (j < G.nth) {  // E_th at (i, j+1/2)
-      double circ = m.r_h[ri - 1] * Bp[o - G.LD] - m.r_h[ri] * Bp[o];
-      Et[o] += (dt * circ - Ft[o] * m.inv_sin_tb[cj] * (0.5 / PI_D)) * m.inv_dr2_h[ri];
-    }
+    const double t0 = m.eT0[ri], t1 = m.eT1[ri], id2 = m.inv_dr2_h[ri];
+    if (j < G.nth)  // E_th at (i, j+1/2)
+      Et[o] += (t0 * Bp[o - G.LD] - t1 * Bp[o]) - Ft[o] * (m.cF[cj] * id2);
     if (j >= 1 && j < G.nth) {  // E_ph at (i, j)
-      double circ = (m.r_h[ri] * Bt[o] - m.r_h[ri - 1] * Bt[o - G.LD]) - (Br[o] - Br[o - 1]) * m.dr_h[ri] * m.inv_dtb[cj];
-      Ep[o] += (dt * circ - Fp[o] * m.inv_dtb[cj]) * m.inv_dr2_h[ri];
+      const double idt = m.inv_dtb[cj];
+      Ep[o] += ((t1 * Bt[o] - t0 * Bt[o - G.LD]) - (Br[o] - Br[o - 1]) * (m.eP[ri] * idt)) - Fp[o] * (idt * id2);
     }
   }
 }
@@ -258,13 +252,13 @@ __global__ void k_field_energy(Grid G, const double *f0, const double *f1, const
 void fields_b_half(pic_ctx *c) {
   const Grid &G = c->G;
   ++c->launches, k_b_half<<<grid2(G.nr + 1, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(G, c->f[ER], c->f[ETH], c->f[EPH], c->f[BR],
-                                                                      c->f[BTH], c->f[BPH], 0.5 * G.dt);
+                                                                      c->f[BTH], c->f[BPH]);
 }
 
 void fields_e_full(pic_ctx *c) {
   const Grid &G = c->G;
   ++c->launches, k_e_full<<<grid2(G.nr + 1, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(
-      G, c->f[ER], c->f[ETH], c->f[EPH], c->f[BR], c->f[BTH], c->f[BPH], c->F[0], c->F[1], c->F[2], G.dt);
+      G, c->f[ER], c->f[ETH], c->f[EPH], c->f[BR], c->f[BTH], c->f[BPH], c->F[0], c->F[1], c->F[2]);
 }
 
 void fields_fill_ghosts(pic_ctx *c) {

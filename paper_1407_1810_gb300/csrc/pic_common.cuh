@@ -47,6 +47,17 @@ struct Metric {
   const double *inv_dcos_tb;        // 1 / (cos tb_{j-1} - cos tb_j), caps at j = 0, nth
   const double *inv_dtb;            // 1 / (tb_j - tb_{j-1})
   const double *vol_t_n, *vol_t_h;  // meridional factors of the cell volumes
+  // the Yee update's factors folded into per-row and per-column coefficients
+  // (h = dt / 2 for the B half steps, dt for E), so each node costs a few FMAs
+  const double *bR;                 // h / r_i                                  (B_r)
+  const double *bT0, *bT1;          // h 2 r_i / (r_{i+1}^2 - r_i^2), same with r_{i+1}  (B_th, B_ph)
+  const double *bP;                 // h 2 (r_{i+1} - r_i) / (r_{i+1}^2 - r_i^2)  (B_ph)
+  const double *eR;                 // dt / rb_i                                (E_r)
+  const double *eT0, *eT1;          // dt 2 rb_{i-1} / (rb_i^2 - rb_{i-1}^2), same with rb_i  (E_th, E_ph)
+  const double *eP;                 // dt 2 (rb_i - rb_{i-1}) / (rb_i^2 - rb_{i-1}^2)  (E_ph)
+  const double *cB1, *cB2;          // sin th_j / dcos_j, sin th_{j+1} / dcos_j  (B_r)
+  const double *cE1, *cE2;          // sin tb_j / dcos_tb_j, sin tb_{j-1} / dcos_tb_j  (E_r)
+  const double *cF;                 // 1 / (2 pi sin tb_j)                      (E_th flux)
 };
 
 struct Grid {
