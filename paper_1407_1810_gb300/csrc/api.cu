@@ -487,6 +487,7 @@ extern "C" int pic_init_grid(pic_ctx **out, const pic_desc *dd, void *stream) {
     }
     c->tiles.row0 = -G.g;
     if ((e = alloc_bins(c, d.tile_shape))) return fail(e);
+    if (tiles32_setup(c)) return fail(pic_fail(PIC_ECUDA, "tensor maps of the field window could not be encoded"));
   }
   if ((e = dalloc(&c->sig, (size_t)d.nth + 1))) return fail(e);
   if ((e = dalloc(&c->d_err, 1)) || (e = dalloc(&c->d_cnt, CNT_N)) || (e = dalloc(&c->d_acc, ACC_N))) return fail(e);

@@ -18,6 +18,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime's driver entry point)
+
 #include "pic_internal.h"
 
 namespace pic {
@@ -30,6 +32,10 @@ namespace {
 // particle-steps at 20 steps per sort, against 0.14 % with 2) the window of
 // 27 x 27 nodes still leaves room for 4 CTAs per SM.
 constexpr int H = 4;
+// the last tile of a row or column reaches up to its side + H + 1 nodes past
+// the grid's ghost band: the padding of the grid arrays must hold it for the
+// longest tile side (32 cells), so the window stays inside the allocation
+static_assert(32 + H + 1 <= PAD, "grid padding must cover every tile window");
 // window nodes of a TI x TJ tile: the tile, the halo and the stencil reach
 template <int TI, int TJ>
 struct Win {
@@ -369,14 +375,66 @@ __device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, 
   P.ur[k] = ur; P.ut[k] = ut; P.up[k] = up;
 }
 
+// ---- the field window through the tensor memory accelerator ---------------
+// Each FP32 field is a 2-D tensor (LD columns x rows of the padded grid).  A
+// tile's window (WI rows x WJ columns from (wi0, wj0)) is fetched as one box
+// per field whose first column is wj0 - WOFF: with the padding PJ a multiple of
+// 8 and every tile's j0 a multiple of 8, that column is a multiple of 4 floats
+// (16 bytes), as a tiled copy requires; the box is WB columns wide, a whole
+// number of 16-byte units.  The boxes land in a staging area, are laid out at
+// the window's own pitch WJ (odd, so lanes in different rows fall in different
+// banks) and the staging area then becomes the deposit accumulators.
+constexpr int WOFF = 3;
+static_assert((PAD - H - 1 - WOFF) % 8 == 0, "window box column must stay 16-byte aligned");
+template <int TI, int TJ>
+struct Box {
+  static constexpr int WI = Win<TI, TJ>::WI, WJ = Win<TI, TJ>::WJ, WN = Win<TI, TJ>::WN;
+  static constexpr int WB = (WOFF + WJ + 3) / 4 * 4;        // box width (floats)
+  static constexpr int SLOT = (WI * WB + 31) / 32 * 32;     // one field's box, 128-byte multiple
+  static constexpr int SF = (6 * WN + 31) / 32 * 32;        // laid-out window (floats)
+  static constexpr int U = 6 * SLOT > 6 * WN ? 6 * SLOT : 6 * WN;  // staging, then accumulators
+};
+
+struct TileMaps {  // the six field tensors for the current tile shape (kernel parameter)
+  CUtensorMap m[6];
+};
+
+__device__ inline uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void tma_window(float *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// wait for phase 0 of the window barrier, at most `limit` polls
+__device__ inline bool window_wait(uint64_t *bar, long long limit) {
+  for (long long k = 0; k < limit; ++k) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar))
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 template <int TI, int TJ, int SPEC>
-__global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
-  constexpr int WI = Win<TI, TJ>::WI, WJ = Win<TI, TJ>::WJ, WN = Win<TI, TJ>::WN;
-  __shared__ float sf[6 * WN];
+__global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P, const __grid_constant__ TileMaps maps) {
+  using BX_ = Box<TI, TJ>;
+  constexpr int WI = BX_::WI, WJ = BX_::WJ, WN = BX_::WN, WB = BX_::WB, SLOT = BX_::SLOT;
+  __shared__ __align__(128) float sbuf[BX_::SF + BX_::U];
+  float *const sf = sbuf;                                      // 6 WN: the window
+  float *const stage = sbuf + BX_::SF;                         // 6 SLOT: the boxes, first
+  int *const shi = reinterpret_cast<int *>(sbuf + BX_::SF);    // 3 WN: then the accumulators
+  int *const slo = shi + 3 * WN;                               // 3 WN
   __shared__ float srn[WI];
-  __shared__ int shi[3 * WN];
-  __shared__ int slo[3 * WN];
-  __shared__ int sdead;
+  __shared__ int sdead, sok;
+  __shared__ __align__(8) uint64_t sbar;
   int dead = 0;
   const float fs = __int_as_float((127 + KFIX - qexp_value(A.qexp)) << 23);  // 2^(KFIX - e)
   if (blockIdx.x < (unsigned)A.ntiles) {
@@ -385,15 +443,36 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P) {
     if (b1 <= b0) return;
     const int i0 = A.row0 + (t / A.ntj) * TI, j0 = (t % A.ntj) * TJ;
     const int wi0 = i0 - H - 1, wj0 = j0 - H - 1;
-    if (threadIdx.x == 0) sdead = 0;
-    for (int e = threadIdx.x; e < WN; e += NT) {
-      const size_t o = pidx(A, wi0 + e / WJ, wj0 + e % WJ);
+    if (threadIdx.x == 0) {
+      sdead = 0;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sbar)));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&sbar)),
+                   "r"((uint32_t)(6 * WI * WB * sizeof(float)))
+                   : "memory");
+      const int x = wj0 - WOFF + A.PJ, y = wi0 + A.PI;  // x: a multiple of 4 (static_assert above)
 #pragma unroll
-      for (int c = 0; c < 6; ++c) sf[c * WN + e] = A.f[c][o];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) { shi[c * WN + e] = 0; slo[c * WN + e] = 0; }
+      for (int c = 0; c < 6; ++c) tma_window(stage + c * SLOT, &maps.m[c], x, y, &sbar);
+      // bounded wait: on a timeout the error is latched, the copies get a
+      // second bounded wait (they write into this block's shared memory) and
+      // the tile is skipped
+      bool ok = window_wait(&sbar, 1ll << 26);
+      if (!ok) {
+        atomicOr(A.err, ERR_TIMEOUT);
+        window_wait(&sbar, 1ll << 26);
+      }
+      sok = ok ? 1 : 0;
     }
     for (int e = threadIdx.x; e < WI; e += NT) srn[e] = A.r_n[wi0 + e + A.PI];
+    __syncthreads();
+    if (!sok) return;
+    for (int e = threadIdx.x; e < WN; e += NT) {
+      const int r = e / WJ, q = e % WJ;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) sf[c * WN + e] = stage[c * SLOT + r * WB + q + WOFF];
+    }
+    __syncthreads();  // the staging area becomes the accumulators
+    for (int e = threadIdx.x; e < 3 * WN; e += NT) { shi[e] = 0; slo[e] = 0; }
     __syncthreads();
     const SmemAcc<WJ, WN> sw{sf, shi, slo, srn, wi0, wj0, fs};
     for (int64_t k = b0 + threadIdx.x; k < b1; k += NT)
@@ -643,9 +722,49 @@ Args32 make_args(pic_ctx *c, double t) {
 
 template <int SPEC>
 static void launch_tiles(pic_ctx *c, const Args32 &A, int64_t blocks) {
-  if (c->tiles.TI == 8) ++c->launches, k_tiles32<8, 32, SPEC><<<(unsigned)blocks, NT, 0, c->stream>>>(A, c->p32);
-  else if (c->tiles.TI == 32) ++c->launches, k_tiles32<32, 8, SPEC><<<(unsigned)blocks, NT, 0, c->stream>>>(A, c->p32);
-  else ++c->launches, k_tiles32<16, 16, SPEC><<<(unsigned)blocks, NT, 0, c->stream>>>(A, c->p32);
+  const TileMaps &M = *reinterpret_cast<const TileMaps *>(c->tile_maps[c->d.tile_shape]);
+  if (c->tiles.TI == 8) ++c->launches, k_tiles32<8, 32, SPEC><<<(unsigned)blocks, NT, 0, c->stream>>>(A, c->p32, M);
+  else if (c->tiles.TI == 32) ++c->launches, k_tiles32<32, 8, SPEC><<<(unsigned)blocks, NT, 0, c->stream>>>(A, c->p32, M);
+  else ++c->launches, k_tiles32<16, 16, SPEC><<<(unsigned)blocks, NT, 0, c->stream>>>(A, c->p32, M);
+}
+
+// The six field tensors of every tile shape (at context creation; the arrays
+// do not move afterwards).  0 or -1 when the encoder is unavailable or
+// rejects a map.
+template <int TI, int TJ>
+static int encode_maps(pic_ctx *c, void *fn, unsigned char *out) {
+  using Enc = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                           const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                           CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  const Grid &G = c->G;
+  const cuuint64_t dims[2] = {(cuuint64_t)G.LD, (cuuint64_t)(c->grid_elems / G.LD)};
+  const cuuint64_t strides[1] = {(cuuint64_t)G.LD * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)Box<TI, TJ>::WB, (cuuint32_t)Box<TI, TJ>::WI};
+  const cuuint32_t estr[2] = {1, 1};
+  TileMaps *M = reinterpret_cast<TileMaps *>(out);
+  for (int k = 0; k < 6; ++k) {
+    const CUresult r = reinterpret_cast<Enc>(fn)(&M->m[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->f32[k], dims, strides,
+                                                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return -1;
+  }
+  return 0;
+}
+
+int tiles32_setup(pic_ctx *c) {
+  static_assert(sizeof(TileMaps) <= sizeof(c->tile_maps[0]), "tensor-map storage");
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return -1;
+  // the grid arrays' pitch must be a whole number of 16-byte units
+  if ((c->G.LD * sizeof(float)) % 16 != 0 || (c->G.PJ - H - 1 - WOFF) % 4 != 0) return -1;
+  if (encode_maps<16, 16>(c, fn, c->tile_maps[0]) || encode_maps<8, 32>(c, fn, c->tile_maps[1]) ||
+      encode_maps<32, 8>(c, fn, c->tile_maps[2]))
+    return -1;
+  return 0;
 }
 
 void particles32(pic_ctx *c, double t) {

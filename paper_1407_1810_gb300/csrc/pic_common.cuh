@@ -17,7 +17,7 @@
 
 namespace pic {
 
-constexpr int PAD = 24;  // padding rows/columns on each side (covers tile windows)
+constexpr int PAD = 40;  // padding rows/columns on each side: covers every tile window (tile side + halo <= PAD)
 
 enum Comp { ER = 0, ETH = 1, EPH = 2, BR = 3, BTH = 4, BPH = 5 };
 // staggering of Eq. (offseteq): 1 = half-integer position

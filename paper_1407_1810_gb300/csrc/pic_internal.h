@@ -99,6 +99,7 @@ struct pic_ctx {
   float *f32[6] = {};     // FP32 gather copies (FP32 path)
   float *r_n32 = nullptr; // f_r(i) per padded row, FP32 (FP32 path)
   long long *acc[3] = {}; // fixed-point flux accumulators (FP32 path)
+  alignas(64) unsigned char tile_maps[3][6 * 128] = {}; // FP32: field tensor maps per tile shape (TMA)
   double *Q = nullptr, *Qa = nullptr, *Qt = nullptr, *gsnap = nullptr;
   bool have_snap = false;
   double *sig = nullptr;  // injection: surface charge per cell
@@ -146,6 +147,7 @@ int64_t compact64(pic_ctx *c);         // stable removal of dead slots; returns 
 void charge64(pic_ctx *c, double *Q, double *Qa);
 void reduce_particles64(pic_ctx *c);   // kinetic energy, live count, total charge
 // particles32.cu
+int tiles32_setup(pic_ctx *c);         // tensor maps of the field window (FP32 path, at creation)
 void particles32(pic_ctx *c, double t);
 void flux_from_acc(pic_ctx *c);        // fixed point -> FP64 fluxes, clears the accumulators
 int64_t sort32(pic_ctx *c);            // tile sort + removal; returns live count
