@@ -634,7 +634,12 @@ __device__ inline int64_t transposed_slot(int64_t q, int64_t n) {
 __global__ void k_scatter_cells(Args32 A, Parts32 S, Parts32 D, int64_t n, int64_t *cursor) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int trash = A.ntiles * A.tc;
-  const int key = k < n ? cell_key(A, S.cell[k], S.qw[k]) : -1;
+  // every load issued before the cursor atomic, whose round trip they overlap
+  const int64_t kk = k < n ? k : 0;
+  const uint32_t cell = S.cell[kk];
+  const float dx = S.dx[kk], dy = S.dy[kk], ur = S.ur[kk], ut = S.ut[kk], up = S.up[kk], qw = S.qw[kk];
+  const int64_t id = S.id[kk];
+  const int key = k < n ? cell_key(A, cell, qw) : -1;
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
   unsigned long long base = 0;
@@ -648,9 +653,9 @@ __global__ void k_scatter_cells(Args32 A, Parts32 S, Parts32 D, int64_t n, int64
     const int64_t t0 = A.start[(int64_t)t * A.tc], t1 = A.start[(int64_t)(t + 1) * A.tc];
     d = t0 + transposed_slot(d - t0, t1 - t0);
   }
-  D.cell[d] = S.cell[k]; D.dx[d] = S.dx[k]; D.dy[d] = S.dy[k];
-  D.ur[d] = S.ur[k]; D.ut[d] = S.ut[k]; D.up[d] = S.up[k];
-  D.qw[d] = S.qw[k]; D.id[d] = S.id[k];
+  D.cell[d] = cell; D.dx[d] = dx; D.dy[d] = dy;
+  D.ur[d] = ur; D.ut[d] = ut; D.up[d] = up;
+  D.qw[d] = qw; D.id[d] = id;
 }
 
 __global__ void k_charge32(int PI, int PJ, int LD, Parts32 P, int64_t n, double *Q, double *Qa) {
