@@ -474,6 +474,38 @@ def ensemble_arm(args, n_members=64):
         torch.distributed.destroy_process_group()
 
 
+def steady_arm(args):
+    """The Table 1 monopole rotator run to its steady state (two rotation
+    periods from an empty domain): throughput over the run and its physics
+    against the force-free solution."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_1407_1810_gb300 import steady
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    res = steady.run()
+    r, L = res["r"], res["L_over_L0"]
+    sel = (r >= 1.5) & (r <= 25.0)
+    bphi = {}
+    for name, p in res["bphi"].items():
+        mid = (p["theta"] > 0.3) & (p["theta"] < math.pi - 0.3)
+        bphi[f"r={p['r']:.2f}"] = float(np.median(p["bphi_over_br"][mid] / p["michel"][mid]))
+    out = {"metric": METRIC, "value": res["particle_steps_per_s"], "unit": UNIT, "n_gpus": world,
+           "steps": res["steps"], "warmup": 0, "ms_per_step": 1e3 * res["seconds"] / res["steps"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "rotator-steady", "grid": "1024x512", "periods": 2, "particles_at_end": res["particles"],
+                      "timing": "host clock over the whole run, from an empty domain"},
+           "physics": {"L_over_L0_r1.5_to_25": {"mean": float(L[sel].mean()), "min": float(L[sel].min()),
+                                                 "max": float(L[sel].max())},
+                       "bphi_over_br_to_michel": bphi, "gauss_residual": res["gauss_residual"]}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -481,6 +513,9 @@ def main():
         return
     if args.workload == "ensemble-64":
         ensemble_arm(args)
+        return
+    if args.workload == "rotator-steady":
+        steady_arm(args)
         return
     gpu_arm(args)
 

@@ -178,6 +178,18 @@ int pic_get_live(pic_ctx *c, int64_t *live, double *kinetic_energy);
 /* Diagnostics (synchronises).  The Gauss residual is relative to the snapshot
  * taken by the first pic_step or by pic_gauss_snapshot. */
 int pic_get_moments(pic_ctx *c, pic_moments *out);
+
+/* Spin-down luminosity profile (Sec. 5.3, the luminosity of Fig. monofig d):
+ * L[i], i = 0..nr, the radial Poynting flux (E x B)_r (c = 1) of the total
+ * field -- plasma plus the analytic field at the current time -- through the
+ * sphere of node radius r_i, for 1 <= i <= nr - 1 (L[0] = L[nr] = 0).  The
+ * staggered components are averaged to the centres of the meridional cells on
+ * the sphere, each cell weighted by its exact area 2 pi r_i^2 (cos th_j -
+ * cos th_{j+1}).  *n receives nr + 1; L == NULL only queries *n.  L is host or
+ * device memory per mem.  For the force-free monopole wind of surface field B0
+ * and angular velocity Omega the profile is (8 pi / 3) B0^2 r0^4 Omega^2 at
+ * every radius. */
+int pic_get_luminosity(pic_ctx *c, double *L, int64_t *n, int32_t mem);
 int pic_gauss_snapshot(pic_ctx *c);
 
 /* Step counter and id counter (for replaying a saved state). */

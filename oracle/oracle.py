@@ -112,6 +112,7 @@ def _load():
         "orc_field_energy": (C.c_double, [P]),
         "orc_kinetic_energy": (C.c_double, [P]),
         "orc_divb": (None, [P, D]),
+        "orc_luminosity": (None, [P, C.c_double, D]),
         "orc_counters": (None, [P, C.POINTER(C.c_int64)]),
     }
     for name, (res, args) in sig.items():
@@ -281,6 +282,12 @@ class Oracle:
     def divb(self):
         a = np.zeros((self.nr, self.nth))
         self.lib.orc_divb(self.h, _dp(a))
+        return a
+
+    def luminosity(self, t):
+        """Radial Poynting flux through the sphere of each node radius."""
+        a = np.zeros(self.nr + 1)
+        self.lib.orc_luminosity(self.h, t, _dp(a))
         return a
 
     def counters(self):

@@ -38,6 +38,9 @@
  *      x2 = j + (k+1/2)/N_pp, each of charge f_inj |sigma_j| dA_j / N_pp;
  *      none where |sigma_j| <= 1e-12 max_j |sigma_j| (zero up to rounding)
  *      (Sec. 5.3).
+ *   R11 Spin-down luminosity (Sec. 5.3): the radial Poynting flux of the total
+ *      field through the sphere of a node radius, with the staggered
+ *      components averaged to the centres of the meridional cells on it.
  */
 #include "picsar_oracle.h"
 
@@ -720,6 +723,36 @@ void orc_step(orc_sim *s, int32_t nsteps) {
 /* ------------------------------------------------------------------------- */
 /* Diagnostics                                                               */
 /* ------------------------------------------------------------------------- */
+/* Spin-down luminosity (Sec. 5.3, Fig. 7d): the radial Poynting flux
+ * (E x B)_r (c = 1) of the total field, plasma plus analytic at time t,
+ * through the sphere of each interior node radius r_i, 1 <= i <= nr - 1
+ * (reading R11).  On the sphere, meridional cell j carries E_th(i, j+1/2);
+ * B_ph, given at i -+ 1/2, is averaged to r_i; E_ph, given at the nodes j and
+ * j+1, and B_th, at (i -+ 1/2, j) and (i -+ 1/2, j+1), are averaged to the
+ * cell's centre; the analytic field is evaluated there.  Each cell adds
+ * (E_th B_ph - E_ph B_th) 2 pi r_i^2 (cos th_j - cos th_{j+1}).  out[0] and
+ * out[nr] are 0. */
+void orc_luminosity(const orc_sim *s, double t, double *out) {
+  const int nr = s->p.nr, nt = s->p.nth;
+  for (int i = 0; i <= nr; ++i) out[i] = 0.0;
+  for (int i = 1; i < nr; ++i) {
+    const double r = orc_f_r(s, (double)i);
+    double L = 0.0;
+    for (int j = 0; j < nt; ++j) {
+      double Ev[3], Bv[3];
+      vacuum_rt(s, r, orc_f_th(s, j + 0.5), t, 0, Ev, Bv);
+      const double et = s->f[1][FI(s, i, j)] + Ev[1];
+      const double bp = 0.5 * (s->f[5][FI(s, i - 1, j)] + s->f[5][FI(s, i, j)]) + Bv[2];
+      const double ep = 0.5 * (s->f[2][FI(s, i, j)] + s->f[2][FI(s, i, j + 1)]) + Ev[2];
+      const double bt = 0.25 * (s->f[4][FI(s, i - 1, j)] + s->f[4][FI(s, i, j)] + s->f[4][FI(s, i - 1, j + 1)] +
+                                s->f[4][FI(s, i, j + 1)]) + Bv[1];
+      const double dA = 2.0 * ORC_PI * r * r * (cos(T_(s, j)) - cos(T_(s, j + 1)));
+      L += (et * bp - ep * bt) * dA;
+    }
+    out[i] = L;
+  }
+}
+
 void orc_node_charge(const orc_sim *s, int32_t absolute, double *q) {
   orc_sim *m = (orc_sim *)s;
   memset(q, 0, ghost_size(s) * sizeof(double));

@@ -105,6 +105,9 @@ double orc_gauss_residual(const orc_sim *s);
 double orc_field_energy(const orc_sim *s);
 double orc_kinetic_energy(const orc_sim *s);
 void orc_divb(const orc_sim *s, double *out); /* nr x nth cells: flux of B out of each cell */
+/* radial Poynting flux through the sphere of each node radius (total field at
+ * time t); out: nr + 1 values, 0 at i = 0 and nr */
+void orc_luminosity(const orc_sim *s, double t, double *out);
 void orc_counters(const orc_sim *s, int64_t *out4); /* live, deleted, injected, next_id */
 
 #ifdef __cplusplus

@@ -96,8 +96,8 @@ int build_metric(pic_ctx *c) {
   Grid &G = c->G;
   const int NRr = d.nr + 2 * G.PI + 1, NC = G.LD;
   // row tables 0-12 (geometry) and 13-20 (update coefficients); column
-  // tables 0-11 (geometry) and 12-16 (update coefficients)
-  const int nrow = 21, ncol = 17;
+  // tables 0-11 and 17 (geometry) and 12-16 (update coefficients)
+  const int nrow = 21, ncol = 18;
   const double hh = 0.5 * G.dt, dt = G.dt;
   std::vector<double> h((size_t)nrow * NRr + (size_t)ncol * NC, 0.0);
   auto row = [&](int t) { return h.data() + (size_t)t * NRr; };
@@ -149,6 +149,7 @@ int build_metric(pic_ctx *c) {
       col(4)[cc] = std::sin(th(j + 0.5));
       col(5)[cc] = 1.0 / std::sin(th(j + 0.5));
       col(11)[cc] = std::cos(th(j)) - std::cos(th(j + 1));
+      col(17)[cc] = std::cos(th(j + 0.5));
     }
     if (j >= 1 && j < d.nth) col(6)[cc] = 1.0 / (th(j + 0.5) - th(j - 0.5));
   }
@@ -180,6 +181,7 @@ int build_metric(pic_ctx *c) {
   m.bR = dr(13); m.bT0 = dr(14); m.bT1 = dr(15); m.bP = dr(16);
   m.eR = dr(17); m.eT0 = dr(18); m.eT1 = dr(19); m.eP = dr(20);
   m.cB1 = dc(12); m.cB2 = dc(13); m.cE1 = dc(14); m.cE2 = dc(15); m.cF = dc(16);
+  m.cos_tb = dc(17);
   return PIC_OK;
 }
 
@@ -768,6 +770,21 @@ extern "C" int pic_get_moments(pic_ctx *c, pic_moments *out) {
   if (!c || !out) return pic_fail(PIC_EINVAL, "null argument");
   moments(c, false, out);
   PIC_CUDA(cudaGetLastError());
+  latch_errors(c);
+  return status(c);
+}
+
+extern "C" int pic_get_luminosity(pic_ctx *c, double *L, int64_t *n, int32_t mem) {
+  if (!c || !n) return pic_fail(PIC_EINVAL, "null argument");
+  *n = c->d.nr + 1;
+  if (!L) return PIC_OK;
+  double *tmp;
+  PIC_CUDA(cudaMalloc((void **)&tmp, (size_t)(c->d.nr + 1) * sizeof(double)));
+  luminosity(c, c->step * c->G.dt, tmp);
+  PIC_CUDA(cudaGetLastError());
+  int e = to_user(c, tmp, L, c->d.nr + 1, mem);
+  cudaFree(tmp);
+  if (e) return e;
   latch_errors(c);
   return status(c);
 }

@@ -324,6 +324,49 @@ void inject(pic_ctx *c, double t) {
   c->next_id += nslots;
 }
 
+// Spin-down luminosity (Sec. 5.3, Fig. monofig d): the radial Poynting flux
+// (E x B)_r of the total field, plasma plus analytic at time t, through the
+// sphere of node radius r_i, one block per interior row.  On the sphere the
+// meridional cell j carries E_th(i, j+1/2); B_ph (at i -+ 1/2), E_ph (at the
+// nodes j, j+1) and B_th (at i -+ 1/2 and j, j+1) are averaged to the cell's
+// centre; each cell adds (E_th B_ph - E_ph B_th) 2 pi r_i^2 (cos th_j -
+// cos th_{j+1}).  L[0] and L[nr] are 0.
+__global__ void k_luminosity(Grid G, const double *__restrict__ Et, const double *__restrict__ Ep,
+                             const double *__restrict__ Bt, const double *__restrict__ Bp, double t, double *L) {
+  __shared__ double sm[32];
+  const Metric &m = G.m;
+  const int i = blockIdx.x;
+  double s = 0.0;
+  if (i >= 1 && i < G.nr) {
+    const double r = m.r_n[i + G.PI], ring = 2.0 * PI_D * r * r;
+    const Vac<double> V{G.vacuum, G.b0, G.r_min, omega_at(G.omega, G.t_spin, t)};
+    for (int j = threadIdx.x; j < G.nth; j += blockDim.x) {
+      const int cj = j + G.PJ;
+      double E[3], B[3];
+      vacuum_field<double>(V, r, m.sin_tb[cj], m.cos_tb[cj], false, E, B);
+      const size_t o = gidx(G, i, j);
+      const double et = Et[o] + E[1];
+      const double bp = 0.5 * (Bp[o - G.LD] + Bp[o]) + B[2];
+      const double ep = 0.5 * (Ep[o] + Ep[o + 1]) + E[2];
+      const double bt = 0.25 * (Bt[o - G.LD] + Bt[o] + Bt[o - G.LD + 1] + Bt[o + 1]) + B[1];
+      s += (et * bp - ep * bt) * ring * m.vol_t_h[cj];
+    }
+  }
+  for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sm[w];
+    L[i] = tot;
+  }
+}
+
+void luminosity(pic_ctx *c, double t, double *L) {
+  const Grid &G = c->G;
+  ++c->launches, k_luminosity<<<G.nr + 1, 256, 0, c->stream>>>(G, c->f[ETH], c->f[EPH], c->f[BTH], c->f[BPH], t, L);
+}
+
 void moments(pic_ctx *c, bool snapshot, pic_moments *out) {
   const Grid &G = c->G;
   cudaMemsetAsync(c->Q, 0, c->grid_elems * sizeof(double), c->stream);

@@ -43,6 +43,7 @@ struct Metric {
   const double *inv_dcos_t;         // 1 / (cos th_j - cos th_{j+1})
   const double *inv_dth_t;          // 1 / (th_{j+1} - th_j)
   const double *sin_tb;             // sin tb_j, with sin tb_{-1} = sin tb_{nth} = 0
+  const double *cos_tb;             // cos tb_j (j < nth)
   const double *inv_sin_tb;         // 1 / sin tb_j
   const double *inv_dcos_tb;        // 1 / (cos tb_{j-1} - cos tb_j), caps at j = 0, nth
   const double *inv_dtb;            // 1 / (tb_j - tb_{j-1})

@@ -140,6 +140,7 @@ void fields_filter(pic_ctx *c);        // n_filt passes on F
 void fields_fill_ghosts(pic_ctx *c);   // axis ghosts only (after pic_set_fields)
 void inject(pic_ctx *c, double t);     // surface pairs into slots [n_used, n_used + 2 npp nth)
 void moments(pic_ctx *c, bool snapshot, pic_moments *out);
+void luminosity(pic_ctx *c, double t, double *L);  // nr + 1 device values (Sec. 5.3)
 void filter_array(pic_ctx *c, double *a, double *tmp, int half_j, int sign, int passes);
 // particles64.cu
 void particles64(pic_ctx *c, double t);

@@ -24,7 +24,8 @@ PIC_VAY, PIC_BORIS = 0, 1
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 
 EXPORTS = ["pic_init_grid", "pic_load_particles", "pic_step", "pic_get_fields", "pic_set_fields", "pic_get_flux",
-           "pic_get_particles", "pic_get_particles_noalloc", "pic_get_live", "pic_get_moments", "pic_gauss_snapshot", "pic_set_clock", "pic_profile",
+           "pic_get_particles", "pic_get_particles_noalloc", "pic_get_live", "pic_get_moments", "pic_get_luminosity",
+           "pic_gauss_snapshot", "pic_set_clock", "pic_profile",
            "pic_get_profile", "pic_get_launches", "pic_ensemble_step", "pic_autotune", "pic_destroy", "pic_last_error"]
 
 
@@ -77,6 +78,7 @@ def lib():
         "pic_get_particles": [P, C.POINTER(C.c_int64), P, P, P, P, P, P, P, I32],
         "pic_get_moments": [P, C.POINTER(pic_moments)],
         "pic_get_live": [P, C.POINTER(C.c_int64), C.POINTER(C.c_double)],
+        "pic_get_luminosity": [P, P, C.POINTER(C.c_int64), I32],
         "pic_get_particles_noalloc": [P, C.POINTER(C.c_int64), P, P, P, P, P, P, P],
         "pic_gauss_snapshot": [P],
         "pic_set_clock": [P, I64, I64],
@@ -230,6 +232,15 @@ class Simulation:
         m = pic_moments()
         check(self.L.pic_get_moments(self.h, C.byref(m)))
         return {k: getattr(m, k) for k, _ in pic_moments._fields_}
+
+    def luminosity(self):
+        """Spin-down luminosity through the sphere of each node radius (nr + 1
+        values, 0 at the conductors): pic_get_luminosity."""
+        n = C.c_int64()
+        check(self.L.pic_get_luminosity(self.h, None, C.byref(n), PIC_MEM_HOST))
+        out = np.empty(n.value)
+        check(self.L.pic_get_luminosity(self.h, C.c_void_p(out.ctypes.data), C.byref(n), PIC_MEM_HOST))
+        return out
 
     def gauss_snapshot(self):
         check(self.L.pic_gauss_snapshot(self.h))

@@ -217,3 +217,19 @@ def test_pinned_and_pageable_host_loads_agree(precision):
     a, b = by_id(s1.particles()), by_id(s2.particles())
     for k in a:
         assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_luminosity_against_oracle(precision):
+    """pic_get_luminosity on a rotator state with currents against the oracle's
+    luminosity of the same fields and clock (both FP64 field arrays)."""
+    cfg = dict(configs.CONFIGS["rotator-512x512"], nr=32, nth=24, pairs_per_cell=3, absorb_cells=8, t_spin=0.3,
+               precision=precision)
+    s, o, plasma, dt = setup(cfg)
+    s.step(25)
+    o2 = O.Oracle(o.p)
+    o2.set_fields(s.fields())
+    t = s.moments()["time"]
+    Lg, Lo = s.luminosity(), o2.luminosity(t)
+    assert Lg[0] == 0.0 and Lg[-1] == 0.0
+    assert np.max(np.abs(Lg - Lo)) <= 1e-12 * np.max(np.abs(Lo)) and np.max(np.abs(Lo)) > 0
