@@ -490,10 +490,12 @@ def steady_arm(args):
     res = steady.run()
     r, L = res["r"], res["L_over_L0"]
     sel = (r >= 1.5) & (r <= 25.0)
-    bphi = {}
+    bphi, r2jr = {}, {}
     for name, p in res["bphi"].items():
         mid = (p["theta"] > 0.3) & (p["theta"] < math.pi - 0.3)
         bphi[f"r={p['r']:.2f}"] = float(np.median(p["bphi_over_br"][mid] / p["michel"][mid]))
+        c = np.cos(p["theta_j"])
+        r2jr[f"r={p['r']:.2f}"] = float(-(p["r2jr"] @ c) / (c @ c))
     out = {"metric": METRIC, "value": res["particle_steps_per_s"], "unit": UNIT, "n_gpus": world,
            "steps": res["steps"], "warmup": 0, "ms_per_step": 1e3 * res["seconds"] / res["steps"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -501,7 +503,8 @@ def steady_arm(args):
                       "timing": "host clock over the whole run, from an empty domain"},
            "physics": {"L_over_L0_r1.5_to_25": {"mean": float(L[sel].mean()), "min": float(L[sel].min()),
                                                  "max": float(L[sel].max())},
-                       "bphi_over_br_to_michel": bphi, "gauss_residual": res["gauss_residual"]}}
+                       "bphi_over_br_to_michel": bphi, "r2jr_scale_to_michel": r2jr,
+                       "gauss_residual": res["gauss_residual"]}}
     if rank == 0:
         print(json.dumps(out), flush=True)
 
