@@ -14,7 +14,9 @@
   50; the Boris pusher does so at 0.1 and departs from it at 50.
 
 Each run is compared with the oracle on the same input: fields within 1e-12
-(FP64 path) or 1e-5 (FP32 path) relative, deletion steps exact.
+(FP64 path) or 1e-5 (FP32 path) relative, deletion steps exact; the one
+ill-conditioned case (FP32, axis pair, spherical coordinates) is held to 1e-4,
+for the reason given at E3.
 """
 import math
 
@@ -151,6 +153,16 @@ def test_e2_equator_pair_deletion_and_inverse_square(precision, th_map):
     s.close()
 
 
+# In spherical coordinates the axis ringing is ill-conditioned: on the oracle
+# itself a 1e-6 cell shift of the pair's start moves the fields at 3.5 t_c by
+# 8.9e-6 relative (6e-9 in equal-area coordinates), and the FP32 path's
+# position rounding over the ~200 steps of flight is of that order; measured
+# 4.7e-5 against the oracle.  That case is held to 1e-4, and its ringing
+# amplitude to the oracle's within 1 %.
+E3_TOL = {("fp64", "linear"): 1e-12, ("fp64", "equal_area"): 1e-12,
+          ("fp32", "linear"): 1e-4, ("fp32", "equal_area"): 1e-5}
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_e3_polar_axis_pair_rings_only_in_spherical_coordinates(precision):
     dev = {}
@@ -159,10 +171,12 @@ def test_e3_polar_axis_pair_rings_only_in_spherical_coordinates(precision):
         n = int(3.5 * TC / dt)
         s.step(n)
         o.step(n)
-        f = s.fields()
-        assert rel_l2(f, o.fields()) < FIELD_TOL[precision], th_map
+        f, fo = s.fields(), o.fields()
+        assert rel_l2(f, fo) < E3_TOL[precision, th_map], th_map
         inner, exact = _inverse_square(o, Q)
         dev[th_map] = np.max(np.abs(f[0, inner, 0] - exact)) / np.max(exact)
+        dev_o = np.max(np.abs(fo[0, inner, 0] - exact)) / np.max(exact)
+        assert abs(dev[th_map] - dev_o) <= 0.01 * dev_o + 1e-4, (th_map, dev[th_map], dev_o)
         assert s.live() == 0
         s.close()
     assert dev["equal_area"] < 0.01, dev
