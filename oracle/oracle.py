@@ -18,7 +18,8 @@ _OUT = os.path.join(_HERE, "_build", "libpicsar_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-VAC = {"none": 0, "monopole": 1, "monopole_rotator": 2, "uniform_bz": 3, "dipole_corot": 4}
+VAC = {"none": 0, "monopole": 1, "monopole_rotator": 2, "uniform_bz": 3, "dipole_corot": 4, "dipole_rotator": 5}
+INJECT = {"off": 0, "fixed": 1, "variable": 2}
 PUSHER = {"vay": 0, "boris": 1}
 ABSORB = {"none": 0, "linear": 1, "quadratic": 2}
 
@@ -37,6 +38,7 @@ class Params(C.Structure):
         ("inject", C.c_int32), ("pairs_per_cell", C.c_int32), ("f_inj", C.c_double),
         ("pusher", C.c_int32),
         ("q_over_m", C.c_double),
+        ("inject_smooth", C.c_int32), ("inject_q", C.c_double), ("inject_seed", C.c_uint64),
     ]
 
 
@@ -48,6 +50,8 @@ def params(**kw) -> Params:
     for k, v in kw.items():
         if k == "vacuum" and isinstance(v, str):
             v = VAC[v]
+        elif k == "inject" and isinstance(v, str):
+            v = INJECT[v]
         elif k == "pusher" and isinstance(v, str):
             v = PUSHER[v]
         elif k == "absorb_profile" and isinstance(v, str):
@@ -114,6 +118,7 @@ def _load():
         "orc_divb": (None, [P, D]),
         "orc_luminosity": (None, [P, C.c_double, D]),
         "orc_counters": (None, [P, C.POINTER(C.c_int64)]),
+        "orc_splitmix64": (C.c_uint64, [C.c_uint64, C.c_uint64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -133,6 +138,11 @@ def _ip(a: np.ndarray):
 
 def courant_dt(p: Params, courant: float) -> float:
     return _load().orc_courant_dt(C.byref(p), courant)
+
+
+def splitmix64(seed: int, n: int) -> int:
+    """Output number n + 1 of the SplitMix64 stream seeded with `seed`."""
+    return int(_load().orc_splitmix64(seed, n))
 
 
 def push(pusher, qmdt, E, B, u):
@@ -291,6 +301,7 @@ class Oracle:
         return a
 
     def counters(self):
-        a = np.zeros(4, dtype=np.int64)
+        a = np.zeros(5, dtype=np.int64)
         self.lib.orc_counters(self.h, _ip(a))
-        return {"live": int(a[0]), "deleted": int(a[1]), "injected": int(a[2]), "next_id": int(a[3])}
+        return {"live": int(a[0]), "deleted": int(a[1]), "injected": int(a[2]), "next_id": int(a[3]),
+                "capped": int(a[4])}

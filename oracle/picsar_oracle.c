@@ -41,6 +41,23 @@
  *   R11 Spin-down luminosity (Sec. 5.3): the radial Poynting flux of the total
  *      field through the sphere of a node radius, with the staggered
  *      components averaged to the centres of the meridional cells on it.
+ *   R12 Surface charge (Sec. 5.3): the jump of E_r across the conductor, i.e.
+ *      the total E_r at (1/2, j) minus the analytic inside field's E_r at
+ *      (r0, theta_j) (zero for the monopole fields); sigma_j averages j, j+1.
+ *      Optional smoothing along theta: passes of (s_{j-1} + 2 s_j + s_{j+1})/4
+ *      with each polar cell its own mirror image across the axis.
+ *   R13 Variable-count injection, Eq. (volinjeq) as printed: n_j =
+ *      f_inj |sigma_j| dA_j / q pairs of charge -+q, rounded stochastically
+ *      (floor, plus one with probability equal to the fraction), the uniform
+ *      number u = top 53 bits of SplitMix64 output (step * nth + j) + 1 of the
+ *      stream seeded with inject_seed; at most pairs_per_cell pairs per cell
+ *      (cells cut to it are counted); pair k of n_j at x2 = j + (k+1/2)/n_j.
+ *      Ids as in R10: the counter advances by 2 * pairs_per_cell * nth.
+ *   R14 Aligned dipole rotator fields (Sec. 4.3 dipole, Sec. 5.2 construction):
+ *      B the dipole mu = B0 r0^3 everywhere; inside the star the corotation E;
+ *      outside the vacuum field of the rotating conducting sphere with no net
+ *      charge, E = -grad Phi, Phi = -(Omega mu r0^2 / 3 r^3)(3 cos^2 th - 1),
+ *      which matches the inside potential's l = 2 part at r0.
  */
 #include "picsar_oracle.h"
 
@@ -64,7 +81,7 @@ struct orc_sim {
   int64_t *id;
   int64_t next_id;
   int64_t step;
-  int64_t n_deleted, n_injected;
+  int64_t n_deleted, n_injected, n_capped;
   double *gq0; /* (G - Qbar) at the snapshot, (nr+1) x (nth+1) */
   int err;
 };
@@ -220,11 +237,23 @@ void orc_get_flux(const orc_sim *s, double *out3) {
   for (int c = 0; c < 3; ++c) memcpy(out3 + c * ghost_size(s), s->F[c], ghost_size(s) * sizeof(double));
 }
 
-void orc_counters(const orc_sim *s, int64_t *out4) {
-  out4[0] = s->np;
-  out4[1] = s->n_deleted;
-  out4[2] = s->n_injected;
-  out4[3] = s->next_id;
+void orc_counters(const orc_sim *s, int64_t *out5) {
+  out5[0] = s->np;
+  out5[1] = s->n_deleted;
+  out5[2] = s->n_injected;
+  out5[3] = s->next_id;
+  out5[4] = s->n_capped;
+}
+
+/* SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): the state advances by the
+ * golden-ratio increment and each output is the state through the variant-13
+ * mixing function; output n + 1 of the stream seeded with `seed` is therefore
+ * the mix of seed + (n + 1) * increment. */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t n) {
+  uint64_t z = seed + (n + 1u) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -266,6 +295,20 @@ static void vacuum_rt(const orc_sim *s, double r, double th, double t, int insid
       B[1] = mu * st / (r * r * r);
       E[0] = mu * W * st * st / (r * r);
       E[1] = -mu * W * 2.0 * st * ct / (r * r);
+      break;
+    }
+    case ORC_VAC_DIPOLE_ROTATOR: { /* reading R14 */
+      double mu = b0 * r0 * r0 * r0;
+      B[0] = 2.0 * mu * ct / (r * r * r);
+      B[1] = mu * st / (r * r * r);
+      if (inside) { /* corotation: -(Omega x r) x B */
+        E[0] = mu * W * st * st / (r * r);
+        E[1] = -mu * W * 2.0 * st * ct / (r * r);
+      } else { /* -grad of -(Omega mu r0^2 / 3 r^3)(3 cos^2 - 1) */
+        double a = mu * W * r0 * r0 / (r * r * r * r);
+        E[0] = -a * (3.0 * ct * ct - 1.0);
+        E[1] = -a * 2.0 * st * ct;
+      }
       break;
     }
     default:
@@ -646,40 +689,70 @@ static void particle_step(orc_sim *s, int64_t k, double t, int *del) {
   *del = ci < -(s->p.n_filt + 1) || ci >= nr + s->p.n_filt + 1;
 }
 
-/* Surface injection, Sec. 5.3 Eq. (volinjeq), reading R10. */
+/* Surface injection, Sec. 5.3 Eq. (volinjeq), readings R10, R12, R13. */
 static void inject(orc_sim *s, double t) {
   const int nt = s->p.nth, npp = s->p.pairs_per_cell;
   const double r0 = s->p.r_min, rb0 = RB(s, 0);
-  double *sig = (double *)malloc(sizeof(double) * nt), smax = 0.0;
+  double *sig = (double *)malloc(sizeof(double) * nt), *tmp = (double *)malloc(sizeof(double) * nt);
+  double smax = 0.0;
   reserve(s, s->np + (int64_t)2 * npp * nt);
   for (int j = 0; j < nt; ++j) {
-    double Ev[3], Bv[3], e0, e1;
+    double Ev[3], Bv[3], Ei[3], e0, e1;
     vacuum_rt(s, rb0, T_(s, j), t, 0, Ev, Bv);
-    e0 = s->f[0][FI(s, 0, j)] + Ev[0];
+    vacuum_rt(s, r0, T_(s, j), t, 1, Ei, Bv);
+    e0 = (s->f[0][FI(s, 0, j)] + Ev[0]) - Ei[0];
     vacuum_rt(s, rb0, T_(s, j + 1), t, 0, Ev, Bv);
-    e1 = s->f[0][FI(s, 0, j + 1)] + Ev[0];
-    sig[j] = 0.5 * (e0 + e1); /* E_r jump: 0 inside the conductor */
-    if (fabs(sig[j]) > smax) smax = fabs(sig[j]);
+    vacuum_rt(s, r0, T_(s, j + 1), t, 1, Ei, Bv);
+    e1 = (s->f[0][FI(s, 0, j + 1)] + Ev[0]) - Ei[0];
+    sig[j] = 0.5 * (e0 + e1); /* jump of E_r across the surface */
   }
+  for (int pass = 0; pass < s->p.inject_smooth; ++pass) {
+    for (int j = 0; j < nt; ++j) {
+      double a = sig[j > 0 ? j - 1 : 0], c = sig[j < nt - 1 ? j + 1 : nt - 1];
+      tmp[j] = ((a + 2.0 * sig[j]) + c) * 0.25;
+    }
+    memcpy(sig, tmp, sizeof(double) * nt);
+  }
+  for (int j = 0; j < nt; ++j)
+    if (fabs(sig[j]) > smax) smax = fabs(sig[j]);
+  const uint64_t step = (uint64_t)s->step;
   for (int j = 0; j < nt; ++j) {
     double dA = 2.0 * ORC_PI * r0 * r0 * (cos(T_(s, j)) - cos(T_(s, j + 1)));
-    double w = s->p.f_inj * fabs(sig[j]) * dA / npp;
-    /* cells whose surface charge is zero up to rounding inject nothing */
-    int on = fabs(sig[j]) > 1e-12 * smax && w > 0.0;
-    for (int k = 0; k < npp; ++k)
+    int m;       /* pairs injected into cell j */
+    double w;    /* |charge| of each */
+    if (s->p.inject == ORC_INJECT_VARIABLE) {
+      double x = s->p.f_inj * fabs(sig[j]) * dA / s->p.inject_q;
+      w = s->p.inject_q;
+      m = 0;
+      if (fabs(sig[j]) > 1e-12 * smax && x > 0.0) {
+        if (x >= npp + 1.0) {
+          m = npp + 1;
+        } else {
+          double fl = floor(x);
+          double u = (double)(orc_splitmix64(s->p.inject_seed, step * (uint64_t)nt + (uint64_t)j) >> 11) *
+                     (1.0 / 9007199254740992.0);
+          m = (int)fl + (u < x - fl ? 1 : 0);
+        }
+        if (m > npp) { m = npp; s->n_capped++; }
+      }
+    } else {
+      w = s->p.f_inj * fabs(sig[j]) * dA / npp;
+      /* cells whose surface charge is zero up to rounding inject nothing */
+      m = (fabs(sig[j]) > 1e-12 * smax && w > 0.0) ? npp : 0;
+    }
+    for (int k = 0; k < m; ++k)
       for (int sgn = 0; sgn < 2; ++sgn) {
-        int64_t pid = s->next_id + ((int64_t)j * npp + k) * 2 + sgn;
-        if (!on) continue;
         int64_t d = s->np++;
         s->x1[d] = 0.5;
-        s->x2[d] = j + (k + 0.5) / npp;
+        s->x2[d] = j + (k + 0.5) / m;
         s->ur[d] = s->uth[d] = s->uph[d] = 0.0;
         s->qw[d] = sgn == 0 ? w : -w;
-        s->id[d] = pid;
+        s->id[d] = s->next_id + ((int64_t)j * npp + k) * 2 + sgn;
         s->n_injected++;
       }
   }
   free(sig);
+  free(tmp);
   s->next_id += (int64_t)2 * npp * nt;
 }
 

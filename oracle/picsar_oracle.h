@@ -25,7 +25,8 @@ enum { ORC_R_LINEAR = 0, ORC_R_LOG = 1 };
 enum { ORC_TH_LINEAR = 0, ORC_TH_EQUAL_AREA = 1 };
 enum { ORC_ABSORB_NONE = 0, ORC_ABSORB_LINEAR = 1, ORC_ABSORB_QUADRATIC = 2 };
 enum { ORC_VAC_NONE = 0, ORC_VAC_MONOPOLE = 1, ORC_VAC_MONOPOLE_ROTATOR = 2,
-       ORC_VAC_UNIFORM_BZ = 3, ORC_VAC_DIPOLE_COROT = 4 };
+       ORC_VAC_UNIFORM_BZ = 3, ORC_VAC_DIPOLE_COROT = 4, ORC_VAC_DIPOLE_ROTATOR = 5 };
+enum { ORC_INJECT_OFF = 0, ORC_INJECT_FIXED = 1, ORC_INJECT_VARIABLE = 2 };
 enum { ORC_VAY = 0, ORC_BORIS = 1 };
 
 typedef struct orc_params {
@@ -41,11 +42,14 @@ typedef struct orc_params {
   double b0;                /* field at r0 */
   double omega;             /* final angular velocity; light cylinder R_l = 1/omega */
   double t_spin;            /* linear spin-up time, Sec. 5.2 */
-  int32_t inject;           /* surface injection on/off, Sec. 5.3 */
-  int32_t pairs_per_cell;   /* pairs injected per surface cell per step */
+  int32_t inject;           /* ORC_INJECT_*: surface injection, Sec. 5.3 */
+  int32_t pairs_per_cell;   /* FIXED: pairs per surface cell per step; VARIABLE: the cap */
   double f_inj;             /* injection multiplier, Eq. (volinjeq) */
   int32_t pusher;           /* ORC_VAY | ORC_BORIS, Sec. 2 */
   double q_over_m;          /* |q|/m of every species (pair plasma) */
+  int32_t inject_smooth;    /* 1-2-1 passes over sigma_j along theta before injecting */
+  double inject_q;          /* VARIABLE: |charge| of each injected particle */
+  uint64_t inject_seed;     /* VARIABLE: seed of the stochastic rounding (SplitMix64) */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -108,7 +112,11 @@ void orc_divb(const orc_sim *s, double *out); /* nr x nth cells: flux of B out o
 /* radial Poynting flux through the sphere of each node radius (total field at
  * time t); out: nr + 1 values, 0 at i = 0 and nr */
 void orc_luminosity(const orc_sim *s, double t, double *out);
-void orc_counters(const orc_sim *s, int64_t *out4); /* live, deleted, injected, next_id */
+/* live, deleted, injected, next_id, capped (VARIABLE injection: cells whose
+ * pair count was cut to pairs_per_cell) */
+void orc_counters(const orc_sim *s, int64_t *out5);
+/* output number n + 1 of the SplitMix64 stream seeded with `seed` */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t n);
 
 #ifdef __cplusplus
 }
