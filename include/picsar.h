@@ -57,7 +57,20 @@ enum { PIC_R_LINEAR = 0, PIC_R_LOG = 1 };                  /* f_r, Sec. 3.2 */
 enum { PIC_TH_LINEAR = 0, PIC_TH_EQUAL_AREA = 1 };         /* f_th, Sec. 3.2 */
 enum { PIC_ABSORB_NONE = 0, PIC_ABSORB_LINEAR = 1, PIC_ABSORB_QUADRATIC = 2 };
 enum { PIC_VAC_NONE = 0, PIC_VAC_MONOPOLE = 1, PIC_VAC_MONOPOLE_ROTATOR = 2,
-       PIC_VAC_UNIFORM_BZ = 3, PIC_VAC_DIPOLE_COROT = 4 };
+       PIC_VAC_UNIFORM_BZ = 3, PIC_VAC_DIPOLE_COROT = 4, PIC_VAC_DIPOLE_ROTATOR = 5 };
+/* Surface injection (Sec. 5.3).  FIXED: pairs_per_cell pairs in every surface
+ * cell, each of charge f_inj |sigma_j| dA_j / pairs_per_cell.  VARIABLE:
+ * Eq. (volinjeq) as printed, n_j = f_inj |sigma_j| dA_j / inject_q pairs of
+ * charge -+inject_q, rounded stochastically (floor, plus one with probability
+ * equal to the fraction; the uniform number is the top 53 bits of SplitMix64
+ * output step * nth + j + 1 of the stream seeded with inject_seed) and cut to
+ * pairs_per_cell (cells cut are counted in pic_moments.inject_capped).  In
+ * both modes sigma_j is the jump of E_r across the surface (total E_r at
+ * (1/2, j) minus the analytic inside field's E_r at r0), averaged over j and
+ * j+1, then smoothed by inject_smooth 1-2-1 passes along theta with each polar
+ * cell its own mirror image; pair k of m in cell j sits at x1 = 1/2,
+ * x2 = j + (k + 1/2)/m; ids advance by 2 pairs_per_cell nth every step. */
+enum { PIC_INJECT_OFF = 0, PIC_INJECT_FIXED = 1, PIC_INJECT_VARIABLE = 2 };
 enum { PIC_FP64 = 0, PIC_FP32 = 1 };
 enum { PIC_VAY = 0, PIC_BORIS = 1 };
 enum { PIC_MEM_HOST = 0, PIC_MEM_DEVICE = 1 };
@@ -76,12 +89,15 @@ typedef struct pic_desc {
   int32_t absorb_cells;      /* lossy layer width in cells (Sec. 3.4.1) */
   int32_t absorb_profile;    /* PIC_ABSORB_* */
   double absorb_sigma_max;   /* sigma* at the outer conductor; <= 0: 2/L linear, 3/L quadratic */
-  int32_t vacuum;            /* PIC_VAC_* analytic field added at the particle (Sec. 5.2, 4.3) */
+  int32_t vacuum;            /* PIC_VAC_* analytic field added at the particle (Sec. 5.2, 4.3);
+                                DIPOLE_ROTATOR: dipole B (mu = b0 r0^3), corotation E inside,
+                                outside the vacuum E of the rotating conductor with no net
+                                charge, -grad of -(Omega mu r0^2 / 3 r^3)(3 cos^2 th - 1) */
   double b0;                 /* field strength at r0 */
   double omega;              /* final angular velocity of the star; R_l = c / omega */
   double t_spin;             /* linear spin-up time (Sec. 5.2); 0 = none */
-  int32_t inject;            /* 1: surface pair injection each step (Sec. 5.3) */
-  int32_t pairs_per_cell;    /* pairs injected per surface cell per step (default 2) */
+  int32_t inject;            /* PIC_INJECT_*: surface pair injection each step (Sec. 5.3) */
+  int32_t pairs_per_cell;    /* FIXED: pairs per surface cell per step; VARIABLE: the cap */
   double f_inj;              /* injection multiplier, 0 < f_inj <= 1 (Eq. volinjeq) */
   int32_t precision;         /* PIC_FP64 (plain FP64 path) or PIC_FP32 (cell+offset path) */
   int32_t pusher;            /* PIC_VAY or PIC_BORIS (Sec. 2) */
@@ -95,6 +111,9 @@ typedef struct pic_desc {
                                 and at least this value rounded up to a power of two. */
   int32_t tile_shape;        /* FP32 path: tile of the shared-memory deposit, 0 = 16x16 cells,
                                 1 = 8 (r) x 32 (theta), 2 = 32 x 8 */
+  int32_t inject_smooth;     /* 1-2-1 passes over sigma_j along theta, 0..64 */
+  double inject_q;           /* VARIABLE injection: |charge| of each injected particle, > 0 */
+  uint64_t inject_seed;      /* VARIABLE injection: seed of the stochastic rounding */
 } pic_desc;
 
 /* Diagnostics returned by pic_get_moments. */
@@ -110,6 +129,7 @@ typedef struct pic_moments {
   double gauss_residual;     /* max |(G - Qbar) - (G - Qbar)_0| / max sum |qw| CIC over the
                                 interior nodes 1 <= i <= nr - absorb_cells - 1 (App. B, Sec. 2) */
   double total_charge;       /* sum qw */
+  int64_t inject_capped;     /* VARIABLE injection: cell-steps whose count was cut to pairs_per_cell */
 } pic_moments;
 
 /* Create a context: allocates the grid arrays on the current CUDA device and
@@ -226,6 +246,10 @@ int pic_destroy(pic_ctx *c);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *pic_last_error(void);
+
+/* sizeof(pic_desc) and sizeof(pic_moments) as compiled into the library, for
+ * bindings that mirror the two structs (no device work). */
+void pic_struct_sizes(int64_t *desc_bytes, int64_t *moments_bytes);
 
 #ifdef __cplusplus
 }

@@ -73,7 +73,9 @@ def desc_kwargs(cfg: dict, dt: float, b0: float, **over):
               absorb_profile=cfg["absorb_profile"], vacuum=cfg["vacuum"], b0=b0, omega=cfg["omega"],
               t_spin=cfg["t_spin"], inject=cfg["inject"], pairs_per_cell=cfg.get("inject_pairs", 2),
               f_inj=cfg.get("f_inj", 0.0), precision=cfg["precision"], pusher=cfg["pusher"], q_over_m=1.0,
-              sort_interval=cfg.get("sort_interval", 20), tile_shape=cfg.get("tile_shape", 0))
+              sort_interval=cfg.get("sort_interval", 20), tile_shape=cfg.get("tile_shape", 0),
+              inject_smooth=cfg.get("inject_smooth", 0), inject_q=cfg.get("inject_q", 0.0),
+              inject_seed=cfg.get("inject_seed", 0))
     kw.update(over)
     return kw
 
@@ -94,7 +96,9 @@ def oracle_kwargs(cfg: dict, dt: float, b0: float, **over):
               th_map=cfg["th_map"], dt=dt, n_filt=cfg["n_filt"], absorb_cells=cfg["absorb_cells"],
               absorb_profile=cfg["absorb_profile"], vacuum=cfg["vacuum"], b0=b0, omega=cfg["omega"],
               t_spin=cfg["t_spin"], inject=cfg["inject"], pairs_per_cell=cfg.get("inject_pairs", 2),
-              f_inj=cfg.get("f_inj", 0.0), pusher=cfg["pusher"], q_over_m=1.0)
+              f_inj=cfg.get("f_inj", 0.0), pusher=cfg["pusher"], q_over_m=1.0,
+              inject_smooth=cfg.get("inject_smooth", 0), inject_q=cfg.get("inject_q", 0.0),
+              inject_seed=cfg.get("inject_seed", 0))
     kw.update(over)
     return kw
 

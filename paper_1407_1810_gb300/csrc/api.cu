@@ -24,6 +24,11 @@ int pic_cuda_check(cudaError_t e, const char *what) {
 
 extern "C" const char *pic_last_error(void) { return g_last_error.c_str(); }
 
+extern "C" void pic_struct_sizes(int64_t *desc_bytes, int64_t *moments_bytes) {
+  if (desc_bytes) *desc_bytes = (int64_t)sizeof(pic_desc);
+  if (moments_bytes) *moments_bytes = (int64_t)sizeof(pic_moments);
+}
+
 namespace {
 
 // ---- host copies of the stretching functions (Sec. 3.2) ----------------------
@@ -54,11 +59,15 @@ int check_desc(const pic_desc &d) {
   if (d.n_filt < 0 || d.n_filt > 16) return pic_fail(PIC_EINVAL, "n_filt must be in [0, 16]");
   if (d.absorb_profile < 0 || d.absorb_profile > 2 || d.absorb_cells < 0 || d.absorb_cells >= d.nr)
     return pic_fail(PIC_EINVAL, "bad absorbing layer");
-  if (d.vacuum < 0 || d.vacuum > 4) return pic_fail(PIC_EINVAL, "bad vacuum field kind");
+  if (d.vacuum < 0 || d.vacuum > 5) return pic_fail(PIC_EINVAL, "bad vacuum field kind");
   if (d.precision != PIC_FP64 && d.precision != PIC_FP32) return pic_fail(PIC_EINVAL, "bad precision");
   if (d.pusher != PIC_VAY && d.pusher != PIC_BORIS) return pic_fail(PIC_EINVAL, "bad pusher");
+  if (d.inject < PIC_INJECT_OFF || d.inject > PIC_INJECT_VARIABLE) return pic_fail(PIC_EINVAL, "bad inject mode");
   if (d.inject && (d.pairs_per_cell < 1 || !(d.f_inj > 0.0) || d.f_inj > 1.0))
     return pic_fail(PIC_EINVAL, "injection needs pairs_per_cell >= 1 and 0 < f_inj <= 1");
+  if (d.inject == PIC_INJECT_VARIABLE && !(d.inject_q > 0.0 && std::isfinite(d.inject_q)))
+    return pic_fail(PIC_EINVAL, "variable-count injection needs a finite inject_q > 0");
+  if (d.inject_smooth < 0 || d.inject_smooth > 64) return pic_fail(PIC_EINVAL, "inject_smooth must be in [0, 64]");
   if (d.r_map == PIC_R_LINEAR) {
     double dr = (d.r_max - d.r_min) / d.nr;
     if (d.r_min - (d.n_filt + 2) * dr <= 0.0)
@@ -491,7 +500,7 @@ extern "C" int pic_init_grid(pic_ctx **out, const pic_desc *dd, void *stream) {
     if ((e = alloc_bins(c, d.tile_shape))) return fail(e);
     if (tiles32_setup(c)) return fail(pic_fail(PIC_ECUDA, "tensor maps of the field window could not be encoded"));
   }
-  if ((e = dalloc(&c->sig, (size_t)d.nth + 1))) return fail(e);
+  if ((e = dalloc(&c->sig, 2 * ((size_t)d.nth + 1)))) return fail(e);
   if ((e = dalloc(&c->d_err, 1)) || (e = dalloc(&c->d_cnt, CNT_N)) || (e = dalloc(&c->d_acc, ACC_N))) return fail(e);
   cudaMemset(c->d_err, 0, sizeof(int));
   cudaMemset(c->d_cnt, 0, CNT_N * sizeof(long long));

@@ -134,51 +134,115 @@ __global__ void k_filter(Grid G, const double *__restrict__ in, double *__restri
   out[o] = s;
 }
 
+// Surface charge per meridional cell: the jump of E_r across the conductor,
+// total E_r at (1/2, j) minus the analytic inside field's E_r at (r0, theta_j)
+// (zero for the monopole fields), averaged over the cell's two nodes.
 __global__ void k_inject_sigma(Grid G, const double *__restrict__ Er, double t, double *sig, long long *smax) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= G.nth) return;
   const Metric &m = G.m;
   const double rb0 = m.r_h[G.PI];
-  double E[3], B[3];
+  double E[3], B[3], Ei[3];
   const Vac<double> V{G.vacuum, G.b0, G.r_min, omega_at(G.omega, G.t_spin, t)};
-  vacuum_field<double>(V, rb0, m.sin_t[j + G.PJ], m.cos_t[j + G.PJ], false, E, B);
-  double e0 = Er[gidx(G, 0, j)] + E[0];
-  vacuum_field<double>(V, rb0, m.sin_t[j + 1 + G.PJ], m.cos_t[j + 1 + G.PJ], false, E, B);
-  double e1 = Er[gidx(G, 0, j + 1)] + E[0];
-  double s = 0.5 * (e0 + e1);  // jump of E_r across r0 (zero inside)
+  double e[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const double st = m.sin_t[j + h + G.PJ], ct = m.cos_t[j + h + G.PJ];
+    vacuum_field<double>(V, rb0, st, ct, false, E, B);
+    vacuum_field<double>(V, G.r_min, st, ct, true, Ei, B);
+    e[h] = (Er[gidx(G, 0, j + h)] + E[0]) - Ei[0];
+  }
+  const double s = 0.5 * (e[0] + e[1]);
   sig[j] = s;
-  atomicMax(smax, __double_as_longlong(fabs(s)));
+  if (smax) atomicMax(smax, __double_as_longlong(fabs(s)));
 }
 
+// One 1-2-1 pass over sigma along theta; each polar cell is its own mirror
+// image across the axis.
+__global__ void k_inject_smooth(int nth, const double *__restrict__ in, double *out, long long *smax) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nth) return;
+  const double a = in[j > 0 ? j - 1 : 0], c = in[j < nth - 1 ? j + 1 : nth - 1];
+  const double s = ((a + 2.0 * in[j]) + c) * 0.25;
+  out[j] = s;
+  if (smax) atomicMax(smax, __double_as_longlong(fabs(s)));
+}
+
+// SplitMix64 (Steele, Lea and Flood 2014) as a counter-based generator:
+// output n + 1 of the stream seeded with `seed` is the variant-13 mix of
+// seed + (n + 1) times the golden-ratio increment.
+__device__ inline uint64_t splitmix64_out(uint64_t seed, uint64_t n) {
+  uint64_t z = seed + (n + 1u) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct InjectRule {
+  int mode, npp;
+  double finj, q;       // q: VARIABLE, |charge| per particle
+  uint64_t seed, step;  // VARIABLE: generator key (seed, step * nth + j)
+};
+
+// Pairs injected into cell j and the |charge| of each (Eq. volinjeq).
+__device__ inline int inject_count(const Grid &G, const InjectRule &R, int j, double sg, double sm, double dA,
+                                   double &w, bool &capped) {
+  capped = false;
+  if (R.mode == PIC_INJECT_VARIABLE) {
+    const double x = R.finj * fabs(sg) * dA / R.q;
+    w = R.q;
+    if (!(fabs(sg) > 1e-12 * sm && x > 0.0)) return 0;
+    int m;
+    if (x >= R.npp + 1.0) {
+      m = R.npp + 1;
+    } else {
+      const double fl = floor(x);
+      const double u = (double)(splitmix64_out(R.seed, R.step * (uint64_t)G.nth + (uint64_t)j) >> 11) *
+                       (1.0 / 9007199254740992.0);
+      m = (int)fl + (u < x - fl ? 1 : 0);
+    }
+    if (m > R.npp) { m = R.npp; capped = true; }
+    return m;
+  }
+  w = R.finj * fabs(sg) * dA / R.npp;
+  return (fabs(sg) > 1e-12 * sm && w > 0.0) ? R.npp : 0;
+}
+
+// One thread per slot (j, k, sign) of the 2 npp nth reserved this step; slots
+// past a cell's count keep zero charge (free).
 template <bool FP32>
 __global__ void k_inject_write(Grid G, const double *__restrict__ sig, const long long *smax, Parts64 P,
-                               Parts32 Q, int64_t base, int64_t id0, int npp, double finj, long long *cnt,
-                               long long *qexp) {
+                               Parts32 Q, int64_t base, int64_t id0, InjectRule R, long long *cnt,
+                               long long *capped_cnt, long long *qexp) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int npp = R.npp;
   int qe = (int)QEXP_NONE;
   if (idx < (int64_t)G.nth * npp * 2) {
     const int j = (int)(idx / (2 * npp)), k = (int)((idx / 2) % npp), s = (int)(idx % 2);
     const double sm = __longlong_as_double(*smax), sg = sig[j];
     const double r0 = G.r_min;
     const double dA = 2.0 * PI_D * r0 * r0 * (G.m.cos_t[j + G.PJ] - G.m.cos_t[j + 1 + G.PJ]);
-    const double w = finj * fabs(sg) * dA / npp;
-    const bool on = fabs(sg) > 1e-12 * sm && w > 0.0;
+    double w;
+    bool capped;
+    const int m = inject_count(G, R, j, sg, sm, dA, w, capped);
+    if (capped && k == 0 && s == 0) add_ll(capped_cnt, 1LL);
+    const bool on = k < m;
     const int64_t slot = base + idx;
-    const double q = on ? (s == 0 ? w : -w) : 0.0;
-    const double oy = (k + 0.5) / npp;
+    const double qv = on ? (s == 0 ? w : -w) : 0.0;
+    const double oy = (k + 0.5) / (on ? m : npp);
     if (FP32) {
       Q.cell[slot] = ((uint32_t)(0 + CELL_BIAS) << 16) | (uint32_t)j;
       Q.dx[slot] = 0.5f;
       Q.dy[slot] = (float)oy;
       Q.ur[slot] = Q.ut[slot] = Q.up[slot] = 0.0f;
-      Q.qw[slot] = (float)q;
+      Q.qw[slot] = (float)qv;
       Q.id[slot] = id0 + idx;
-      if (on) qe = charge_exp(fabsf((float)q));
+      if (on) qe = charge_exp(fabsf((float)qv));
     } else {
       P.x1[slot] = 0.5;
       P.x2[slot] = j + oy;
       P.ur[slot] = P.ut[slot] = P.up[slot] = 0.0;
-      P.qw[slot] = q;
+      P.qw[slot] = qv;
       P.id[slot] = id0 + idx;
     }
     if (on) add_ll(cnt, 1LL);
@@ -308,18 +372,25 @@ void fields_filter(pic_ctx *c) {
 
 void inject(pic_ctx *c, double t) {
   const Grid &G = c->G;
-  const int npp = c->d.pairs_per_cell;
+  const int npp = c->d.pairs_per_cell, ns = c->d.inject_smooth;
   long long *smax = c->d_cnt + CNT_SMAX;
   cudaMemsetAsync(smax, 0, sizeof(long long), c->stream);
-  ++c->launches, k_inject_sigma<<<(G.nth + 127) / 128, 128, 0, c->stream>>>(G, c->f[ER], t, c->sig, smax);
+  double *a = c->sig, *b = c->sig + (G.nth + 1);
+  const int tb = (G.nth + 127) / 128;
+  ++c->launches, k_inject_sigma<<<tb, 128, 0, c->stream>>>(G, c->f[ER], t, a, ns ? nullptr : smax);
+  for (int p = 0; p < ns; ++p) {
+    ++c->launches, k_inject_smooth<<<tb, 128, 0, c->stream>>>(G.nth, a, b, p == ns - 1 ? smax : nullptr);
+    double *x = a; a = b; b = x;
+  }
+  const InjectRule R{c->d.inject, npp, c->d.f_inj, c->d.inject_q, c->d.inject_seed, (uint64_t)c->step};
   const int64_t nslots = (int64_t)G.nth * npp * 2;
   const int blocks = (int)((nslots + 255) / 256);
   if (c->d.precision == PIC_FP32)
-    ++c->launches, k_inject_write<true><<<blocks, 256, 0, c->stream>>>(G, c->sig, smax, c->p64, c->p32, c->n_used, c->next_id, npp,
-                                                        c->d.f_inj, c->d_cnt + CNT_INJECTED, c->d_cnt + CNT_QEXP);
+    ++c->launches, k_inject_write<true><<<blocks, 256, 0, c->stream>>>(G, a, smax, c->p64, c->p32, c->n_used, c->next_id, R,
+                                                        c->d_cnt + CNT_INJECTED, c->d_cnt + CNT_CAPPED, c->d_cnt + CNT_QEXP);
   else
-    ++c->launches, k_inject_write<false><<<blocks, 256, 0, c->stream>>>(G, c->sig, smax, c->p64, c->p32, c->n_used, c->next_id, npp,
-                                                         c->d.f_inj, c->d_cnt + CNT_INJECTED, c->d_cnt + CNT_QEXP);
+    ++c->launches, k_inject_write<false><<<blocks, 256, 0, c->stream>>>(G, a, smax, c->p64, c->p32, c->n_used, c->next_id, R,
+                                                         c->d_cnt + CNT_INJECTED, c->d_cnt + CNT_CAPPED, c->d_cnt + CNT_QEXP);
   c->n_used += nslots;
   c->next_id += nslots;
 }
@@ -399,6 +470,7 @@ void moments(pic_ctx *c, bool snapshot, pic_moments *out) {
   out->live = cnt[CNT_LIVE];
   out->deleted = cnt[CNT_DELETED];
   out->injected = cnt[CNT_INJECTED];
+  out->inject_capped = cnt[CNT_CAPPED];
   out->step = c->step;
   out->dt = G.dt;
   out->time = c->step * G.dt;

@@ -145,6 +145,20 @@ __device__ inline void vacuum_field(const Vac<T> &V, T r, T st, T ct, bool insid
       E[1] = -mu * W * T(2) * st * ct * ir * ir;
       break;
     }
+    case 5: {  // aligned dipole rotator: corotation inside, l = 2 vacuum field outside
+      T mu = b0 * r0 * r0 * r0, ir2 = ir * ir;
+      B[0] = T(2) * mu * ct * ir2 * ir;
+      B[1] = mu * st * ir2 * ir;
+      if (inside) {
+        E[0] = mu * W * st * st * ir2;
+        E[1] = -mu * W * T(2) * st * ct * ir2;
+      } else {
+        T a = mu * W * (q * q) * ir2;  // Omega mu r0^2 / r^4
+        E[0] = -a * (T(3) * ct * ct - T(1));
+        E[1] = -a * T(2) * st * ct;
+      }
+      break;
+    }
     default:
       break;
   }

@@ -28,7 +28,7 @@ constexpr int CELL_BIAS = 1024;
 
 // device counters (one int64 array)
 enum Counter { CNT_DELETED = 0, CNT_INJECTED = 1, CNT_LIVE = 2, CNT_SMAX = 3, CNT_GMAX = 4,
-               CNT_QMAX = 5, CNT_SORTED = 6, CNT_QEXP = 7, CNT_N };
+               CNT_QMAX = 5, CNT_SORTED = 6, CNT_QEXP = 7, CNT_CAPPED = 8, CNT_N };
 
 // FP32 path fixed-point deposit.  One flux unit is 2^(e - KFIX) with e =
 // ceil(log2 max |qw|) over every charge the context has held (loaded or
@@ -102,7 +102,7 @@ struct pic_ctx {
   alignas(64) unsigned char tile_maps[3][6 * 128] = {}; // FP32: field tensor maps per tile shape (TMA)
   double *Q = nullptr, *Qa = nullptr, *Qt = nullptr, *gsnap = nullptr;
   bool have_snap = false;
-  double *sig = nullptr;  // injection: surface charge per cell
+  double *sig = nullptr;  // injection: surface charge per cell, two buffers of nth + 1 (smoothing)
   // particles
   int64_t cap = 0, n_used = 0;
   pic::Parts64 p64, q64;  // current and alternate (compaction) buffers

@@ -26,7 +26,8 @@ PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 EXPORTS = ["pic_init_grid", "pic_load_particles", "pic_step", "pic_get_fields", "pic_set_fields", "pic_get_flux",
            "pic_get_particles", "pic_get_particles_noalloc", "pic_get_live", "pic_get_moments", "pic_get_luminosity",
            "pic_gauss_snapshot", "pic_set_clock", "pic_profile",
-           "pic_get_profile", "pic_get_launches", "pic_ensemble_step", "pic_autotune", "pic_destroy", "pic_last_error"]
+           "pic_get_profile", "pic_get_launches", "pic_ensemble_step", "pic_autotune", "pic_destroy", "pic_last_error",
+           "pic_struct_sizes"]
 
 
 class pic_desc(C.Structure):
@@ -44,6 +45,7 @@ class pic_desc(C.Structure):
         ("sort_interval", C.c_int32), ("capacity", C.c_int64),
         ("flux_quantum", C.c_double),
         ("tile_shape", C.c_int32),
+        ("inject_smooth", C.c_int32), ("inject_q", C.c_double), ("inject_seed", C.c_uint64),
     ]
 
 
@@ -53,6 +55,7 @@ class pic_moments(C.Structure):
         ("time", C.c_double), ("dt", C.c_double),
         ("kinetic_energy", C.c_double), ("field_energy", C.c_double),
         ("gauss_residual", C.c_double), ("total_charge", C.c_double),
+        ("inject_capped", C.c_int64),
     ]
 
 
@@ -116,7 +119,9 @@ def make_desc(**kw) -> pic_desc:
     enums = {
         "r_map": {"linear": 0, "log": 1}, "th_map": {"linear": 0, "equal_area": 1},
         "absorb_profile": {"none": 0, "linear": 1, "quadratic": 2},
-        "vacuum": {"none": 0, "monopole": 1, "monopole_rotator": 2, "uniform_bz": 3, "dipole_corot": 4},
+        "vacuum": {"none": 0, "monopole": 1, "monopole_rotator": 2, "uniform_bz": 3, "dipole_corot": 4,
+                   "dipole_rotator": 5},
+        "inject": {"off": 0, "fixed": 1, "variable": 2},
         "precision": {"fp64": 0, "fp32": 1}, "pusher": {"vay": 0, "boris": 1},
     }
     for k, v in kw.items():

@@ -34,6 +34,21 @@ def test_library_exports_every_declared_symbol():
     assert set(picsar.EXPORTS) == set(declared_symbols())
 
 
+def test_binding_structs_match_the_library():
+    """The ctypes mirrors of pic_desc and pic_moments have the library's sizes."""
+    from paper_1407_1810_gb300 import build, picsar
+
+    try:
+        path = build.build()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    lib = ctypes.CDLL(path)
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    lib.pic_struct_sizes(ctypes.byref(a), ctypes.byref(b))
+    assert a.value == ctypes.sizeof(picsar.pic_desc)
+    assert b.value == ctypes.sizeof(picsar.pic_moments)
+
+
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     from paper_1407_1810_gb300 import picsar
 
