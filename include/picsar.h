@@ -74,7 +74,7 @@ enum { PIC_INJECT_OFF = 0, PIC_INJECT_FIXED = 1, PIC_INJECT_VARIABLE = 2 };
 enum { PIC_FP64 = 0, PIC_FP32 = 1 };
 enum { PIC_VAY = 0, PIC_BORIS = 1 };
 enum { PIC_MEM_HOST = 0, PIC_MEM_DEVICE = 1 };
-enum { PIC_FIELDS_PLASMA = 0 };
+enum { PIC_FIELDS_PLASMA = 0, PIC_FIELDS_TOTAL = 1 };
 
 typedef struct pic_ctx pic_ctx;
 
@@ -155,11 +155,14 @@ int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const double *x2
  * update, lossy layer, injection).  Returns errors latched by earlier steps. */
 int pic_step(pic_ctx *c, int32_t nsteps);
 
-/* Plasma fields: out6 = 6 planes [E_r, E_th, E_ph, B_r, B_th, B_ph], each
+/* Fields: out6 = 6 planes [E_r, E_th, E_ph, B_r, B_th, B_ph], each
  * (nr+1) x (nth+1) FP64, row-major [i][j]; index (i, j) of a component means its
  * staggered point of Eq. (offseteq) (e.g. E_r[i][j] is at (i+1/2, j)); entries
- * outside a component's range are 0.  *n receives the element count
- * 6*(nr+1)*(nth+1); out6 == NULL only queries *n. */
+ * outside a component's range are 0.  which: PIC_FIELDS_PLASMA, the stored
+ * plasma field; PIC_FIELDS_TOTAL, plasma plus the analytic field of the
+ * descriptor's vacuum kind at time step * dt (Sec. 5.2; every grid point lies
+ * at r >= r0, where the outside analytic field applies).  *n receives the
+ * element count 6*(nr+1)*(nth+1); out6 == NULL only queries *n. */
 int pic_get_fields(pic_ctx *c, int32_t which, double *out6, int64_t *n, int32_t mem);
 
 /* Replace the plasma fields (layout of pic_get_fields; other entries ignored). */
@@ -169,6 +172,22 @@ int pic_set_fields(pic_ctx *c, const double *in6, int32_t mem);
  * (nr+2g+1) x (nth+1) FP64 with row index i+g, g = n_filt + 2 (ghost rows
  * inside the conductors).  *n receives the element count; out3 == NULL queries. */
 int pic_get_flux(pic_ctx *c, double *out3, int64_t *n, int32_t mem);
+
+/* Charge density in integral form (Sec. 2, Eq. Jcons): Q at every node, the
+ * sum over live particles of qw times the area (CIC) weight of the node in
+ * grid coordinates; with filtered != 0, after the n_filt 1-2-1 passes with
+ * the polar fold that the current also receives (App. B), i.e. the charge
+ * Gauss's law conserves.  Layout of one pic_get_flux plane: (nr+2g+1) x
+ * (nth+1) FP64, row index i+g.  *n receives the element count; out == NULL
+ * queries. */
+int pic_get_charge(pic_ctx *c, int32_t filtered, double *out, int64_t *n, int32_t mem);
+
+/* Grid coordinates of physical positions (Sec. 3.2): x1 = f_r^-1(r),
+ * x2 = f_th^-1(th) for n points, computed on the device; r, th, x1, x2 are n
+ * FP64 values each, host or device per mem.  Use it to load particles given
+ * as (r, theta). */
+int pic_grid_coords(pic_ctx *c, int64_t n, const double *r, const double *th, double *x1, double *x2,
+                    int32_t mem);
 
 /* Live particles, any order, FP64 (FP32 state is widened exactly: x1 = cell +
  * offset).  *n in: capacity of the buffers; out: live count.  A NULL x1 only

@@ -99,6 +99,7 @@ def _load():
         "orc_set_clock": (None, [P, I64, I64]),
         "orc_get_step": (I64, [P]),
         "orc_get_fields": (None, [P, D]),
+        "orc_get_fields_total": (None, [P, D]),
         "orc_set_fields": (None, [P, D]),
         "orc_ghost": (I32, [P]),
         "orc_get_flux": (None, [P, D]),
@@ -219,9 +220,10 @@ class Oracle:
     def set_clock(self, step, next_id):
         self.lib.orc_set_clock(self.h, step, next_id)
 
-    def fields(self):
+    def fields(self, total=False):
+        """Plasma fields, or with total=True plasma plus analytic field."""
         a = np.zeros(self.field_shape)
-        self.lib.orc_get_fields(self.h, _dp(a))
+        (self.lib.orc_get_fields_total if total else self.lib.orc_get_fields)(self.h, _dp(a))
         return a
 
     def set_fields(self, a):

@@ -230,6 +230,25 @@ int64_t orc_get_step(const orc_sim *s) { return s->step; }
 void orc_get_fields(const orc_sim *s, double *out6) {
   for (int c = 0; c < 6; ++c) memcpy(out6 + c * field_size(s), s->f[c], field_size(s) * sizeof(double));
 }
+static void vacuum_rt(const orc_sim *s, double r, double th, double t, int inside, double E[3], double B[3]);
+
+/* Total field (Sec. 5.2: plasma plus the analytic field, by linearity) at
+ * each component's staggered point, at the context's time step * dt; every
+ * grid point is at r >= r0, where the outside analytic field applies. */
+void orc_get_fields_total(const orc_sim *s, double *out6) {
+  static const int SI[6] = {1, 0, 0, 0, 1, 1}, SJ[6] = {0, 1, 0, 1, 0, 1};
+  const double t = s->step * s->p.dt;
+  orc_get_fields(s, out6);
+  for (int c = 0; c < 6; ++c) {
+    const int imax = SI[c] ? s->p.nr - 1 : s->p.nr, jmax = SJ[c] ? s->p.nth - 1 : s->p.nth;
+    for (int i = 0; i <= imax; ++i)
+      for (int j = 0; j <= jmax; ++j) {
+        double E[3], B[3];
+        vacuum_rt(s, SI[c] ? RB(s, i) : orc_f_r(s, (double)i), SJ[c] ? TB(s, j) : T_(s, j), t, 0, E, B);
+        out6[c * field_size(s) + FI(s, i, j)] += c < 3 ? E[c] : B[c - 3];
+      }
+  }
+}
 void orc_set_fields(orc_sim *s, const double *in6) {
   for (int c = 0; c < 6; ++c) memcpy(s->f[c], in6 + c * field_size(s), field_size(s) * sizeof(double));
 }

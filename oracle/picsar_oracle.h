@@ -80,6 +80,8 @@ int64_t orc_get_step(const orc_sim *s);
  * row-major [i][j]; entries outside a component's staggered range are 0. */
 void orc_get_fields(const orc_sim *s, double *out6);
 void orc_set_fields(orc_sim *s, const double *in6);
+/* the same layout, plasma plus analytic field at time step * dt (Sec. 5.2) */
+void orc_get_fields_total(const orc_sim *s, double *out6);
 /* fluxes F_r, F_th, F_ph of the last step (after filtering): 3 planes of
  * (nr+2g+1) x (nth+1), row index i+g, g = n_filt+2. */
 int32_t orc_ghost(const orc_sim *s);

@@ -292,6 +292,31 @@ __global__ void k_pack(Grid G, const double *__restrict__ src, double *__restric
   else dst[q] = in ? src[o] : 0.0;
 }
 
+// plasma plus analytic field of component k at its staggered points, time t
+__global__ void k_pack_total(Grid G, const double *__restrict__ src, double *__restrict__ dst, int k, int rows,
+                             int cols, int imax, int jmax, double t) {
+  const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+  if (i >= rows || j >= cols) return;
+  const size_t q = (size_t)i * cols + j;
+  if (i > imax || j > jmax) { dst[q] = 0.0; return; }
+  const Metric &m = G.m;
+  const double r = stag_i(k) ? m.r_h[i + G.PI] : m.r_n[i + G.PI];
+  const double st = stag_j(k) ? m.sin_tb[j + G.PJ] : m.sin_t[j + G.PJ];
+  const double ct = stag_j(k) ? m.cos_tb[j + G.PJ] : m.cos_t[j + G.PJ];
+  double E[3], B[3];
+  const Vac<double> V{G.vacuum, G.b0, G.r_min, omega_at(G.omega, G.t_spin, t)};
+  vacuum_field<double>(V, r, st, ct, false, E, B);
+  dst[q] = src[gidx(G, i, j)] + (k < 3 ? E[k] : B[k - 3]);
+}
+
+__global__ void k_grid_coords(Grid G, int64_t n, const double *__restrict__ r, const double *__restrict__ th,
+                              double *x1, double *x2) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  x1[k] = map_r_inv(G, r[k]);
+  x2[k] = map_th_inv(G, th[k]);
+}
+
 int to_user(pic_ctx *c, const double *dsrc, double *out, size_t n, int mem) {
   PIC_CUDA(cudaMemcpyAsync(out, dsrc, n * sizeof(double),
                            mem == PIC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
@@ -678,7 +703,7 @@ extern "C" int pic_step(pic_ctx *c, int32_t nsteps) {
 
 extern "C" int pic_get_fields(pic_ctx *c, int32_t which, double *out6, int64_t *n, int32_t mem) {
   if (!c || !n) return pic_fail(PIC_EINVAL, "null argument");
-  if (which != PIC_FIELDS_PLASMA) return pic_fail(PIC_EINVAL, "only the plasma field is stored");
+  if (which != PIC_FIELDS_PLASMA && which != PIC_FIELDS_TOTAL) return pic_fail(PIC_EINVAL, "bad field selector");
   const int rows = c->d.nr + 1, cols = c->d.nth + 1;
   const size_t plane = (size_t)rows * cols;
   *n = (int64_t)(6 * plane);
@@ -688,7 +713,11 @@ extern "C" int pic_get_fields(pic_ctx *c, int32_t which, double *out6, int64_t *
   dim3 gr((cols + 31) / 32, (rows + 7) / 8);
   for (int k = 0; k < 6; ++k) {
     int imax = stag_i(k) ? c->d.nr - 1 : c->d.nr, jmax = stag_j(k) ? c->d.nth - 1 : c->d.nth;
-    ++c->launches, k_pack<<<gr, dim3(32, 8), 0, c->stream>>>(c->G, c->f[k], tmp + k * plane, 0, rows, cols, imax, jmax, 0);
+    if (which == PIC_FIELDS_TOTAL)
+      ++c->launches, k_pack_total<<<gr, dim3(32, 8), 0, c->stream>>>(c->G, c->f[k], tmp + k * plane, k, rows, cols, imax,
+                                                                     jmax, c->step * c->G.dt);
+    else
+      ++c->launches, k_pack<<<gr, dim3(32, 8), 0, c->stream>>>(c->G, c->f[k], tmp + k * plane, 0, rows, cols, imax, jmax, 0);
   }
   int e = to_user(c, tmp, out6, 6 * plane, mem);
   cudaFree(tmp);
@@ -732,6 +761,53 @@ extern "C" int pic_get_flux(pic_ctx *c, double *out3, int64_t *n, int32_t mem) {
   int e = to_user(c, tmp, out3, 3 * plane, mem);
   cudaFree(tmp);
   return e;
+}
+
+extern "C" int pic_get_charge(pic_ctx *c, int32_t filtered, double *out, int64_t *n, int32_t mem) {
+  if (!c || !n) return pic_fail(PIC_EINVAL, "null argument");
+  const int g = c->G.g, rows = c->d.nr + 2 * g + 1, cols = c->d.nth + 1;
+  const size_t plane = (size_t)rows * cols;
+  *n = (int64_t)plane;
+  if (!out) return PIC_OK;
+  cudaMemsetAsync(c->Q, 0, c->grid_elems * sizeof(double), c->stream);
+  cudaMemsetAsync(c->Qa, 0, c->grid_elems * sizeof(double), c->stream);
+  if (c->d.precision == PIC_FP32) charge32(c, c->Q, c->Qa);
+  else charge64(c, c->Q, c->Qa);
+  if (filtered) filter_array(c, c->Q, c->Qt, 0, +1, c->d.n_filt);
+  double *tmp;
+  PIC_CUDA(cudaMalloc((void **)&tmp, plane * sizeof(double)));
+  dim3 gr((cols + 31) / 32, (rows + 7) / 8);
+  ++c->launches, k_pack<<<gr, dim3(32, 8), 0, c->stream>>>(c->G, c->Q, tmp, -g, rows, cols, c->d.nr + g, c->d.nth, 0);
+  int e = to_user(c, tmp, out, plane, mem);
+  cudaFree(tmp);
+  if (e) return e;
+  latch_errors(c);
+  return status(c);
+}
+
+extern "C" int pic_grid_coords(pic_ctx *c, int64_t n, const double *r, const double *th, double *x1, double *x2,
+                               int32_t mem) {
+  if (!c || n < 0) return pic_fail(PIC_EINVAL, "bad argument");
+  if (n == 0) return PIC_OK;
+  if (!r || !th || !x1 || !x2) return pic_fail(PIC_EINVAL, "null array");
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (mem == PIC_MEM_DEVICE) {
+    ++c->launches, k_grid_coords<<<blocks, 256, 0, c->stream>>>(c->G, n, r, th, x1, x2);
+    PIC_CUDA(cudaGetLastError());
+    PIC_CUDA(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+  }
+  double *d;
+  PIC_CUDA(cudaMalloc((void **)&d, 4 * (size_t)n * sizeof(double)));
+  cudaMemcpyAsync(d, r, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(d + n, th, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  ++c->launches, k_grid_coords<<<blocks, 256, 0, c->stream>>>(c->G, n, d, d + n, d + 2 * n, d + 3 * n);
+  cudaMemcpyAsync(x1, d + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(x2, d + 3 * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t err = cudaStreamSynchronize(c->stream);
+  cudaFree(d);
+  if (err != cudaSuccess) return pic_fail(PIC_ECUDA, cudaGetErrorString(err));
+  return PIC_OK;
 }
 
 extern "C" int pic_get_particles(pic_ctx *c, int64_t *n, double *x1, double *x2, double *u_r, double *u_th,

@@ -27,7 +27,7 @@ EXPORTS = ["pic_init_grid", "pic_load_particles", "pic_step", "pic_get_fields", 
            "pic_get_particles", "pic_get_particles_noalloc", "pic_get_live", "pic_get_moments", "pic_get_luminosity",
            "pic_gauss_snapshot", "pic_set_clock", "pic_profile",
            "pic_get_profile", "pic_get_launches", "pic_ensemble_step", "pic_autotune", "pic_destroy", "pic_last_error",
-           "pic_struct_sizes"]
+           "pic_struct_sizes", "pic_get_charge", "pic_grid_coords"]
 
 
 class pic_desc(C.Structure):
@@ -78,6 +78,8 @@ def lib():
         "pic_get_fields": [P, I32, P, C.POINTER(C.c_int64), I32],
         "pic_set_fields": [P, P, I32],
         "pic_get_flux": [P, P, C.POINTER(C.c_int64), I32],
+        "pic_get_charge": [P, I32, P, C.POINTER(C.c_int64), I32],
+        "pic_grid_coords": [P, I64, P, P, P, P, I32],
         "pic_get_particles": [P, C.POINTER(C.c_int64), P, P, P, P, P, P, P, I32],
         "pic_get_moments": [P, C.POINTER(pic_moments)],
         "pic_get_live": [P, C.POINTER(C.c_int64), C.POINTER(C.c_double)],
@@ -177,12 +179,31 @@ class Simulation:
     def step_rc(self, n=1):
         return self.L.pic_step(self.h, n)
 
-    def fields(self):
+    def fields(self, total=False):
+        """Plasma fields (6, nr+1, nth+1), or plasma plus analytic field."""
+        which = 1 if total else 0
         n = C.c_int64()
-        check(self.L.pic_get_fields(self.h, 0, None, C.byref(n), PIC_MEM_HOST))
+        check(self.L.pic_get_fields(self.h, which, None, C.byref(n), PIC_MEM_HOST))
         out = np.empty(n.value)
-        check(self.L.pic_get_fields(self.h, 0, C.c_void_p(out.ctypes.data), C.byref(n), PIC_MEM_HOST))
+        check(self.L.pic_get_fields(self.h, which, C.c_void_p(out.ctypes.data), C.byref(n), PIC_MEM_HOST))
         return out.reshape(6, self.nr + 1, self.nth + 1)
+
+    def charge(self, filtered=False):
+        """Node charge (nr+2g+1, nth+1), row i+g: pic_get_charge."""
+        n = C.c_int64()
+        check(self.L.pic_get_charge(self.h, int(filtered), None, C.byref(n), PIC_MEM_HOST))
+        out = np.empty(n.value)
+        check(self.L.pic_get_charge(self.h, int(filtered), C.c_void_p(out.ctypes.data), C.byref(n), PIC_MEM_HOST))
+        return out.reshape(self.nr + 2 * self.g + 1, self.nth + 1)
+
+    def grid_coords(self, r, th):
+        """(x1, x2) of physical positions: pic_grid_coords."""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        th = np.ascontiguousarray(th, dtype=np.float64)
+        x1, x2 = np.empty_like(r), np.empty_like(r)
+        check(self.L.pic_grid_coords(self.h, len(r), C.c_void_p(r.ctypes.data), C.c_void_p(th.ctypes.data),
+                                     C.c_void_p(x1.ctypes.data), C.c_void_p(x2.ctypes.data), PIC_MEM_HOST))
+        return x1, x2
 
     def set_fields(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64)

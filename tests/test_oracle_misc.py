@@ -156,3 +156,31 @@ def test_particles_only_is_the_particle_part_of_a_step(oracle_mod):
     assert a.counters() == b.counters()
     assert np.array_equal(a.fields(), fa)
     assert a.lib.orc_get_step(a.h) == 4 and b.lib.orc_get_step(b.h) == 5
+
+
+def test_total_fields_add_the_analytic_field_at_each_stagger(oracle_mod):
+    """Sec. 5.2: the total field is the plasma field plus the analytic field,
+    each component at its own staggered point of Eq. (offseteq) (E_r at
+    (i+1/2, j), E_th at (i, j+1/2), B_r at (i, j+1/2)), at time step * dt."""
+    b0, om = 2.0, 0.2
+    o = _o(vacuum="monopole_rotator", b0=b0, omega=om, t_spin=0.0, nr=12, nth=10)
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal(o.field_shape)
+    o.set_fields(f)
+    f = o.fields()
+    o.set_clock(7, 0)
+    tot = o.fields(total=True)
+    i, j = np.arange(o.nr + 1), np.arange(o.nth + 1)
+    rn, rh = o.f_r(i), o.f_r(i + 0.5)
+    tn, th = o.f_th(j), o.f_th(np.arange(o.nth) + 0.5)
+    a = lambda r: b0 * om / r**3  # B0 r0^4 Omega / r^3 with r0 = 1
+    N, M = o.nr, o.nth
+    np.testing.assert_allclose(tot[0, :N, :] - f[0, :N, :], (-2 * a(rh[:N]))[:, None] * np.cos(tn)[None, :],
+                               rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(tot[1, :, :M] - f[1, :, :M], (-a(rn))[:, None] * np.sin(th[:M])[None, :],
+                               rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(tot[3, :, :M] - f[3, :, :M], (b0 / rn**2)[:, None] * np.ones(M)[None, :], rtol=1e-13)
+    for c in (2, 4, 5):
+        np.testing.assert_array_equal(tot[c], f[c])
+    # outside a component's range nothing is added
+    assert np.array_equal(tot[0, N, :], f[0, N, :]) and np.array_equal(tot[1, :, M], f[1, :, M])
