@@ -260,24 +260,47 @@ def gpu_arm(args):
 
 
 def fp64_run(cfg, dev, stream, args):
+    """The plain FP64 path on the same workload, timed; both paths then run
+    the same number of steps from one FP32-rounded state and their plasma
+    fields are compared (relative L2)."""
+    import numpy as np
     import torch
 
     ntot = cfg["nr"] * cfg["nth"] * cfg["pairs_per_cell"] * 2
     sim, qw, _, _ = W.make_sim(cfg, "fp64", stream.cuda_stream, ntot + (1 << 20))
-    W.load_plasma(sim, cfg, qw, dev, stream)
+    W.load_plasma(sim, cfg, qw, dev, stream, fp32_state=True)
     sim.step(2)
     sim.profile(True)
     ms, units, _ = time_steps(sim, args.fp64_steps, stream)
+    sim.profile(False)
     prof, _ = sim.get_profile()
     live = sim.live()
     kms = prof["particles"]
     res = {"value": units / (ms * 1e-3), "steps": args.fp64_steps, "ms_per_step": ms / args.fp64_steps,
            "hot_kernel": {"name": "k_particles64", "ms_per_launch": kms,
                           "achieved_GBps": ALG_BYTES_FP64 * live / (kms * 1e-3) / 1e9 if kms else None}}
+    nsteps = 2 + args.fp64_steps
+    f64 = sim.fields()
+    gauss64 = sim.moments()["gauss_residual"]
     sim.close()
     del sim
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
+    sim, qw, _, _ = W.make_sim(cfg, "fp32", stream.cuda_stream, ntot + (1 << 20))
+    W.load_plasma(sim, cfg, qw, dev, stream, fp32_state=True)
+    sim.step(nsteps)
+    f32 = sim.fields()
+    sim.close()
+    del sim
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    band = slice(32, cfg["nth"] + 1 - 32)  # 32 cells clear of each pole
+    d = f32 - f64
+    res["fp32_vs_fp64_fields"] = {
+        "rel_l2": float(np.linalg.norm(d) / np.linalg.norm(f64)),
+        "rel_l2_away_from_axis": float(np.linalg.norm(d[:, :, band]) / np.linalg.norm(f64[:, :, band])),
+        "steps": nsteps, "start": "one FP32-rounded state", "fp64_gauss_residual": gauss64,
+        "note": "near the poles an axis crossing with u_ph within rounding of 0 sweeps +pi or -pi of azimuth"}
     return res
 
 

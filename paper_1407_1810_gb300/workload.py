@@ -30,8 +30,12 @@ def make_sim(cfg: dict, precision: str | None = None, stream=0, capacity: int | 
     return P.Simulation(P.make_desc(**kw), stream=stream), qw, dt, b0
 
 
-def load_plasma(sim, cfg: dict, qw: float, device, stream=None, rows_per_chunk: int = 128) -> int:
-    """Draw the config's pair plasma on the device and load it; returns the count."""
+def load_plasma(sim, cfg: dict, qw: float, device, stream=None, rows_per_chunk: int = 128,
+                fp32_state: bool = False) -> int:
+    """Draw the config's pair plasma on the device and load it; returns the
+    count.  fp32_state: round it first to what the FP32 path stores (cell +
+    FP32 offset, FP32 momenta and charge), so that both paths can start from
+    one state."""
     import torch
 
     from . import synthetic
@@ -41,6 +45,12 @@ def load_plasma(sim, cfg: dict, qw: float, device, stream=None, rows_per_chunk: 
     with ctx:
         for ch in synthetic.pair_plasma_torch(cfg["nr"], cfg["nth"], cfg["pairs_per_cell"], cfg["T"], qw,
                                               cfg["seed"], device, rows_per_chunk=rows_per_chunk):
+            if fp32_state:
+                for k in ("x1", "x2"):
+                    c = torch.floor(ch[k])
+                    ch[k] = c + (ch[k] - c).float().double()
+                for k in ("ur", "uth", "uph", "qw"):
+                    ch[k] = ch[k].float().double()
             sim.load(ch["x1"], ch["x2"], ch["ur"], ch["uth"], ch["uph"], ch["qw"])
             n += ch["x1"].numel()
             del ch
