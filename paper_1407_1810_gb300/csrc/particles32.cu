@@ -498,16 +498,40 @@ __global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P, const __gri
   }
 }
 
+// (double)v * 2^s built on the integer pipes: v rounded to 53 bits (to
+// nearest, ties to even, as the FP64 conversion does; exact for the sums
+// below 2^53 that occur in practice) and the power of two added to the
+// exponent, which is exact while the result stays normal (s in [-126, 64] here).
+// The same IEEE value as the conversion and multiply, without the FP64 pipe,
+// whose rate on this part made the conversion pass compute-bound.
+__device__ inline double fixed_to_f64(long long v, int s) {
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long m = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  int e = 63 - __clzll((long long)m);  // m in [2^e, 2^(e+1))
+  unsigned long long mant;
+  if (e <= 52) {
+    mant = m << (52 - e);
+  } else {
+    const int sh = e - 52;
+    const unsigned long long q = m >> sh, rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    mant = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+    if (mant >> 53) { mant >>= 1; ++e; }
+  }
+  const unsigned long long bits = sign | ((unsigned long long)(e + s + 1023) << 52) | (mant & ((1ull << 52) - 1ull));
+  return __longlong_as_double((long long)bits);
+}
+
 // fixed point -> FP64 fluxes over the ghost band; clears the accumulators
 __global__ void k_flux_from_acc(int nr, int nth, int g, int PI, int PJ, int LD, const long long *qexp,
                                 long long *a0, long long *a1, long long *a2, double *F0, double *F1, double *F2) {
   const int j = blockIdx.x * 32 + threadIdx.x, i = -g + (int)(blockIdx.y * 8 + threadIdx.y);
   if (i > nr + g || j > nth) return;
-  const double q0 = ldexp(1.0, qexp_value(qexp) - KFIX);  // charge of one flux unit
+  const int s = qexp_value(qexp) - KFIX;  // one flux unit is 2^s of charge
   const size_t o = (size_t)(i + PI) * LD + (size_t)(j + PJ);
-  F0[o] = (double)a0[o] * q0; a0[o] = 0;
-  F1[o] = (double)a1[o] * q0; a1[o] = 0;
-  F2[o] = (double)a2[o] * q0; a2[o] = 0;
+  F0[o] = fixed_to_f64(a0[o], s); a0[o] = 0;
+  F1[o] = fixed_to_f64(a1[o], s); a1[o] = 0;
+  F2[o] = fixed_to_f64(a2[o], s); a2[o] = 0;
 }
 
 // ---- counting sort into tile bins (drops removed particles) ---------------
