@@ -218,7 +218,7 @@ int pic_get_live(pic_ctx *c, int64_t *live, double *kinetic_energy);
  * taken by the first pic_step or by pic_gauss_snapshot. */
 int pic_get_moments(pic_ctx *c, pic_moments *out);
 
-/* Spin-down luminosity profile (Sec. 5.3, the luminosity of Fig. monofig d):
+/* Spin-down luminosity profile (Sec. 5.3, the luminosity of Fig. 7d):
  * L[i], i = 0..nr, the radial Poynting flux (E x B)_r (c = 1) of the total
  * field -- plasma plus the analytic field at the current time -- through the
  * sphere of node radius r_i, for 1 <= i <= nr - 1 (L[0] = L[nr] = 0).  The

@@ -395,7 +395,7 @@ void inject(pic_ctx *c, double t) {
   c->next_id += nslots;
 }
 
-// Spin-down luminosity (Sec. 5.3, Fig. monofig d): the radial Poynting flux
+// Spin-down luminosity (Sec. 5.3, Fig. 7d): the radial Poynting flux
 // (E x B)_r of the total field, plasma plus analytic at time t, through the
 // sphere of node radius r_i, one block per interior row.  On the sphere the
 // meridional cell j carries E_th(i, j+1/2); B_ph (at i -+ 1/2), E_ph (at the
