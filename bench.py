@@ -527,7 +527,10 @@ def steady_arm(args):
            "physics": {"L_over_L0_r1.5_to_25": {"mean": float(L[sel].mean()), "min": float(L[sel].min()),
                                                  "max": float(L[sel].max())},
                        "bphi_over_br_to_michel": bphi, "r2jr_scale_to_michel": r2jr,
-                       "gauss_residual": res["gauss_residual"]}}
+                       "poynting_plus_particle_flux_over_L0": {
+                           f"r={x:g}": round(float(L[np.argmin(np.abs(r - x))] + lp), 4)
+                           for x, lp in zip(res["lp_radii"], res["Lp_over_L0"])},
+                       "gamma_median": res["gamma_median"], "gauss_residual": res["gauss_residual"]}}
     if rank == 0:
         print(json.dumps(out), flush=True)
 

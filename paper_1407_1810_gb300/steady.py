@@ -71,6 +71,31 @@ def r2jr(fr_mean, cfg: dict, b0: float, dt: float, r: float, band: float = 0.04)
     return np.arccos(1.0 - 2.0 * j / nth), prof / j0r02
 
 
+def particle_energy_flux(sim, cfg: dict, radii, band: float = 0.05, q_over_m: float = 1.0):
+    """Kinetic energy carried outward by the plasma through the sphere of each
+    radius: the sum over the particles in the shell r (1 -+ band) of
+    (gamma - 1) |qw| / (q/m) v_r, divided by the shell's width (c = 1, the
+    units of the Poynting flux).  Also the median gamma beyond 2 r0."""
+    import torch
+
+    d = sim.particles(device="cuda")
+    gam = torch.sqrt(1.0 + d["ur"] ** 2 + d["uth"] ** 2 + d["uph"] ** 2)
+    e = (gam - 1.0) * d["qw"].abs() / q_over_m * d["ur"] / gam
+    if cfg["r_map"] == "log":
+        r = cfg["r_min"] * torch.exp(d["x1"] * (math.log(cfg["r_max"] / cfg["r_min"]) / cfg["nr"]))
+    else:
+        r = cfg["r_min"] + d["x1"] * ((cfg["r_max"] - cfg["r_min"]) / cfg["nr"])
+    flux = []
+    for rad in radii:
+        m = (r > rad * (1 - band)) & (r < rad * (1 + band))
+        flux.append(float(e[m].sum()) / (2 * band * rad))
+    far = r > 2.0 * cfg["r_min"]
+    gmed = float(gam[far].median()) if bool(far.any()) else float("nan")
+    del d, gam, e, r, far
+    torch.cuda.empty_cache()
+    return np.array(flux), gmed
+
+
 def run(cfg: dict | None = None, periods: float = 2.0, chunk: int = 500, average_over: float = 0.05, log=None):
     """Run the rotator for `periods` rotation periods on the current GPU.
 
@@ -125,7 +150,10 @@ def run(cfg: dict | None = None, periods: float = 2.0, chunk: int = 500, average
                           "theta_j": tj, "r2jr": jr, "r2jr_err": float(np.linalg.norm(jr + np.cos(tj)) /
                                                                       np.linalg.norm(np.cos(tj)))}
     m = sim.moments()
+    radii = np.array([1.5, 2.0, 3.0, 5.0, 7.5, 10.0, 15.0, 20.0, 25.0])
+    lp, gmed = particle_energy_flux(sim, cfg, radii)
     sim.close()
     return {"r": r, "L_over_L0": L / michel_l0(b0, omega, cfg["r_min"]), "steps": steps, "dt": dt, "b0": b0,
             "particles": m["live"], "injected": m["injected"], "gauss_residual": m["gauss_residual"],
-            "particle_steps_per_s": units / elapsed, "seconds": elapsed, "bphi": profiles}
+            "particle_steps_per_s": units / elapsed, "seconds": elapsed, "bphi": profiles,
+            "lp_radii": radii, "Lp_over_L0": lp / michel_l0(b0, omega, cfg["r_min"]), "gamma_median": gmed}
