@@ -17,7 +17,7 @@ import pytest
 import oracle as O
 from paper_1407_1810_gb300 import configs
 
-from gpu_common import KEYS, by_id, fp32_state, rel_l2, replay_compare_fp32, setup
+from gpu_common import KEYS, rel_l2, replay_compare_fp32, setup
 
 pytestmark = pytest.mark.gpu
 TAU = 2e-6

@@ -3,14 +3,11 @@
 Bar (FP64 path): fields, fluxes and momenta within 1e-12 relative after 100
 steps; particle counts, cells, injections and removals exact.
 """
-import math
-
 import numpy as np
 import pytest
 
 import oracle as O
-from oracle.oracle import courant_dt
-from paper_1407_1810_gb300 import configs, synthetic
+from paper_1407_1810_gb300 import configs
 
 from gpu_common import KEYS, by_id, rel_l2, setup
 

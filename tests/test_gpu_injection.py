@@ -61,10 +61,6 @@ def _variable_q(cfg):
     return cfg["f_inj"] * float(np.max(sig * dA)) / 5.0
 
 
-def _ids(d):
-    return set(d["id"].tolist())
-
-
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_variable_count_injection_against_oracle(precision):
     cfg = _cfg(precision, inject=2, inject_pairs=4, inject_seed=12345)
