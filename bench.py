@@ -543,7 +543,9 @@ def steady_arm(args):
                        "poynting_plus_particle_flux_over_L0": {
                            f"r={x:g}": round(float(L[np.argmin(np.abs(r - x))] + lp), 4)
                            for x, lp in zip(res["lp_radii"], res["Lp_over_L0"])},
-                       "gamma_median": res["gamma_median"], "gauss_residual": res["gauss_residual"]}}
+                       "gamma_median": res["gamma_median"],
+                       "positive_charge_share_beyond_2r0": res["positive_share"],
+                       "gauss_residual": res["gauss_residual"]}}
     if rank == 0:
         print(json.dumps(out), flush=True)
 

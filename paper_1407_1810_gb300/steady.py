@@ -91,9 +91,23 @@ def particle_energy_flux(sim, cfg: dict, radii, band: float = 0.05, q_over_m: fl
         flux.append(float(e[m].sum()) / (2 * band * rad))
     far = r > 2.0 * cfg["r_min"]
     gmed = float(gam[far].median()) if bool(far.any()) else float("nan")
-    del d, gam, e, r, far
+    # charge separation (Fig. 7c): share of the charge that is positive in
+    # each hemisphere (theta < 80 deg, theta > 100 deg), beyond 2 r0; the
+    # Goldreich-Julian density of a monopole, -2 Omega.B, changes sign with
+    # cos(theta)
+    if cfg["th_map"] == "equal_area":
+        th = torch.arccos(torch.clamp(1.0 - 2.0 * d["x2"] / cfg["nth"], -1.0, 1.0))
+    else:
+        th = d["x2"] * (math.pi / cfg["nth"])
+    sep = {}
+    for name, zone in (("north", th < 4 * math.pi / 9), ("south", th > 5 * math.pi / 9)):
+        m = far & zone
+        q = d["qw"][m]
+        tot = float(q.abs().sum())
+        sep[name] = float(q[q > 0].sum()) / tot if tot > 0 else float("nan")
+    del d, gam, e, r, far, th
     torch.cuda.empty_cache()
-    return np.array(flux), gmed
+    return np.array(flux), gmed, sep
 
 
 def run(cfg: dict | None = None, periods: float = 2.0, chunk: int = 500, average_over: float = 0.05, log=None):
@@ -151,9 +165,10 @@ def run(cfg: dict | None = None, periods: float = 2.0, chunk: int = 500, average
                                                                       np.linalg.norm(np.cos(tj)))}
     m = sim.moments()
     radii = np.array([1.5, 2.0, 3.0, 5.0, 7.5, 10.0, 15.0, 20.0, 25.0])
-    lp, gmed = particle_energy_flux(sim, cfg, radii)
+    lp, gmed, sep = particle_energy_flux(sim, cfg, radii)
     sim.close()
     return {"r": r, "L_over_L0": L / michel_l0(b0, omega, cfg["r_min"]), "steps": steps, "dt": dt, "b0": b0,
             "particles": m["live"], "injected": m["injected"], "gauss_residual": m["gauss_residual"],
             "particle_steps_per_s": units / elapsed, "seconds": elapsed, "bphi": profiles,
-            "lp_radii": radii, "Lp_over_L0": lp / michel_l0(b0, omega, cfg["r_min"]), "gamma_median": gmed}
+            "lp_radii": radii, "Lp_over_L0": lp / michel_l0(b0, omega, cfg["r_min"]), "gamma_median": gmed,
+            "positive_share": sep}

@@ -77,6 +77,17 @@ def test_energy_flux_is_conserved_across_radii(steady_run):
     assert 15.0 <= steady_run["gamma_median"] <= 45.0, steady_run["gamma_median"]
 
 
+def test_plasma_is_charge_separated_by_hemisphere(steady_run):
+    """Fig. 7c: surface injection gives a charge-separated plasma.  Beyond
+    2 r0 the charge is mostly negative in the northern hemisphere and mostly
+    positive in the southern one, the sign of -2 Omega.B for the monopole
+    (measured: 29.8 % and 70.5 % of the charge positive), mirror images of
+    each other."""
+    sh = steady_run["positive_share"]
+    assert sh["north"] < 0.4 and sh["south"] > 0.6, sh
+    assert abs(sh["north"] + sh["south"] - 1.0) < 0.02, sh
+
+
 def test_particle_count_and_gauss(steady_run):
     assert 1.5e7 <= steady_run["particles"] <= 2.5e7, steady_run["particles"]
     assert steady_run["gauss_residual"] <= 1e-6
