@@ -56,3 +56,27 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(picsar, "_lib", None)
     with pytest.raises(ImportError):
         picsar.lib()
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nr=1), dict(r_min=0.0), dict(r_max=0.5), dict(r_map=2), dict(th_map=2), dict(n_filt=17),
+    dict(absorb_cells=64), dict(vacuum=6), dict(precision=2), dict(pusher=2), dict(tile_shape=3),
+    dict(inject=3), dict(inject=1, f_inj=1.5), dict(inject=1, f_inj=0.0), dict(inject=2, f_inj=0.5, inject_q=0.0),
+    dict(inject=2, f_inj=0.5, inject_q=float("inf")), dict(inject_smooth=65), dict(inject_smooth=-1),
+    dict(flux_quantum=-1.0),
+])
+def test_descriptor_validation_rejects_bad_values(bad):
+    """pic_init_grid checks the descriptor before any device work, so a bad
+    value is refused with PIC_EINVAL on any machine."""
+    from paper_1407_1810_gb300 import build, picsar as P
+
+    try:
+        build.build()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    kw = dict(nr=64, nth=64, r_min=1.0, r_max=10.0, r_map="log", th_map="linear", dt=0.01, n_filt=0,
+              absorb_cells=8, absorb_profile="linear", vacuum="monopole", b0=1.0, precision="fp64", pusher="vay")
+    kw.update(bad)
+    with pytest.raises(P.PicError) as e:
+        P.Simulation(P.make_desc(**kw))
+    assert e.value.code == P.PIC_EINVAL
