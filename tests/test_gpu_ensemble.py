@@ -64,6 +64,33 @@ def test_ensemble_equals_independent_steps(precision):
         assert a.moments()["live"] == b.moments()["live"], k
 
 
+def test_ensemble_with_variable_count_injection():
+    """Variable-count injection keys its rounding on the step number; the
+    ensemble captures each member's steps into CUDA graphs, and every
+    captured step must carry its own key: the members' injected ids, counts
+    and fields equal those of independent steps bit for bit."""
+    from paper_1407_1810_gb300 import picsar as P
+
+    base = dict(configs.CONFIGS["rotator-1024x1024"], nr=24, nth=16, pairs_per_cell=1, absorb_cells=4, t_spin=0.0,
+                inject=2, inject_pairs=6, inject_smooth=1)
+    cfgs = [dict(base, inject_q=q, inject_seed=sd) for q, sd in ((2.0, 11), (0.7, 12))]
+    ens, ref = [], []
+    for cfg in cfgs:
+        s1, _, plasma, _ = setup(cfg)
+        s2, _, _, _ = setup(cfg, plasma=plasma)
+        ens.append(s1)
+        ref.append(s2)
+    P.ensemble_step(ens, 50)
+    for s in ref:
+        s.step(50)
+    for k, (a, b) in enumerate(zip(ens, ref)):
+        ma, mb = a.moments(), b.moments()
+        assert ma["injected"] == mb["injected"] > 0 and ma["inject_capped"] == mb["inject_capped"], k
+        assert np.array_equal(a.fields(), b.fields()), k
+        ia, ib = np.sort(a.particles()["id"]), np.sort(b.particles()["id"])
+        assert np.array_equal(ia, ib), k
+
+
 def test_ensemble_with_injection_member():
     from paper_1407_1810_gb300 import picsar as P
 
