@@ -10,7 +10,10 @@ value L0 = (8 pi / 3) B0^2 r0^4 Omega^2 (Lorentz-Heaviside units; the paper
 writes (2c/3) (B0 r0^2 / R_l)^2 in Gaussian units), and B_ph / B_r follows
 the split-monopole (Michel) solution -Omega r sin(theta) / c; the radial
 current follows r^2 J_r = -J0 r0^2 cos(theta) with J0 r0^2 = 2 B0 Omega r0^2
-(Fig. 7a, b, d).
+(Fig. 7a, b, d).  The run also measures the plasma's kinetic energy flux
+through the same spheres (Poynting plus particle flux is the conserved
+total), the particles' median gamma (the paper: about 28) and the charge
+separation of Fig. 7c (the share of positive charge in each hemisphere).
 
 The paper gives no B0; it asks for a Larmor radius below a cell at the
 surface for particles of gamma ~ 28, i.e. omega_c dt above ~17: omega_c dt = 40
