@@ -13,7 +13,13 @@ end through the C-ABI with the particle state loaded from pinned host memory
 the FP64 CPU oracle on a bounded sample (cpu_baseline) and the SM clocks seen
 during the timed region.
 
+The FP64 leg also runs both paths from one FP32-rounded state and reports
+their field difference, whole grid and away from the poles.
+
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py --workload NAME [--precision fp32|fp64]   # any workload on either path
+  python bench.py --workload ensemble-64                     # 64 uneven members in CUDA graphs
+  python bench.py --workload rotator-steady                  # the Table 1 run and its physics
 Under torchrun every rank runs an independent replica (weak scaling).
 """
 from __future__ import annotations
