@@ -348,12 +348,14 @@ __global__ void k_load64(Grid G, Parts64 P, int64_t base, int64_t n, const doubl
                          int *err) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
-  const double a = x1[k], b = x2[k], q = qw[k];
-  const bool ok = a >= -(double)(G.n_filt + 1) && a < (double)(G.nr + G.n_filt + 1) && b >= 0.0 && b <= G.nth &&
-                  q != 0.0 && isfinite(q) && isfinite(ur[k]) && isfinite(ut[k]) && isfinite(up[k]);
+  // all six reads first, then the checks (without short-circuit): from
+  // pinned host memory each dependent read would cost a host-link round trip
+  const double a = x1[k], b = x2[k], q = qw[k], vr = ur[k], vt = ut[k], vp = up[k];
+  const bool ok = (a >= -(double)(G.n_filt + 1)) & (a < (double)(G.nr + G.n_filt + 1)) & (b >= 0.0) & (b <= G.nth) &
+                  (q != 0.0) & isfinite(q) & isfinite(vr) & isfinite(vt) & isfinite(vp);
   const int64_t d = base + k;
   if (!ok) { atomicOr(err, ERR_RANGE); P.qw[d] = 0.0; return; }
-  P.x1[d] = a; P.x2[d] = b; P.ur[d] = ur[k]; P.ut[d] = ut[k]; P.up[d] = up[k]; P.qw[d] = q; P.id[d] = id0 + k;
+  P.x1[d] = a; P.x2[d] = b; P.ur[d] = vr; P.ut[d] = vt; P.up[d] = vp; P.qw[d] = q; P.id[d] = id0 + k;
 }
 
 __global__ void k_load32(Grid G, Parts32 P, int64_t base, int64_t n, const double *x1, const double *x2,
@@ -362,9 +364,12 @@ __global__ void k_load32(Grid G, Parts32 P, int64_t base, int64_t n, const doubl
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int qe = (int)QEXP_NONE;
   if (k < n) {
-    const double a = x1[k], b = x2[k], q = qw[k];
-    const bool ok = a >= -(double)(G.n_filt + 1) && a < (double)(G.nr + G.n_filt + 1) && b >= 0.0 && b <= G.nth &&
-                    fabs(q) >= 0x1p-100 && fabs(q) <= 0x1p100 && isfinite(ur[k]) && isfinite(ut[k]) && isfinite(up[k]);
+    // all six reads first, then the checks (without short-circuit): from
+    // pinned host memory each dependent read would cost a host-link round trip
+    const double a = x1[k], b = x2[k], q = qw[k], vr = ur[k], vt = ut[k], vp = up[k];
+    const bool ok = (a >= -(double)(G.n_filt + 1)) & (a < (double)(G.nr + G.n_filt + 1)) & (b >= 0.0) &
+                    (b <= G.nth) & (fabs(q) >= 0x1p-100) & (fabs(q) <= 0x1p100) & isfinite(vr) & isfinite(vt) &
+                    isfinite(vp);
     const int64_t d = base + k;
     if (!ok) {
       atomicOr(err, ERR_RANGE);
@@ -378,7 +383,7 @@ __global__ void k_load32(Grid G, Parts32 P, int64_t base, int64_t n, const doubl
       if (oy >= 1.0f && cj < G.nth - 1) { oy = 0.0f; ++cj; }
       P.cell[d] = ((uint32_t)(ci + CELL_BIAS) << 16) | (uint32_t)cj;
       P.dx[d] = ox; P.dy[d] = oy;
-      P.ur[d] = (float)ur[k]; P.ut[d] = (float)ut[k]; P.up[d] = (float)up[k]; P.qw[d] = (float)q;
+      P.ur[d] = (float)vr; P.ut[d] = (float)vt; P.up[d] = (float)vp; P.qw[d] = (float)q;
       P.id[d] = id0 + k;
       qe = charge_exp(fabsf((float)q));
     }
