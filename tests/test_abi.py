@@ -80,3 +80,18 @@ def test_descriptor_validation_rejects_bad_values(bad):
     with pytest.raises(P.PicError) as e:
         P.Simulation(P.make_desc(**kw))
     assert e.value.code == P.PIC_EINVAL
+
+
+@pytest.mark.parametrize("lang,std", [("c", "c99"), ("c", "c11"), ("c++", "c++17")])
+def test_header_compiles_as_plain_c_and_cpp(lang, std):
+    """include/picsar.h is the boundary for C callers: it must compile on its
+    own, pedantically, without CUDA or torch headers."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    r = subprocess.run([cc, f"-std={std}", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", lang,
+                        os.path.join(ROOT, "include", "picsar.h")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
