@@ -206,7 +206,10 @@ int pic_get_particles(pic_ctx *c, int64_t *n, double *x1, double *x2, double *u_
  * static 4 MiB device array per GPU, which bounds the context to at most 2^28
  * particle slots (PIC_EINVAL beyond).  The first call on a device looks up the
  * array's address, so make it outside any stream capture; calls that overlap
- * on the GPU share the array and race.  Synchronises the context's stream. */
+ * on the GPU share the array and race.  Every output pointer must be memory
+ * of the context's device (or managed memory): anything else is refused with
+ * PIC_EINVAL before a kernel runs.  Synchronises the context's stream and,
+ * like the other getters, returns errors latched by earlier steps. */
 int pic_get_particles_noalloc(pic_ctx *c, int64_t *n, double *x1, double *x2, double *u_r,
                               double *u_th, double *u_ph, double *qw, int64_t *id);
 
@@ -245,10 +248,13 @@ int pic_get_profile(pic_ctx *c, double *ms6, int64_t *steps);
  * library's own kernels, all phases); *n receives the count. */
 int pic_get_launches(pic_ctx *c, int64_t *n);
 
-/* Advance n independent contexts by nsteps each, batched: each step launches
- * one kernel per phase for all members (grouped by precision), the whole
- * nsteps captured once as a CUDA graph and replayed.  All contexts must share
- * one stream and device.  (Batched ensemble of independent simulations.) */
+/* Advance n independent contexts by nsteps each, batched (an ensemble of
+ * independent simulations): the members' steps are captured into one CUDA
+ * graph, each member on its own parallel branch with its own kernels and
+ * grid, and the graph is launched once per block of steps; a member's tile
+ * sort (FP32) or compaction (FP64) runs between graphs when its own sort
+ * interval comes due.  All contexts must be on one device; each member's own
+ * stream waits for the graph.  Errors latched in any member are returned. */
 int pic_ensemble_step(pic_ctx *const *ctxs, int32_t n, int32_t nsteps);
 
 /* Pick the FP32 path's tile shape and sort interval by measurement: every

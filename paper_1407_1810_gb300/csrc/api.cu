@@ -448,6 +448,13 @@ void prof_drain(pic_ctx *c) {
 
 }  // namespace
 
+// errors latched on the device, then the status they give (for the other
+// translation units' entry points)
+int pic_latch_status(pic_ctx *c) {
+  int e = latch_errors(c);
+  return e ? e : status(c);
+}
+
 // =============================================================================
 // tile geometry and cell bins of the FP32 path for a tile shape (0: 16 x 16,
 // 1: 8 x 32, 2: 32 x 8 cells)

@@ -18,6 +18,7 @@
 // threads) race on it; every call overwrites the counts it uses, so nothing
 // has to be cleared between calls.
 #include <mutex>
+#include <string>
 
 #include "pic_internal.h"
 
@@ -127,6 +128,22 @@ __global__ void k_export_fp32_nc(pic::Parts32 P, int64_t n, const uint32_t *offs
   if (O.id) O.id[d] = P.id[k];
 }
 
+// A caller buffer must be memory of the context's device (or managed memory)
+// before any kernel writes into it: a host pointer, or one of another GPU,
+// would otherwise turn into an invalid device write instead of an error code.
+int check_out(const pic_ctx *c, const void *p, const char *name) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error the query left behind
+    return pic_fail(PIC_EINVAL, std::string("pic_get_particles_noalloc: ") + name + " is not device memory");
+  }
+  const bool ok = a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == c->device);
+  if (!ok)
+    return pic_fail(PIC_EINVAL,
+                    std::string("pic_get_particles_noalloc: ") + name + " is not memory of the context's device");
+  return PIC_OK;
+}
+
 }  // namespace
 
 extern "C" int pic_get_particles_noalloc(pic_ctx *c, int64_t *n, double *x1, double *x2, double *u_r,
@@ -134,6 +151,15 @@ extern "C" int pic_get_particles_noalloc(pic_ctx *c, int64_t *n, double *x1, dou
   if (!c || !n) return pic_fail(PIC_EINVAL, "null argument");
   if (!x1 || !x2 || !u_r || !u_th || !u_ph || !qw) return pic_fail(PIC_EINVAL, "null output array");
   if (*n < 0) return pic_fail(PIC_EINVAL, "negative output capacity");
+  {
+    const void *bufs[7] = {x1, x2, u_r, u_th, u_ph, qw, id};
+    const char *names[7] = {"x1", "x2", "u_r", "u_th", "u_ph", "qw", "id"};
+    for (int k = 0; k < 7; ++k) {
+      if (!bufs[k]) continue;  // only id may be NULL (checked above)
+      const int e = check_out(c, bufs[k], names[k]);
+      if (e) return e;
+    }
+  }
   const int64_t slots = c->n_used;
   if (slots > MAX_SLOTS)
     return pic_fail(PIC_EINVAL, "pic_get_particles_noalloc: the context holds more than 2^28 particle slots, "
@@ -161,5 +187,5 @@ extern "C" int pic_get_particles_noalloc(pic_ctx *c, int64_t *n, double *x1, dou
   const int64_t cap = *n;
   *n = total;
   if ((int64_t)total > cap) return pic_fail(PIC_EINVAL, "output buffers too small (*n now holds the live count)");
-  return PIC_OK;
+  return pic_latch_status(c);  // errors latched by earlier steps, as every getter reports them
 }

@@ -159,6 +159,7 @@ void reduce_particles32(pic_ctx *c);
 // error plumbing (api.cu)
 int pic_fail(int code, const std::string &msg);
 int pic_cuda_check(cudaError_t e, const char *what);
+int pic_latch_status(pic_ctx *c);  // read the device error word, return the context's status
 #define PIC_CUDA(call)                                          \
   do {                                                          \
     cudaError_t e_ = (call);                                    \

@@ -19,6 +19,9 @@ PIC_R_LINEAR, PIC_R_LOG = 0, 1
 PIC_TH_LINEAR, PIC_TH_EQUAL_AREA = 0, 1
 PIC_ABSORB_NONE, PIC_ABSORB_LINEAR, PIC_ABSORB_QUADRATIC = 0, 1, 2
 PIC_VAC_NONE, PIC_VAC_MONOPOLE, PIC_VAC_MONOPOLE_ROTATOR, PIC_VAC_UNIFORM_BZ, PIC_VAC_DIPOLE_COROT = 0, 1, 2, 3, 4
+PIC_VAC_DIPOLE_ROTATOR = 5
+PIC_INJECT_OFF, PIC_INJECT_FIXED, PIC_INJECT_VARIABLE = 0, 1, 2
+PIC_FIELDS_PLASMA, PIC_FIELDS_TOTAL = 0, 1
 PIC_FP64, PIC_FP32 = 0, 1
 PIC_VAY, PIC_BORIS = 0, 1
 PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
@@ -240,9 +243,19 @@ class Simulation:
 
     def particles_noalloc(self, out: dict):
         """Live particles into caller-owned device tensors (keys x1, x2, ur,
-        uth, uph, qw as float64, id as int64); returns the live count."""
+        uth, uph, qw as float64, id as int64 or None); returns the live count.
+        Every tensor must be a contiguous CUDA tensor: the C entry point
+        writes up to the smallest buffer's length into each of them."""
+        import torch
+
         keys = ("x1", "x2", "ur", "uth", "uph", "qw")
-        cap = min(out[k].numel() for k in keys)
+        bufs = [(k, out[k], torch.float64) for k in keys]
+        if out.get("id") is not None:
+            bufs.append(("id", out["id"], torch.int64))
+        for k, t, dt in bufs:
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.dtype == dt):
+                raise ValueError(f"particles_noalloc: {k} must be a contiguous CUDA tensor of {dt}")
+        cap = min(t.numel() for _, t, _ in bufs)
         n = C.c_int64(cap)
         ptrs = [C.c_void_p(out[k].data_ptr()) for k in keys]
         idp = C.c_void_p(out["id"].data_ptr()) if out.get("id") is not None else None

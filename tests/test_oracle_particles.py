@@ -317,17 +317,6 @@ def test_gauss_law_holds_with_filtered_charge(oracle_mod, n_filt, th_map):
     assert o.gauss_residual() < 1e-12
 
 
-def test_gauss_law_detects_a_wrong_filter_fold(oracle_mod):
-    """Control: filtering the charge with the odd fold breaks Gauss at the
-    axis, so the invariant above really tests the fold sign."""
-    o = _plasma_oracle(1)
-    o.step(10)
-    q = o.node_charge()
-    good = o.filter_pass(q, 0, +1)
-    bad = o.filter_pass(q, 0, -1)
-    assert np.max(np.abs(good - bad)) > 1e-6
-
-
 # --------------------------------------------------------------------------
 # injection and deletion
 # --------------------------------------------------------------------------

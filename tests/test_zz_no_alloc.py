@@ -38,13 +38,20 @@ def test_noalloc_export_matches_pic_get_particles(precision):
     # a hot plasma on a small grid: particles cross both conductors and are
     # deleted between the calls, so the context holds freed slots each time
     cfg = dict(configs.CONFIGS["monopole-64x64"], nr=24, nth=24, pairs_per_cell=3, T=1.0, precision=precision)
+    import torch
+
     s, _, _, _ = setup(cfg, sort_interval=1000)
     for call in range(2):
         s.step(15)
         live = s.live()
         out = _device_buffers(live)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         n = s.particles_noalloc(out)
+        free1 = torch.cuda.mem_get_info()[0]
         assert n == live
+        if call == 1:  # after the first call's one-time symbol lookup: no device memory taken
+            assert free1 == free0, (free0, free1)
         got = by_id({k: v[:n].cpu().numpy() for k, v in out.items()})
         ref = by_id(s.particles())  # the existing entry point (compacts the context)
         assert np.array_equal(got["id"], ref["id"]), call
@@ -62,3 +69,31 @@ def test_noalloc_reports_small_buffers():
     with pytest.raises(P.PicError) as e:
         s.particles_noalloc(out)
     assert e.value.code == P.PIC_EINVAL
+
+
+def test_noalloc_refuses_buffers_it_cannot_write():
+    """A host array, a CPU tensor or a tensor of the wrong type is refused
+    before any kernel runs (binding and C entry point)."""
+    import ctypes
+
+    import torch
+
+    from paper_1407_1810_gb300 import picsar as P
+
+    cfg = dict(configs.CONFIGS["monopole-64x64"], nr=16, nth=16, pairs_per_cell=2, precision="fp64")
+    s, _, _, _ = setup(cfg)
+    live = s.live()
+    out = _device_buffers(live)
+    for key, bad in (("x2", torch.empty(live, dtype=torch.float64)),
+                     ("id", torch.empty(live, dtype=torch.int32, device="cuda")),
+                     ("qw", torch.empty(2 * live, dtype=torch.float64, device="cuda")[::2])):
+        with pytest.raises(ValueError):
+            s.particles_noalloc(dict(out, **{key: bad}))
+    host = np.empty(live)
+    n = ctypes.c_int64(live)
+    ptrs = [ctypes.c_void_p(out[k].data_ptr()) for k in KEYS]
+    ptrs[3] = ctypes.c_void_p(host.ctypes.data)  # u_th on the host
+    rc = P.lib().pic_get_particles_noalloc(s.h, ctypes.byref(n), *ptrs, None)
+    assert rc == P.PIC_EINVAL
+    assert b"u_th" in P.lib().pic_last_error()
+    assert s.particles_noalloc(out) == live  # the context is unharmed
