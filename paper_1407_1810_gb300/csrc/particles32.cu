@@ -173,6 +173,73 @@ __device__ inline float clamp01(float v) { return fminf(fmaxf(v, 0.f), 1.f); }
 
 
 
+// ---- momentum in increments ----------------------------------------------
+// The FP32 step computes each change of the momentum -- the push, then the
+// rotation into the particle's new local frame -- as an increment du whose
+// rounding errors are relative to |du|, not to |u|: for a particle turning by
+// a small angle per step they are that much smaller, and the step adds to u
+// only the rounding of the one sum u + du that stores it.
+//
+// This arithmetic is written with explicitly rounded operations: the step is
+// inlined twice (shared-memory window and global memory), and a product the
+// compiler fused into an FMA in one copy but not in the other would make the
+// two paths differ in the last bit.
+
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// a x b - c x d (one component of a cross product)
+__device__ __forceinline__ float cross_(float a, float b, float c, float d) { return fma_(a, b, -mul_(c, d)); }
+__device__ __forceinline__ float dot3_(float a0, float a1, float a2, float b0, float b1, float b2) {
+  return fma_(a0, b0, fma_(a1, b1, mul_(a2, b2)));
+}
+
+// Vay (2008) push, Sec. 2, as u' - u: with a = u + (q dt/m) E + v x tau and
+// t = tau / gamma', u' = s (a + (a.t) t + a x t), s = 1 / (1 + t^2), i.e.
+// u' - a = s ((a.t) t + a x t - t^2 a).
+__device__ inline void vay_delta(float qmdt, const float E[3], const float B[3], const float u[3], float du[3]) {
+  const float h = mul_(0.5f, qmdt);
+  const float ig0 = rsqrt_(add_(1.f, dot3_(u[0], u[1], u[2], u[0], u[1], u[2])));
+  const float tau0 = mul_(h, B[0]), tau1 = mul_(h, B[1]), tau2 = mul_(h, B[2]);
+  const float v0 = mul_(u[0], ig0), v1 = mul_(u[1], ig0), v2 = mul_(u[2], ig0);
+  const float d0 = fma_(qmdt, E[0], cross_(v1, tau2, v2, tau1));
+  const float d1 = fma_(qmdt, E[1], cross_(v2, tau0, v0, tau2));
+  const float d2 = fma_(qmdt, E[2], cross_(v0, tau1, v1, tau0));
+  const float a0 = add_(u[0], d0), a1 = add_(u[1], d1), a2 = add_(u[2], d2);
+  const float tau2s = dot3_(tau0, tau1, tau2, tau0, tau1, tau2);
+  const float ustar = dot3_(a0, a1, a2, tau0, tau1, tau2);
+  const float sigma = sub_(add_(1.f, dot3_(a0, a1, a2, a0, a1, a2)), tau2s);
+  const float disc = fma_(sigma, sigma, mul_(4.f, fma_(ustar, ustar, tau2s)));
+  const float g2 = mul_(0.5f, add_(sigma, sqrtf(disc)));
+  const float ig = rsqrt_(g2);
+  const float t0 = mul_(tau0, ig), t1 = mul_(tau1, ig), t2 = mul_(tau2, ig);
+  const float tt = dot3_(t0, t1, t2, t0, t1, t2);
+  const float sc = rcp_(add_(1.f, tt));
+  const float at = dot3_(a0, a1, a2, t0, t1, t2);
+  du[0] = fma_(sc, sub_(fma_(at, t0, cross_(a1, t2, a2, t1)), mul_(tt, a0)), d0);
+  du[1] = fma_(sc, sub_(fma_(at, t1, cross_(a2, t0, a0, t2)), mul_(tt, a1)), d1);
+  du[2] = fma_(sc, sub_(fma_(at, t2, cross_(a0, t1, a1, t0)), mul_(tt, a2)), d2);
+}
+
+// Boris (1970) push, Sec. 2, as u' - u: half electric kick h E, rotation
+// u- -> u+ = u- + (u- + u- x t) x s, half kick; u' - u = 2 h E + (u- + u- x t) x s.
+__device__ inline void boris_delta(float qmdt, const float E[3], const float B[3], const float u[3], float du[3]) {
+  const float h = mul_(0.5f, qmdt);
+  const float he0 = mul_(h, E[0]), he1 = mul_(h, E[1]), he2 = mul_(h, E[2]);
+  const float um0 = add_(u[0], he0), um1 = add_(u[1], he1), um2 = add_(u[2], he2);
+  const float ig = rsqrt_(add_(1.f, dot3_(um0, um1, um2, um0, um1, um2)));
+  const float hi = mul_(h, ig);
+  const float t0 = mul_(hi, B[0]), t1 = mul_(hi, B[1]), t2 = mul_(hi, B[2]);
+  const float f = mul_(2.f, rcp_(add_(1.f, dot3_(t0, t1, t2, t0, t1, t2))));
+  const float p0 = add_(um0, cross_(um1, t2, um2, t1)), p1 = add_(um1, cross_(um2, t0, um0, t2)),
+              p2 = add_(um2, cross_(um0, t1, um1, t0));
+  const float s0 = mul_(f, t0), s1 = mul_(f, t1), s2 = mul_(f, t2);
+  du[0] = fma_(2.f, he0, cross_(p1, s2, p2, s1));
+  du[1] = fma_(2.f, he1, cross_(p2, s0, p0, s2));
+  du[2] = fma_(2.f, he2, cross_(p0, s1, p1, s0));
+}
+
 // Specialisations of the step: the grid maps, pusher and analytic field kind
 // fixed at compile time for the two common configurations, so their branches
 // fold away (8 % faster than reading them from the arguments), on grids fine
@@ -215,6 +282,7 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
     ct = -ct;
   }
   // ---- gather + push (ballistic inside the outer conductor) -----------------
+  float du[3] = {0.f, 0.f, 0.f};  // momentum change of the step: push, then frame rotation
   if (ci < A.nr) {
     float E[3], B[3];
     const Vac<float> V{F.vacuum, A.b0, A.r_min, A.omega_t};
@@ -234,15 +302,18 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
       B[1] += bilin(w, BTH, ih, cj, ah, dy);
       B[2] += bilin(w, BPH, ih, jh, ah, bh);
     }
-    float u[3] = {ur, ut, up};
+    const float u[3] = {ur, ut, up};
     // local (r, th, ph) is a right-handed orthonormal frame: the Cartesian
     // push formulas apply to its components unchanged
-    push<float>(F.pusher, qw > 0.f ? A.qmdt : -A.qmdt, E, B, u);
-    ur = u[0]; ut = u[1]; up = u[2];
+    const float qmdt = qw > 0.f ? A.qmdt : -A.qmdt;
+    if (F.pusher == PIC_BORIS) boris_delta(qmdt, E, B, u, du);
+    else vay_delta(qmdt, E, B, u, du);
   }
+  // u^{n+1/2} in FP32, for the move
+  const float pr = add_(ur, du[0]), pt = add_(ut, du[1]), pp = add_(up, du[2]);
   // ---- move in the local frame (Sec. 3.3) -----------------------------------
-  const float ig = rsqrt_(1.f + ur * ur + ut * ut + up * up);
-  const float vr = ur * ig, vt = ut * ig, vp = up * ig;
+  const float ig = rsqrt_(1.f + pr * pr + pt * pt + pp * pp);
+  const float vr = pr * ig, vt = pt * ig, vp = pp * ig;
   const float Dr = fmaf(vr, A.dt, vr * A.dt_lo), Dt = fmaf(vt, A.dt, vt * A.dt_lo), Dp = fmaf(vp, A.dt, vp * A.dt_lo);
   const float ir = rcp_(r);
   const float a = Dr * ir, b = Dt * ir, c = Dp * ir;
@@ -254,12 +325,19 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   const float Rn = sqrtf(Px * Px + Dp * Dp);
   const float kap = Px >= 0.f ? (Rn + Px > 0.f ? Dp * Dp * rcp_(Rn + Px) : 0.f) : Rn - Px;  // R' - Px
   const float dth = series ? atan_series(q + ct * kap, p + st * kap) : atan2_small(q + ct * kap, p + st * kap);
-  float D2;
-  if (F.th_ea) {
+  // sin(dth) and cos(dth) - 1 of the meridional rotation, from the half angle
+  // (or, for the small angles of the specialised grids, short series)
+  float D2, sd, cd1;
+  if (F.th_ea || !series) {
     float sh, ch;
     sincosf(0.5f * dth, &sh, &ch);
-    D2 = A.nth_f * (st * ch + ct * sh) * sh;
-  } else {
+    sd = mul_(2.f, mul_(sh, ch));
+    cd1 = mul_(-2.f, mul_(sh, sh));
+    D2 = F.th_ea ? A.nth_f * (st * ch + ct * sh) * sh : fmaf(dth, A.k2_hi, dth * A.k2_lo);
+  } else {  // sin x = x (1 - x^2/6 + x^4/120), cos x - 1 = -x^2/2 (1 - x^2/12 + x^4/360)
+    const float d2 = mul_(dth, dth);
+    sd = mul_(dth, fma_(-d2, fma_(-d2, 0.008333334f, 0.16666667f), 1.f));
+    cd1 = mul_(mul_(-0.5f, d2), fma_(-d2, fma_(-d2, 0.0027777778f, 0.083333336f), 1.f));
     D2 = fmaf(dth, A.k2_hi, dth * A.k2_lo);
   }
   // new cell and offsets (carries are exact integers)
@@ -271,14 +349,23 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   int ncj = cj + ky;
   if (ncj < 0) { ncj = 0; ky = -cj; ny = 0.f; }                       // rounding below the axis
   if (ncj > A.nth - 1) { ncj = A.nth - 1; ky = ncj - cj; ny = 1.f; }   // rounding past the south axis
-  // momentum: to Cartesian at phi = 0, rotate back by -phi', to the new frame
-  const float ux = ur * st + ut * ct, uz = ur * ct - ut * st;
-  const float iRn = Rn > 0.f ? rcp_(Rn) : 0.f;
-  const float cph = Rn > 0.f ? Px * iRn : 1.f, sph = Dp * iRn;
-  const float uxx = cph * ux + sph * up, uyy = -sph * ux + cph * up;
-  const float irn = rsqrtf(fmaxf(Rn * Rn + Pz * Pz, 1e-30f));
-  const float stn = Rn * irn, ctn = Pz * irn;
-  const float nur = uxx * stn + uz * ctn, nut = uxx * ctn - uz * stn, nup = uyy;
+  // momentum into the new local frame, as an increment: Cartesian at phi = 0
+  // (x along R), rotated back about z by -phi' (cos phi' - 1 = -kap / R',
+  // sin phi' = Dp / R'), then into (r', th') at th' = th + dth:
+  //   u_r' = u_r cos dth + u_th sin dth + dx st',  u_th' = -u_r sin dth + u_th cos dth + dx ct',
+  //   u_ph' = u_ph + dy,  with (dx, dy) the change of (u_x, u_ph) under the azimuthal rotation
+  {
+    const float ux = fma_(pr, st, mul_(pt, ct));
+    const float iRn = Rn > 0.f ? rcp_(Rn) : 0.f;
+    const float cm1 = mul_(-kap, iRn), sph = mul_(Dp, iRn);
+    const float dxr = fma_(ux, cm1, mul_(sph, pp)), dyr = fma_(pp, cm1, -mul_(sph, ux));
+    const float irn = rsqrtf(fmaxf(fma_(Rn, Rn, mul_(Pz, Pz)), 1e-30f));
+    const float stn = mul_(Rn, irn), ctn = mul_(Pz, irn);
+    du[0] = add_(du[0], fma_(pr, cd1, fma_(pt, sd, mul_(dxr, stn))));
+    du[1] = add_(du[1], fma_(pt, cd1, fma_(-pr, sd, mul_(dxr, ctn))));
+    du[2] = add_(du[2], dyr);
+  }
+  const float nur = add_(ur, du[0]), nut = add_(ut, du[1]), nup = add_(up, du[2]);
   if (!(isfinite(nx) && isfinite(ny) && isfinite(nur) && isfinite(nut) && isfinite(nup)) || kx < -1 || kx > 1 ||
       ky < -1 || ky > 1) {
     atomicOr(A.err, (isfinite(nx) && isfinite(nur)) ? ERR_COURANT : ERR_NAN);
@@ -359,10 +446,12 @@ __device__ inline bool step32_global(const Args32 &A, float fs, uint32_t &cell, 
 template <int SPEC, class SW>
 __device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, const SW &sw,
                                int wi_lo, int wi_hi, int wj_lo, int wj_hi, int &dead) {
+  // every load first: the free-slot test would otherwise put a second memory
+  // round trip behind the first
   const float qw = P.qw[k];
-  if (qw == 0.f) return;
   uint32_t cell = P.cell[k];
   float dx = P.dx[k], dy = P.dy[k], ur = P.ur[k], ut = P.ut[k], up = P.up[k];
+  if (qw == 0.f) return;
   const int ci = (int)(cell >> 16) - CELL_BIAS, cj = (int)(cell & 0xffffu);
   bool alive;
   if (win && ci >= wi_lo && ci < wi_hi && cj >= wj_lo && cj < wj_hi)
@@ -424,7 +513,7 @@ __device__ inline bool window_wait(uint64_t *bar, long long limit) {
 }
 
 template <int TI, int TJ, int SPEC>
-__global__ void __launch_bounds__(NT) k_tiles32(Args32 A, Parts32 P, const __grid_constant__ TileMaps maps) {
+__global__ void __launch_bounds__(NT, 4) k_tiles32(Args32 A, Parts32 P, const __grid_constant__ TileMaps maps) {
   using BX_ = Box<TI, TJ>;
   constexpr int WI = BX_::WI, WJ = BX_::WJ, WN = BX_::WN, WB = BX_::WB, SLOT = BX_::SLOT;
   __shared__ __align__(128) float sbuf[BX_::SF + BX_::U];
