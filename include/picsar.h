@@ -269,6 +269,51 @@ int pic_autotune(pic_ctx *c, int32_t trial_steps, int32_t *sort_interval, int32_
 /* Release every device buffer of the context.  NULL is allowed. */
 int pic_destroy(pic_ctx *c);
 
+/* ---- one simulation split into radial slabs ---------------------------------
+ * The grid decomposition the paper parallelises over MPI (Sec. 2, Overview;
+ * the scaling discussion of Sec. 6): the nr rows are cut into nslabs
+ * contiguous radial slabs, each held by a context of its own on the current
+ * device.  Every step exchanges between neighbouring slabs: the field rows
+ * next to each interface after each Yee sub-step (the gather and the curl read
+ * one row across it), the charge flux the particles deposit into the
+ * neighbour's rows (summed back into the owner before the N_filt filter
+ * passes, which then read N_filt + 2 ghost rows), and the particles that
+ * crossed the interface (at most one cell per step, by the Courant limit).
+ * Each exchange is a contiguous block copied on the stream, the message a
+ * point-to-point send would carry between GPUs.  The results are those of one
+ * context over the whole grid (pic_init_grid) up to the order of the FP64
+ * current sums.  FP64 path only (precision must be PIC_FP64). */
+typedef struct pic_slabs pic_slabs;
+
+/* d: the whole grid's descriptor (as for pic_init_grid; dt <= 0 takes the
+ * whole grid's Courant step).  rows: nslabs + 1 slab boundaries in global
+ * rows, 0 = rows[0] < ... < rows[nslabs] = nr, or NULL for equal slabs.  Every
+ * slab needs at least 2 (n_filt + 2) + 2 rows, and the lossy layer must lie in
+ * the last slab.  Errors: PIC_EINVAL (bad descriptor or rows), PIC_ENOMEM,
+ * PIC_ECUDA. */
+int pic_slabs_init(pic_slabs **out, const pic_desc *d, int32_t nslabs, const int32_t *rows, void *stream);
+
+/* Append n particles in global grid coordinates (as pic_load_particles; ids
+ * are consecutive over the whole load); each goes to the slab of its row. */
+int pic_slabs_load_particles(pic_slabs *g, int64_t n, const double *x1, const double *x2, const double *u_r,
+                             const double *u_th, const double *u_ph, const double *qw, int32_t mem);
+
+/* nsteps full time steps of the whole grid (synchronises once per step to
+ * hand over the migrating particles).  Returns errors latched in any slab. */
+int pic_slabs_step(pic_slabs *g, int32_t nsteps);
+
+/* The whole grid's fields, fluxes, particles (global x1) and moments, in the
+ * layouts of pic_get_fields, pic_get_flux, pic_get_particles and
+ * pic_get_moments, assembled from the rows each slab owns. */
+int pic_slabs_get_fields(pic_slabs *g, int32_t which, double *out6, int64_t *n, int32_t mem);
+int pic_slabs_get_flux(pic_slabs *g, double *out3, int64_t *n, int32_t mem);
+int pic_slabs_get_particles(pic_slabs *g, int64_t *n, double *x1, double *x2, double *u_r, double *u_th,
+                            double *u_ph, double *qw, int64_t *id, int32_t mem);
+int pic_slabs_get_moments(pic_slabs *g, pic_moments *out);
+
+/* Release every slab.  NULL is allowed. */
+int pic_slabs_destroy(pic_slabs *g);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *pic_last_error(void);
 

@@ -41,10 +41,11 @@ double h_fth(const pic_desc &d, double x) {
   return d.th_map == PIC_TH_EQUAL_AREA ? std::acos(1.0 - 2.0 * x / d.nth) : M_PI * x / d.nth;
 }
 
-double sigma_star(const pic_desc &d, double rho) {
+// rho: global radial grid coordinate; nr: the global row count
+double sigma_star(const pic_desc &d, double rho, int nr) {
   const int L = d.absorb_cells;
   if (d.absorb_profile == PIC_ABSORB_NONE || L <= 0) return 0.0;
-  double x = rho - (d.nr - L);
+  double x = rho - (nr - L);
   if (x <= 0.0) return 0.0;
   double u = x / L;
   if (d.absorb_profile == PIC_ABSORB_QUADRATIC) return (d.absorb_sigma_max > 0 ? d.absorb_sigma_max : 3.0 / L) * u * u;
@@ -104,6 +105,7 @@ int build_metric(pic_ctx *c) {
   const pic_desc &d = c->d;
   Grid &G = c->G;
   const int NRr = d.nr + 2 * G.PI + 1, NC = G.LD;
+  const int nrg = G.nr_glob;  // rows of the whole grid (a slab's tables hold its global rows)
   // row tables 0-12 (geometry) and 13-20 (update coefficients); column
   // tables 0-11 and 17 (geometry) and 12-16 (update coefficients)
   const int nrow = 21, ncol = 18;
@@ -114,7 +116,7 @@ int build_metric(pic_ctx *c) {
   const double dxi = G.dxi;
   auto fr = [&](double x) { return h_fr(d, dxi, x); };
   for (int ii = 0; ii < NRr; ++ii) {
-    const int i = ii - G.PI;
+    const int i = ii - G.PI + G.i0;  // global row
     double rn = fr(i), rn1 = fr(i + 1), rh = fr(i + 0.5), rhm = fr(i - 0.5);
     row(0)[ii] = rn;
     row(1)[ii] = rh;
@@ -125,8 +127,8 @@ int build_metric(pic_ctx *c) {
     row(6)[ii] = 1.0 / (2.0 * M_PI * rh * rh);
     row(7)[ii] = 2.0 / (rh * rh - rhm * rhm);
     row(8)[ii] = rh - rhm;
-    row(9)[ii] = 1.0 - sigma_star(d, i);
-    row(10)[ii] = 1.0 - sigma_star(d, i + 0.5);
+    row(9)[ii] = 1.0 - sigma_star(d, i, nrg);
+    row(10)[ii] = 1.0 - sigma_star(d, i + 0.5, nrg);
     const double id2n = 2.0 / (rn1 * rn1 - rn * rn), id2h = 2.0 / (rh * rh - rhm * rhm);
     row(13)[ii] = hh / rn;
     row(14)[ii] = hh * id2n * rn;
@@ -136,10 +138,10 @@ int build_metric(pic_ctx *c) {
     row(18)[ii] = dt * id2h * rhm;
     row(19)[ii] = dt * id2h * rh;
     row(20)[ii] = dt * id2h * (rh - rhm);
-    if (i >= 0 && i <= d.nr) {
-      double a = std::fmax(i - 0.5, 0.0), b = std::fmin(i + 0.5, (double)d.nr);
+    if (i >= 0 && i <= nrg) {
+      double a = std::fmax(i - 0.5, 0.0), b = std::fmin(i + 0.5, (double)nrg);
       row(11)[ii] = 2.0 * M_PI / 3.0 * (std::pow(fr(b), 3) - std::pow(fr(a), 3));
-      row(12)[ii] = i < d.nr ? 2.0 * M_PI / 3.0 * (std::pow(rn1, 3) - std::pow(rn, 3)) : 0.0;
+      row(12)[ii] = i < nrg ? 2.0 * M_PI / 3.0 * (std::pow(rn1, 3) - std::pow(rn, 3)) : 0.0;
     }
   }
   auto th = [&](double x) { return h_fth(d, x); };
@@ -351,7 +353,7 @@ __global__ void k_load64(Grid G, Parts64 P, int64_t base, int64_t n, const doubl
   // all six reads first, then the checks (without short-circuit): from
   // pinned host memory each dependent read would cost a host-link round trip
   const double a = x1[k], b = x2[k], q = qw[k], vr = ur[k], vt = ut[k], vp = up[k];
-  const bool ok = (a >= -(double)(G.n_filt + 1)) & (a < (double)(G.nr + G.n_filt + 1)) & (b >= 0.0) & (b <= G.nth) &
+  const bool ok = (a >= -(double)(G.n_filt + 1)) & (a < (double)(G.nr_glob + G.n_filt + 1)) & (b >= 0.0) & (b <= G.nth) &
                   (q != 0.0) & isfinite(q) & isfinite(vr) & isfinite(vt) & isfinite(vp);
   const int64_t d = base + k;
   if (!ok) { atomicOr(err, ERR_RANGE); P.qw[d] = 0.0; return; }
@@ -455,6 +457,14 @@ int pic_latch_status(pic_ctx *c) {
   return e ? e : status(c);
 }
 
+int pic_grow_particles(pic_ctx *c, int64_t new_cap) { return grow_parts(c, new_cap); }
+int pic_reserve(pic_ctx *c, int64_t need) {
+  if (c->cap == 0) return alloc_parts(c, std::max<int64_t>(need, 1024));
+  if (need > c->cap) return grow_parts(c, need * 3 / 2 + 1024);
+  return PIC_OK;
+}
+int pic_compact(pic_ctx *c) { return compact(c); }
+
 // =============================================================================
 // tile geometry and cell bins of the FP32 path for a tile shape (0: 16 x 16,
 // 1: 8 x 32, 2: 32 x 8 cells)
@@ -476,25 +486,31 @@ static int alloc_bins(pic_ctx *c, int shape) {
   return PIC_OK;
 }
 
-extern "C" int pic_init_grid(pic_ctx **out, const pic_desc *dd, void *stream) {
-  if (!out || !dd) return pic_fail(PIC_EINVAL, "null argument");
+int pic_desc_defaults(pic_desc *d) {
+  if (d->q_over_m == 0.0) d->q_over_m = 1.0;
+  if (d->pairs_per_cell == 0) d->pairs_per_cell = 2;
+  if (d->sort_interval <= 0) d->sort_interval = 20;
+  return check_desc(*d);
+}
+
+// A context over rows [i0, i0 + d.nr) of a grid of nr_glob rows (the whole
+// grid: i0 = 0, nr_glob = d.nr); d has been checked by pic_desc_defaults
+// against the whole grid.
+int pic_create_context(pic_ctx **out, const pic_desc &d, void *stream, int i0, int nr_glob, int open_lo,
+                       int open_hi) {
   *out = nullptr;
-  pic_desc d = *dd;
-  if (d.q_over_m == 0.0) d.q_over_m = 1.0;
-  if (d.pairs_per_cell == 0) d.pairs_per_cell = 2;
-  if (d.sort_interval <= 0) d.sort_interval = 20;
-  int e = check_desc(d);
-  if (e) return e;
+  int e;
   pic_ctx *c = new pic_ctx();
   c->d = d;
   c->stream = (cudaStream_t)stream;
   cudaGetDevice(&c->device);
   Grid &G = c->G;
   G.nr = d.nr; G.nth = d.nth; G.n_filt = d.n_filt; G.g = d.n_filt + 2;
+  G.i0 = i0; G.nr_glob = nr_glob; G.open_lo = open_lo; G.open_hi = open_hi;
   G.PI = G.g + PAD; G.PJ = PAD;
   G.LD = ((d.nth + 1 + 2 * G.PJ) + 7) / 8 * 8;
   G.r_map = d.r_map; G.th_map = d.th_map; G.r_min = d.r_min;
-  G.dxi = d.r_map == PIC_R_LOG ? std::log(d.r_max / d.r_min) / d.nr : (d.r_max - d.r_min) / d.nr;
+  G.dxi = d.r_map == PIC_R_LOG ? std::log(d.r_max / d.r_min) / nr_glob : (d.r_max - d.r_min) / nr_glob;
   G.dt = d.dt > 0.0 ? d.dt : courant_dt(d, G.dxi);
   if (!(G.dt > 0.0)) { delete c; return pic_fail(PIC_EINVAL, "dt must be > 0 (set dt or courant)"); }
   G.qm = d.q_over_m; G.vacuum = d.vacuum; G.pusher = d.pusher;
@@ -551,6 +567,15 @@ extern "C" int pic_init_grid(pic_ctx **out, const pic_desc *dd, void *stream) {
   PIC_CUDA(cudaDeviceSynchronize());
   *out = c;
   return PIC_OK;
+}
+
+extern "C" int pic_init_grid(pic_ctx **out, const pic_desc *dd, void *stream) {
+  if (!out || !dd) return pic_fail(PIC_EINVAL, "null argument");
+  *out = nullptr;
+  pic_desc d = *dd;
+  int e = pic_desc_defaults(&d);
+  if (e) return e;
+  return pic_create_context(out, d, stream, 0, d.nr, 0, 0);
 }
 
 // Device-visible addresses of six host arrays that are page-locked (pinned):

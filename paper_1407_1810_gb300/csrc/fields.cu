@@ -59,7 +59,8 @@ __global__ void k_e_full(Grid G, double *__restrict__ Er, double *__restrict__ E
   const size_t o = gidx(G, i, j);
   if (i < G.nr)  // E_r at (i+1/2, j)
     Er[o] += m.eR[ri] * (Bp[o] * m.cE1[cj] - Bp[o - 1] * m.cE2[cj]) - Fr[o] * (m.inv_area_h[ri] * m.inv_dcos_tb[cj]);
-  if (i >= 1 && i < G.nr) {
+  // E_th, E_ph stay 0 on a conductor; a slab's open side is an interior row
+  if ((i >= 1 || G.open_lo) && (i < G.nr || G.open_hi)) {
     const double t0 = m.eT0[ri], t1 = m.eT1[ri], id2 = m.inv_dr2_h[ri];
     if (j < G.nth)  // E_th at (i, j+1/2)
       Et[o] += (t0 * Bp[o - G.LD] - t1 * Bp[o]) - Ft[o] * (m.cF[cj] * id2);
@@ -263,9 +264,9 @@ __device__ inline double warp_sum(double v) {
 // (i, j) (caps close at the axis); d = G - Qbar.  snapshot: store d; else
 // reduce max |d - d_0| and max |Q| over interior nodes 1 <= i <= imax.
 __global__ void k_gauss(Grid G, const double *__restrict__ Er, const double *__restrict__ Et,
-                        const double *__restrict__ Qf, const double *__restrict__ Qa, double *snap, int imax,
+                        const double *__restrict__ Qf, const double *__restrict__ Qa, double *snap, int ilo, int imax,
                         int snapshot, long long *gmax, long long *qmax) {
-  const int j = blockIdx.x * BX + threadIdx.x, i = 1 + blockIdx.y * BY + threadIdx.y;
+  const int j = blockIdx.x * BX + threadIdx.x, i = ilo + blockIdx.y * BY + threadIdx.y;
   double v = 0.0, qa = 0.0;
   if (i <= imax && j <= G.nth) {
     const Metric &m = G.m;
@@ -288,11 +289,12 @@ __global__ void k_gauss(Grid G, const double *__restrict__ Er, const double *__r
   }
 }
 
+// rows 0..imax (a slab leaves its open outer interface row to the neighbour)
 __global__ void k_field_energy(Grid G, const double *f0, const double *f1, const double *f2, const double *f3,
-                               const double *f4, const double *f5, double *acc) {
+                               const double *f4, const double *f5, int imax, double *acc) {
   const int j = blockIdx.x * BX + threadIdx.x, i = blockIdx.y * BY + threadIdx.y;
   double e = 0.0;
-  if (i <= G.nr && j <= G.nth) {
+  if (i <= imax && j <= G.nth) {
     const Metric &m = G.m;
     const int ri = i + G.PI, cj = j + G.PJ;
     const size_t o = gidx(G, i, j);
@@ -438,6 +440,20 @@ void luminosity(pic_ctx *c, double t, double *L) {
   ++c->launches, k_luminosity<<<G.nr + 1, 256, 0, c->stream>>>(G, c->f[ETH], c->f[EPH], c->f[BTH], c->f[BPH], t, L);
 }
 
+void gauss_rows(pic_ctx *c, int ilo, int imax, bool snapshot) {
+  const Grid &G = c->G;
+  if (imax < ilo) return;
+  ++c->launches, k_gauss<<<grid2(imax - ilo + 1, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(
+      G, c->f[ER], c->f[ETH], c->Q, c->Qa, c->gsnap, ilo, imax, snapshot ? 1 : 0, c->d_cnt + CNT_GMAX,
+      c->d_cnt + CNT_QMAX);
+}
+
+void field_energy_rows(pic_ctx *c, int imax) {
+  const Grid &G = c->G;
+  ++c->launches, k_field_energy<<<grid2(G.nr + 1, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(
+      G, c->f[0], c->f[1], c->f[2], c->f[3], c->f[4], c->f[5], imax, c->d_acc + ACC_FIELD);
+}
+
 void moments(pic_ctx *c, bool snapshot, pic_moments *out) {
   const Grid &G = c->G;
   cudaMemsetAsync(c->Q, 0, c->grid_elems * sizeof(double), c->stream);
@@ -450,13 +466,13 @@ void moments(pic_ctx *c, bool snapshot, pic_moments *out) {
   cudaMemsetAsync(c->d_cnt + CNT_GMAX, 0, 2 * sizeof(long long), c->stream);
   if (imax >= 1)
     ++c->launches, k_gauss<<<grid2(imax, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(G, c->f[ER], c->f[ETH], c->Q, c->Qa, c->gsnap,
-                                                                    imax, snapshot ? 1 : 0, c->d_cnt + CNT_GMAX,
+                                                                    1, imax, snapshot ? 1 : 0, c->d_cnt + CNT_GMAX,
                                                                     c->d_cnt + CNT_QMAX);
   if (snapshot) { c->have_snap = true; return; }
   cudaMemsetAsync(c->d_acc, 0, ACC_N * sizeof(double), c->stream);
   cudaMemsetAsync(c->d_cnt + CNT_LIVE, 0, sizeof(long long), c->stream);
   ++c->launches, k_field_energy<<<grid2(G.nr + 1, G.nth + 1), dim3(BX, BY), 0, c->stream>>>(
-      G, c->f[0], c->f[1], c->f[2], c->f[3], c->f[4], c->f[5], c->d_acc + ACC_FIELD);
+      G, c->f[0], c->f[1], c->f[2], c->f[3], c->f[4], c->f[5], G.nr, c->d_acc + ACC_FIELD);
   if (c->d.precision == PIC_FP32) reduce_particles32(c);
   else reduce_particles64(c);
   long long cnt[CNT_N];

@@ -15,7 +15,8 @@ __device__ inline int cell_j(const Grid &G, double x2) {
 }
 
 // bilinear interpolation in grid coordinates from a component's staggered
-// lattice (reading of the gather; the axis and conductor ghosts are stored)
+// lattice (reading of the gather; the axis and conductor ghosts are stored);
+// x1 is the slab's local coordinate (global - i0, an exact difference)
 __device__ inline double interp64(const Grid &G, const double *__restrict__ a, double x1, double x2, int si, int sj) {
   const double p1 = x1 - 0.5 * si, p2 = x2 - 0.5 * sj;
   const double fi = floor(p1), fj = floor(p2);
@@ -81,17 +82,19 @@ __global__ void __launch_bounds__(256) k_particles64(Grid G, Parts64 P, int64_t 
   const double ur = P.ur[k], ut = P.ut[k], up = P.up[k];
   // local spherical basis at phi = 0 -> Cartesian (x = R, y = phi, z)
   double u[3] = {ur * st + ut * ct, up, ur * ct - ut * st};
-  if (x1 < G.nr) {  // inside the outer conductor particles fly ballistically
+  // physical tests in global coordinates, array indices in the slab's rows
+  const double xl = x1 - (double)G.i0;
+  if (x1 < G.nr_glob) {  // inside the outer conductor particles fly ballistically
     double Es[3], Bs[3];
     const Vac<double> V{G.vacuum, G.b0, G.r_min, omega_at(G.omega, G.t_spin, t)};
     vacuum_field<double>(V, r, st, ct, x1 < 0.0, Es, Bs);
     if (x1 >= 0.0) {  // no plasma field inside the inner conductor
-      Es[0] += interp64(G, F.f[ER], x1, x2, 1, 0);
-      Es[1] += interp64(G, F.f[ETH], x1, x2, 0, 1);
-      Es[2] += interp64(G, F.f[EPH], x1, x2, 0, 0);
-      Bs[0] += interp64(G, F.f[BR], x1, x2, 0, 1);
-      Bs[1] += interp64(G, F.f[BTH], x1, x2, 1, 0);
-      Bs[2] += interp64(G, F.f[BPH], x1, x2, 1, 1);
+      Es[0] += interp64(G, F.f[ER], xl, x2, 1, 0);
+      Es[1] += interp64(G, F.f[ETH], xl, x2, 0, 1);
+      Es[2] += interp64(G, F.f[EPH], xl, x2, 0, 0);
+      Bs[0] += interp64(G, F.f[BR], xl, x2, 0, 1);
+      Bs[1] += interp64(G, F.f[BTH], xl, x2, 1, 0);
+      Bs[2] += interp64(G, F.f[BPH], xl, x2, 1, 1);
     }
     const double E[3] = {Es[0] * st + Es[1] * ct, Es[2], Es[0] * ct - Es[1] * st};
     const double B[3] = {Bs[0] * st + Bs[1] * ct, Bs[2], Bs[0] * ct - Bs[1] * st};
@@ -112,15 +115,16 @@ __global__ void __launch_bounds__(256) k_particles64(Grid G, Parts64 P, int64_t 
     return;
   }
   const int ia = (int)floor(x1);
-  const double lo = -(double)G.g, hi = (double)(G.nr + G.g);
+  const double lo = -(double)G.g, hi = (double)(G.nr_glob + G.g);
   if (!(nx1 >= lo && nx1 < hi) || abs((int)floor(nx1) - ia) > 1 || abs(cell_j(G, nx2) - cell_j(G, x2)) > 1) {
     set_err(err, ERR_COURANT);
   } else {
+    const double nxl = nx1 - (double)G.i0;
     const int ib = (int)floor(nx1);
-    vb_path64(G, D.Fr, D.Ft, qw, x1, x2, nx1, nx2, ia, ib);
+    vb_path64(G, D.Fr, D.Ft, qw, xl, x2, nxl, nx2, ia - G.i0, ib - G.i0);
     // azimuthal flux: charge crossing the meridional half-plane, area weights
     // at the midpoint of the grid-coordinate path (reading of the paper)
-    const double m1 = 0.5 * (x1 + nx1), m2 = 0.5 * (x2 + nx2);
+    const double m1 = 0.5 * (xl + nxl), m2 = 0.5 * (x2 + nx2);
     const double fi = floor(m1), fj = floor(m2), w1 = m1 - fi, w2 = m2 - fj;
     const double v = qw * phi * (0.5 / PI_D);
     const size_t o = gidx(G, (int)fi, (int)fj);
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(256) k_particles64(Grid G, Parts64 P, int64_t 
   }
   // removal once the filtered shape lies inside a conductor (Sec. 3.4.2)
   const int ci = (int)floor(nx1);
-  if (ci < -(G.n_filt + 1) || ci >= G.nr + G.n_filt + 1) {
+  if (ci < -(G.n_filt + 1) || ci >= G.nr_glob + G.n_filt + 1) {
     P.qw[k] = 0.0;
     add_ll(cnt + CNT_DELETED, 1LL);
     return;
@@ -202,7 +206,7 @@ __global__ void k_charge64(Grid G, const double *__restrict__ x1, const double *
   if (k >= n) return;
   const double q = qw[k];
   if (q == 0.0) return;
-  const double a = x1[k], b = x2[k], fi = floor(a), fj = floor(b), w1 = a - fi, w2 = b - fj;
+  const double a = x1[k] - (double)G.i0, b = x2[k], fi = floor(a), fj = floor(b), w1 = a - fi, w2 = b - fj;
   const size_t o = gidx(G, (int)fi, (int)fj);
   const double c00 = (1 - w1) * (1 - w2), c10 = w1 * (1 - w2), c01 = (1 - w1) * w2, c11 = w1 * w2;
   atomicAdd(Q + o, q * c00); atomicAdd(Q + o + G.LD, q * c10);

@@ -63,6 +63,12 @@ struct Metric {
 
 struct Grid {
   int nr, nth, g, n_filt;
+  // radial slab of a larger grid (Sec. 2: the grid split among processes):
+  // local row i is global row i + i0 of a grid of nr_glob rows; particles keep
+  // global coordinates, arrays and the row loops use local rows.  An open
+  // side is an interface to a neighbouring slab, not a conductor.  A whole
+  // grid has i0 = 0, nr_glob = nr and both sides closed.
+  int i0, nr_glob, open_lo, open_hi;
   int PI, PJ, LD;
   int r_map, th_map;
   double r_min, dxi;  // log: ln(r_max/r_min)/nr ; linear: (r_max - r_min)/nr

@@ -142,6 +142,10 @@ void inject(pic_ctx *c, double t);     // surface pairs into slots [n_used, n_us
 void moments(pic_ctx *c, bool snapshot, pic_moments *out);
 void luminosity(pic_ctx *c, double t, double *L);  // nr + 1 device values (Sec. 5.3)
 void filter_array(pic_ctx *c, double *a, double *tmp, int half_j, int sign, int passes);
+// Gauss law (G - Qbar against the snapshot, into d_cnt[CNT_GMAX/QMAX]) over
+// local rows ilo..imax, with Q, Qa already deposited and filtered
+void gauss_rows(pic_ctx *c, int ilo, int imax, bool snapshot);
+void field_energy_rows(pic_ctx *c, int imax);  // adds rows 0..imax to d_acc[ACC_FIELD]
 // particles64.cu
 void particles64(pic_ctx *c, double t);
 int64_t compact64(pic_ctx *c);         // stable removal of dead slots; returns live count
@@ -160,6 +164,12 @@ void reduce_particles32(pic_ctx *c);
 int pic_fail(int code, const std::string &msg);
 int pic_cuda_check(cudaError_t e, const char *what);
 int pic_latch_status(pic_ctx *c);  // read the device error word, return the context's status
+int pic_desc_defaults(pic_desc *d);  // fill the zero defaults and check the descriptor
+// a context over rows [i0, i0 + d.nr) of a grid of nr_glob rows (api.cu)
+int pic_create_context(pic_ctx **out, const pic_desc &d, void *stream, int i0, int nr_glob, int open_lo, int open_hi);
+int pic_grow_particles(pic_ctx *c, int64_t new_cap);  // keep [0, n_used), reallocate
+int pic_compact(pic_ctx *c);                          // remove free slots (sort on the FP32 path)
+int pic_reserve(pic_ctx *c, int64_t need);            // capacity for at least `need` particle slots
 #define PIC_CUDA(call)                                          \
   do {                                                          \
     cudaError_t e_ = (call);                                    \

@@ -30,7 +30,9 @@ EXPORTS = ["pic_init_grid", "pic_load_particles", "pic_step", "pic_get_fields", 
            "pic_get_particles", "pic_get_particles_noalloc", "pic_get_live", "pic_get_moments", "pic_get_luminosity",
            "pic_gauss_snapshot", "pic_set_clock", "pic_profile",
            "pic_get_profile", "pic_get_launches", "pic_ensemble_step", "pic_autotune", "pic_destroy", "pic_last_error",
-           "pic_struct_sizes", "pic_get_charge", "pic_grid_coords"]
+           "pic_struct_sizes", "pic_get_charge", "pic_grid_coords",
+           "pic_slabs_init", "pic_slabs_load_particles", "pic_slabs_step", "pic_slabs_get_fields",
+           "pic_slabs_get_flux", "pic_slabs_get_particles", "pic_slabs_get_moments", "pic_slabs_destroy"]
 
 
 class pic_desc(C.Structure):
@@ -96,6 +98,14 @@ def lib():
         "pic_ensemble_step": [C.POINTER(C.c_void_p), I32, I32],
         "pic_autotune": [P, I32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
         "pic_destroy": [P],
+        "pic_slabs_init": [C.POINTER(C.c_void_p), C.POINTER(pic_desc), I32, C.POINTER(C.c_int32), P],
+        "pic_slabs_load_particles": [P, I64, P, P, P, P, P, P, I32],
+        "pic_slabs_step": [P, I32],
+        "pic_slabs_get_fields": [P, I32, P, C.POINTER(C.c_int64), I32],
+        "pic_slabs_get_flux": [P, P, C.POINTER(C.c_int64), I32],
+        "pic_slabs_get_particles": [P, C.POINTER(C.c_int64), P, P, P, P, P, P, P, I32],
+        "pic_slabs_get_moments": [P, C.POINTER(pic_moments)],
+        "pic_slabs_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -307,6 +317,77 @@ class Simulation:
         check(self.L.pic_get_profile(self.h, ms, C.byref(steps)))
         names = ["particles", "reduce", "filter", "fields", "inject", "sort"]
         return dict(zip(names, list(ms))), steps.value
+
+
+class Slabs:
+    """One simulation split into radial slabs: pic_slabs_init .. pic_slabs_destroy.
+    The methods mirror Simulation's for the whole grid."""
+
+    def __init__(self, desc: pic_desc, nslabs: int, rows=None, stream: int = 0):
+        self.L = lib()
+        self.desc = desc
+        h = C.c_void_p()
+        rp = None
+        if rows is not None:
+            rows = (C.c_int32 * len(rows))(*rows)
+            rp = C.cast(rows, C.POINTER(C.c_int32))
+        check(self.L.pic_slabs_init(C.byref(h), C.byref(desc), nslabs, rp, C.c_void_p(stream)))
+        self.h = h
+        self.nr, self.nth = desc.nr, desc.nth
+        self.g = desc.n_filt + 2
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.pic_slabs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, x1, x2, ur, uth, uph, qw):
+        ptrs = [_ptr(a) for a in (x1, x2, ur, uth, uph, qw)]
+        mems = {m for _, m in ptrs}
+        assert len(mems) == 1, "all arrays on the host or all on the device"
+        check(self.L.pic_slabs_load_particles(self.h, len(x1), *[p for p, _ in ptrs], mems.pop()))
+
+    def step(self, n=1):
+        return check(self.L.pic_slabs_step(self.h, n))
+
+    def fields(self, total=False):
+        n = C.c_int64()
+        check(self.L.pic_slabs_get_fields(self.h, 1 if total else 0, None, C.byref(n), PIC_MEM_HOST))
+        out = np.empty(n.value)
+        check(self.L.pic_slabs_get_fields(self.h, 1 if total else 0, C.c_void_p(out.ctypes.data), C.byref(n),
+                                          PIC_MEM_HOST))
+        return out.reshape(6, self.nr + 1, self.nth + 1)
+
+    def flux(self):
+        n = C.c_int64()
+        check(self.L.pic_slabs_get_flux(self.h, None, C.byref(n), PIC_MEM_HOST))
+        out = np.empty(n.value)
+        check(self.L.pic_slabs_get_flux(self.h, C.c_void_p(out.ctypes.data), C.byref(n), PIC_MEM_HOST))
+        return out.reshape(3, self.nr + 2 * self.g + 1, self.nth + 1)
+
+    def particles(self):
+        keys = ("x1", "x2", "ur", "uth", "uph", "qw")
+        n = C.c_int64(0)
+        check(self.L.pic_slabs_get_particles(self.h, C.byref(n), None, None, None, None, None, None, None,
+                                             PIC_MEM_HOST))
+        out = {k: np.empty(n.value) for k in keys}
+        ids = np.empty(n.value, dtype=np.int64)
+        ptrs = [C.c_void_p(out[k].ctypes.data) for k in keys]
+        check(self.L.pic_slabs_get_particles(self.h, C.byref(n), *ptrs, C.c_void_p(ids.ctypes.data), PIC_MEM_HOST))
+        out = {k: v[: n.value] for k, v in out.items()}
+        out["id"] = ids[: n.value]
+        return out
+
+    def moments(self):
+        m = pic_moments()
+        check(self.L.pic_slabs_get_moments(self.h, C.byref(m)))
+        return {k: getattr(m, k) for k, _ in pic_moments._fields_}
 
 
 def ensemble_step(sims, nsteps):

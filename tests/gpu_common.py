@@ -59,6 +59,19 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
 
 
+def maxnorm_rel(a, b):
+    """Element-wise check of stacked planes (fields or fluxes): the largest
+    |a - b| of each component relative to that component's own largest |b|,
+    maximised over the components.  A localised error that a global L2 norm
+    would average away shows up here."""
+    out = 0.0
+    for c in range(a.shape[0]):
+        den = float(np.max(np.abs(b[c])))
+        num = float(np.max(np.abs(a[c] - b[c])))
+        out = max(out, num / den if den > 0 else num)
+    return out
+
+
 def replay_compare_fp32(g, r, tau):
     """Compare the FP32 path's step with the oracle's replay of it, both given
     as particle dicts.  Removals agree: ids kept by one side only (a removal

@@ -95,3 +95,27 @@ def test_header_compiles_as_plain_c_and_cpp(lang, std):
     r = subprocess.run([cc, f"-std={std}", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", lang,
                         os.path.join(ROOT, "include", "picsar.h")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+@pytest.mark.parametrize("nslabs,rows,over", [
+    (16, None, {}),              # slabs of 4 rows are narrower than their halos (2 (n_filt + 2) + 2 rows)
+    (2, [0, 40, 60], {}),        # the rows do not end at nr
+    (2, [0, 56, 64], {}),        # the lossy layer (8 cells) does not fit in the last slab
+    (2, None, {"precision": "fp32"}),  # slabs run the FP64 path
+    (0, None, {}),
+])
+def test_slab_descriptor_and_rows_are_checked(nslabs, rows, over):
+    """pic_slabs_init checks the grid, the slab rows and the path before any
+    device work: refused with PIC_EINVAL on any machine."""
+    from paper_1407_1810_gb300 import build, picsar as P
+
+    try:
+        build.build()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    kw = dict(nr=64, nth=40, r_min=1.0, r_max=10.0, r_map="log", th_map="linear", dt=0.01, n_filt=0,
+              absorb_cells=8, absorb_profile="linear", vacuum="monopole", b0=1.0, precision="fp64", pusher="vay")
+    kw.update(over)
+    with pytest.raises(P.PicError) as e:
+        P.Slabs(P.make_desc(**kw), nslabs, rows)
+    assert e.value.code == P.PIC_EINVAL
