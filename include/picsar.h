@@ -130,6 +130,7 @@ typedef struct pic_moments {
                                 interior nodes 1 <= i <= nr - absorb_cells - 1 (App. B, Sec. 2) */
   double total_charge;       /* sum qw */
   int64_t inject_capped;     /* VARIABLE injection: cell-steps whose count was cut to pairs_per_cell */
+  int64_t axis_ties;         /* axis crossings whose azimuth branch was a tie (see pic_get_axis_ties) */
 } pic_moments;
 
 /* Create a context: allocates the grid arrays on the current CUDA device and
@@ -243,6 +244,25 @@ int pic_set_clock(pic_ctx *c, int64_t step, int64_t next_id);
  * injection, sort] into ms6 and the number of timed steps into *steps. */
 int pic_profile(pic_ctx *c, int32_t enable);
 int pic_get_profile(pic_ctx *c, double *ms6, int64_t *steps);
+
+/* Ties of the azimuth branch at the polar axis (Sec. 3.3; the azimuthal flux
+ * of a move is qw times the swept azimuth over 2 pi).  A move that carries a
+ * particle across the polar axis sweeps an azimuth near +pi or -pi with the
+ * sign of u_ph; when it lies within 2^-13 of +-pi (|D_ph| <= 2^-13 |P_x|,
+ * P_x < 0 the displaced point's coordinate along the old cylindrical radius)
+ * the branch is set by the rounding of a nearly vanishing u_ph, either branch
+ * is a valid result, and the two differ by the particle's whole charge in the
+ * azimuthal flux.  Every context counts its ties (pic_moments.axis_ties) and
+ * logs the first 65536 as (step, id, sign = +1 or -1, the branch taken).
+ *
+ * pic_get_axis_ties: *n in: capacity of the host arrays; out: ties logged.
+ * steps == NULL only queries *n.  signs may be NULL.
+ * pic_set_axis_hints: n host entries (step, id, sign) that fix the branch of
+ * those ties when this context meets them (a replay of another run follows
+ * that run's branches); any previous table is replaced, n = 0 removes it.
+ * Ties the table does not list keep their own branch. */
+int pic_get_axis_ties(pic_ctx *c, int64_t *n, int64_t *steps, int64_t *ids, int32_t *signs);
+int pic_set_axis_hints(pic_ctx *c, int64_t n, const int64_t *steps, const int64_t *ids, const int32_t *signs);
 
 /* Number of kernels this context has launched so far (every launch of the
  * library's own kernels, all phases); *n receives the count. */

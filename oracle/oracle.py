@@ -120,6 +120,8 @@ def _load():
         "orc_luminosity": (None, [P, C.c_double, D]),
         "orc_counters": (None, [P, C.POINTER(C.c_int64)]),
         "orc_splitmix64": (C.c_uint64, [C.c_uint64, C.c_uint64]),
+        "orc_axis_ties": (I64, [P]),
+        "orc_set_axis_hints": (None, [P, I64, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -301,6 +303,17 @@ class Oracle:
         a = np.zeros(self.nr + 1)
         self.lib.orc_luminosity(self.h, t, _dp(a))
         return a
+
+    def axis_ties(self):
+        """Ties of the azimuth branch at the polar axis met so far (R15)."""
+        return int(self.lib.orc_axis_ties(self.h))
+
+    def set_axis_hints(self, ties):
+        """Follow another run's branches at its logged ties: dict of step, id, sign."""
+        st = np.ascontiguousarray(ties["step"], dtype=np.int64)
+        ids = np.ascontiguousarray(ties["id"], dtype=np.int64)
+        sg = np.ascontiguousarray(ties["sign"], dtype=np.int32)
+        self.lib.orc_set_axis_hints(self.h, len(st), _ip(st), _ip(ids), sg.ctypes.data_as(C.POINTER(C.c_int32)))
 
     def counters(self):
         a = np.zeros(5, dtype=np.int64)

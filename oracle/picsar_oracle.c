@@ -58,6 +58,14 @@
  *      outside the vacuum field of the rotating conducting sphere with no net
  *      charge, E = -grad Phi, Phi = -(Omega mu r0^2 / 3 r^3)(3 cos^2 th - 1),
  *      which matches the inside potential's l = 2 part at r0.
+ *   R15 Ties of the azimuth branch (adjudication, not arithmetic): a move that
+ *      crosses the polar axis sweeps an azimuth near +pi or -pi with the sign
+ *      of u_ph (R4); when |Y| <= 2^-13 (-X) (X < 0, the displaced point's
+ *      coordinate along the old cylindrical radius) the sign is set by the
+ *      rounding of a nearly vanishing u_ph and both branches are valid.  Such
+ *      ties are counted; a table of hints (step, id -> sign) from another run
+ *      fixes the branch of the ties it lists, so a replay follows that run.
+ *      Without hints every tie keeps atan2's own branch.
  */
 #include "picsar_oracle.h"
 
@@ -84,6 +92,10 @@ struct orc_sim {
   int64_t n_deleted, n_injected, n_capped;
   double *gq0; /* (G - Qbar) at the snapshot, (nr+1) x (nth+1) */
   int err;
+  /* R15: ties met so far, and the hints (sorted by step, then id) */
+  int64_t n_ties, nh;
+  int64_t *h_step, *h_id;
+  int *h_sign;
 };
 
 /* ------------------------------------------------------------------------- */
@@ -168,6 +180,7 @@ void orc_destroy(orc_sim *s) {
   for (int c = 0; c < 3; ++c) free(s->F[c]);
   free(s->x1); free(s->x2); free(s->ur); free(s->uth); free(s->uph); free(s->qw); free(s->id);
   free(s->gq0);
+  free(s->h_step); free(s->h_id); free(s->h_sign);
   free(s);
 }
 
@@ -675,6 +688,19 @@ void orc_field_step(orc_sim *s, int32_t nsteps) {
 /* the meridional plane phi = 0; after the move the particle is rotated back  */
 /* to phi = 0 (axisymmetry), which also reflects it through the polar axis.   */
 /* ------------------------------------------------------------------------- */
+/* R15: the hinted branch of a tie at (current step, id), else phi's own */
+static double tie_branch(orc_sim *s, int64_t id, double phi) {
+  int sg = phi < 0 ? -1 : 1;
+  s->n_ties++;
+  for (int64_t lo = 0, hi = s->nh; lo < hi;) {
+    int64_t mid = (lo + hi) / 2;
+    if (s->h_step[mid] == s->step && s->h_id[mid] == id) { sg = s->h_sign[mid] < 0 ? -1 : 1; break; }
+    if (s->h_step[mid] < s->step || (s->h_step[mid] == s->step && s->h_id[mid] < id)) lo = mid + 1;
+    else hi = mid;
+  }
+  return sg * fabs(phi);
+}
+
 static void particle_step(orc_sim *s, int64_t k, double t, int *del) {
   const int nr = s->p.nr;
   double x1 = s->x1[k], x2 = s->x2[k], qw = s->qw[k];
@@ -692,6 +718,7 @@ static void particle_step(orc_sim *s, int64_t k, double t, int *del) {
   double g = sqrt(1.0 + dot(u, u));
   double X = r * st + u[0] / g * s->p.dt, Y = u[1] / g * s->p.dt, Z = r * ct + u[2] / g * s->p.dt;
   double R = hypot(X, Y), phi = atan2(Y, X), rn = hypot(R, Z), thn = atan2(R, Z);
+  if (X < 0 && fabs(Y) <= -X / 8192.0) phi = tie_branch(s, s->id[k], phi); /* R15 */
   double cp = R > 0 ? X / R : 1.0, sp = R > 0 ? Y / R : 0.0;
   double ux = cp * u[0] + sp * u[1], uy = -sp * u[0] + cp * u[1], uz = u[2];
   double stn = rn > 0 ? R / rn : 0.0, ctn = rn > 0 ? Z / rn : 1.0;
@@ -946,3 +973,36 @@ void orc_divb(const orc_sim *s, double *out) {
                                 Bt[FI(s, i, j + 1)] * dA_rph(ra, rb, tb) - Bt[FI(s, i, j)] * dA_rph(ra, rb, ta);
     }
 }
+
+/* R15 hints: n entries (step, id, sign), any order; replaces the table */
+static const int64_t *g_hs, *g_hi;
+static int hint_cmp(const void *a, const void *b) {
+  int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
+  if (g_hs[i] != g_hs[j]) return g_hs[i] < g_hs[j] ? -1 : 1;
+  if (g_hi[i] != g_hi[j]) return g_hi[i] < g_hi[j] ? -1 : 1;
+  return 0;
+}
+
+void orc_set_axis_hints(orc_sim *s, int64_t n, const int64_t *steps, const int64_t *ids, const int32_t *signs) {
+  free(s->h_step); free(s->h_id); free(s->h_sign);
+  s->h_step = s->h_id = NULL;
+  s->h_sign = NULL;
+  s->nh = 0;
+  if (n <= 0) return;
+  int64_t *ord = (int64_t *)malloc(n * sizeof(int64_t));
+  for (int64_t k = 0; k < n; ++k) ord[k] = k;
+  g_hs = steps; g_hi = ids;
+  qsort(ord, (size_t)n, sizeof(int64_t), hint_cmp);
+  s->h_step = (int64_t *)malloc(n * sizeof(int64_t));
+  s->h_id = (int64_t *)malloc(n * sizeof(int64_t));
+  s->h_sign = (int *)malloc(n * sizeof(int));
+  for (int64_t k = 0; k < n; ++k) {
+    s->h_step[k] = steps[ord[k]];
+    s->h_id[k] = ids[ord[k]];
+    s->h_sign[k] = signs[ord[k]];
+  }
+  s->nh = n;
+  free(ord);
+}
+
+int64_t orc_axis_ties(const orc_sim *s) { return s->n_ties; }

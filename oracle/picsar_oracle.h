@@ -117,6 +117,10 @@ void orc_luminosity(const orc_sim *s, double t, double *out);
 /* live, deleted, injected, next_id, capped (VARIABLE injection: cells whose
  * pair count was cut to pairs_per_cell) */
 void orc_counters(const orc_sim *s, int64_t *out5);
+/* R15: ties of the azimuth branch at the polar axis met so far, and hints
+ * (step, id -> sign) that fix the branch of the ties they list */
+int64_t orc_axis_ties(const orc_sim *s);
+void orc_set_axis_hints(orc_sim *s, int64_t n, const int64_t *steps, const int64_t *ids, const int32_t *signs);
 /* output number n + 1 of the SplitMix64 stream seeded with `seed` */
 uint64_t orc_splitmix64(uint64_t seed, uint64_t n);
 

@@ -1,5 +1,6 @@
 // api.cu -- the C-ABI of include/picsar.h: context set-up, the metric tables,
 // particle loading, the step sequence and the getters.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -563,6 +564,8 @@ int pic_create_context(pic_ctx **out, const pic_desc &d, void *stream, int i0, i
       q0 = std::min<long long>(QEXP_MAX, std::max<long long>(QEXP_MIN, (long long)std::ceil(std::log2(d.flux_quantum)) + KFIX));
     PIC_CUDA(cudaMemcpy(c->d_cnt + CNT_QEXP, &q0, sizeof q0, cudaMemcpyHostToDevice));
   }
+  if ((e = dalloc(&c->tie_step, TIE_LOG)) || (e = dalloc(&c->tie_id, TIE_LOG)) || (e = dalloc(&c->tie_sign, TIE_LOG)))
+    return fail(e);
   PIC_CUDA(cudaMallocHost((void **)&c->h_pinned, 64));
   PIC_CUDA(cudaDeviceSynchronize());
   *out = c;
@@ -959,6 +962,58 @@ extern "C" int pic_get_profile(pic_ctx *c, double *ms6, int64_t *steps) {
   return PIC_OK;
 }
 
+extern "C" int pic_get_axis_ties(pic_ctx *c, int64_t *n, int64_t *steps, int64_t *ids, int32_t *signs) {
+  if (!c || !n) return pic_fail(PIC_EINVAL, "null argument");
+  long long total = 0;
+  PIC_CUDA(cudaMemcpyAsync(&total, c->d_cnt + CNT_TIES, sizeof total, cudaMemcpyDeviceToHost, c->stream));
+  PIC_CUDA(cudaStreamSynchronize(c->stream));
+  const int64_t logged = std::min<int64_t>(total, TIE_LOG);
+  if (!steps) { *n = logged; return PIC_OK; }
+  if (*n < logged) { *n = logged; return pic_fail(PIC_EINVAL, "output arrays too small"); }
+  if (!ids) return pic_fail(PIC_EINVAL, "null output array");
+  *n = logged;
+  if (logged == 0) return PIC_OK;
+  std::vector<int8_t> sg(logged);
+  PIC_CUDA(cudaMemcpy(steps, c->tie_step, logged * sizeof(int64_t), cudaMemcpyDeviceToHost));
+  PIC_CUDA(cudaMemcpy(ids, c->tie_id, logged * sizeof(int64_t), cudaMemcpyDeviceToHost));
+  PIC_CUDA(cudaMemcpy(sg.data(), c->tie_sign, logged, cudaMemcpyDeviceToHost));
+  if (signs)
+    for (int64_t k = 0; k < logged; ++k) signs[k] = sg[k];
+  return PIC_OK;
+}
+
+extern "C" int pic_set_axis_hints(pic_ctx *c, int64_t n, const int64_t *steps, const int64_t *ids,
+                                  const int32_t *signs) {
+  if (!c || n < 0) return pic_fail(PIC_EINVAL, "bad argument");
+  if (n > 0 && (!steps || !ids || !signs)) return pic_fail(PIC_EINVAL, "null hint array");
+  PIC_CUDA(cudaStreamSynchronize(c->stream));
+  cudaFree(c->hint_step); cudaFree(c->hint_id); cudaFree(c->hint_sign);
+  c->hint_step = c->hint_id = nullptr;
+  c->hint_sign = nullptr;
+  c->nhint = 0;
+  if (n == 0) return PIC_OK;
+  // sorted by (step, id) for the kernels' binary search
+  std::vector<int64_t> ord(n);
+  for (int64_t k = 0; k < n; ++k) ord[k] = k;
+  std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
+    return steps[a] < steps[b] || (steps[a] == steps[b] && ids[a] < ids[b]);
+  });
+  std::vector<int64_t> hs(n), hi(n);
+  std::vector<int8_t> hg(n);
+  for (int64_t k = 0; k < n; ++k) {
+    hs[k] = steps[ord[k]];
+    hi[k] = ids[ord[k]];
+    hg[k] = signs[ord[k]] < 0 ? -1 : 1;
+  }
+  int e;
+  if ((e = dalloc(&c->hint_step, n)) || (e = dalloc(&c->hint_id, n)) || (e = dalloc(&c->hint_sign, n))) return e;
+  PIC_CUDA(cudaMemcpy(c->hint_step, hs.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice));
+  PIC_CUDA(cudaMemcpy(c->hint_id, hi.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice));
+  PIC_CUDA(cudaMemcpy(c->hint_sign, hg.data(), n, cudaMemcpyHostToDevice));
+  c->nhint = n;
+  return PIC_OK;
+}
+
 extern "C" int pic_get_launches(pic_ctx *c, int64_t *n) {
   if (!c || !n) return pic_fail(PIC_EINVAL, "null argument");
   *n = c->launches;
@@ -1164,6 +1219,8 @@ extern "C" int pic_destroy(pic_ctx *c) {
   cudaFree(c->Q); cudaFree(c->Qa); cudaFree(c->Qt); cudaFree(c->gsnap); cudaFree(c->sig);
   cudaFree(c->d_err); cudaFree(c->d_cnt); cudaFree(c->d_acc);
   cudaFree(c->tiles.start); cudaFree(c->tiles.cursor); cudaFree(c->tiles.bsum);
+  cudaFree(c->tie_step); cudaFree(c->tie_id); cudaFree(c->tie_sign);
+  cudaFree(c->hint_step); cudaFree(c->hint_id); cudaFree(c->hint_sign);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;

@@ -487,6 +487,7 @@ void moments(pic_ctx *c, bool snapshot, pic_moments *out) {
   out->deleted = cnt[CNT_DELETED];
   out->injected = cnt[CNT_INJECTED];
   out->inject_capped = cnt[CNT_CAPPED];
+  out->axis_ties = cnt[CNT_TIES];
   out->step = c->step;
   out->dt = G.dt;
   out->time = c->step * G.dt;

@@ -59,6 +59,8 @@ struct Args32 {
   float dt_lo, inv_dxi_lo, k2_hi, k2_lo;  // k2 = nth / pi (linear theta map)
   float b0_lo, qmdt;     // qmdt = (q/m) dt rounded once
   const long long *qexp;    // fixed-point exponent e: one flux unit is 2^(e - KFIX)
+  const int64_t *ids;       // particle ids (read only for an axis-crossing tie)
+  AxisTies ties;
   const float *r_n;         // f_r(i) per padded row (FP32)
   const float *f[6];        // FP32 field copies (padded)
   long long *acc[3];        // global fixed-point flux accumulators (padded)
@@ -259,8 +261,8 @@ struct Flags {
 
 // One particle step.  Returns false when the particle is removed.
 template <int SPEC, class W>
-__device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float &dx, float &dy, float &ur, float &ut,
-                              float &up, const float qw) {
+__device__ inline bool step32(const Args32 &A, const W &w, int64_t k, uint32_t &cell, float &dx, float &dy, float &ur,
+                              float &ut, float &up, const float qw) {
   const Flags<SPEC> F(A);
   const int ci = (int)(cell >> 16) - CELL_BIAS, cj = (int)(cell & 0xffffu);
   // ---- geometry of the particle's position (Sec. 3.2) -----------------------
@@ -408,7 +410,8 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
   // azimuthal flux: charge crossing the meridional half-plane, qw dphi / 2 pi,
   // area weights at the midpoint of the grid path
   {
-    const float phi = atan2_small(Dp, Px);
+    float phi = atan2_small(Dp, Px);
+    if (Px < 0.f && fabsf(Dp) <= (float)AXIS_TIE * -Px) phi = axis_tie(A.ties, A.ids[k], phi);  // rare
     const float v = scale * phi * 0.15915494309189535f;
     const float mx = 0.5f * (dx + (float)kx + nx), my = 0.5f * (dy + (float)ky + ny);
     const float fx = floorf(mx), fy = floorf(my);
@@ -437,10 +440,10 @@ __device__ inline bool step32(const Args32 &A, const W &w, uint32_t &cell, float
 // the rare path: a particle outside its tile's window (inlined: an
 // out-of-line call costs register spills around it in the hot loop)
 template <int SPEC>
-__device__ inline bool step32_global(const Args32 &A, float fs, uint32_t &cell, float &dx, float &dy, float &ur,
-                                     float &ut, float &up, const float qw) {
+__device__ inline bool step32_global(const Args32 &A, float fs, int64_t k, uint32_t &cell, float &dx, float &dy,
+                                     float &ur, float &ut, float &up, const float qw) {
   const GlobAcc gw{&A, fs};
-  return step32<SPEC>(A, gw, cell, dx, dy, ur, ut, up, qw);
+  return step32<SPEC>(A, gw, k, cell, dx, dy, ur, ut, up, qw);
 }
 
 template <int SPEC, class SW>
@@ -455,9 +458,9 @@ __device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, 
   const int ci = (int)(cell >> 16) - CELL_BIAS, cj = (int)(cell & 0xffffu);
   bool alive;
   if (win && ci >= wi_lo && ci < wi_hi && cj >= wj_lo && cj < wj_hi)
-    alive = step32<SPEC>(A, sw, cell, dx, dy, ur, ut, up, qw);
+    alive = step32<SPEC>(A, sw, k, cell, dx, dy, ur, ut, up, qw);
   else
-    alive = step32_global<SPEC>(A, sw.fs, cell, dx, dy, ur, ut, up, qw);
+    alive = step32_global<SPEC>(A, sw.fs, k, cell, dx, dy, ur, ut, up, qw);
   if (!alive) { P.qw[k] = 0.f; ++dead; return; }
   P.cell[k] = cell;
   P.dx[k] = dx; P.dy[k] = dy;
@@ -818,6 +821,8 @@ Args32 make_args(pic_ctx *c, double t) {
   A.k2_lo = (float)(G.nth / M_PI - (double)A.k2_hi);
   A.inv_nth = (float)(1.0 / G.nth); A.nth_f = (float)G.nth;
   A.qexp = c->d_cnt + CNT_QEXP;
+  A.ids = c->p32.id;
+  A.ties = axis_ties(c);
   A.r_n = c->r_n32;
   for (int k = 0; k < 6; ++k) A.f[k] = c->f32[k];
   for (int k = 0; k < 3; ++k) A.acc[k] = c->acc[k];

@@ -70,7 +70,7 @@ struct Fields64 { const double *f[6]; };
 struct Flux64 { double *Fr, *Ft, *Fp; };
 
 __global__ void __launch_bounds__(256) k_particles64(Grid G, Parts64 P, int64_t n, double t, Fields64 F, Flux64 D,
-                                                     int *err, long long *cnt) {
+                                                     int *err, long long *cnt, AxisTies ties) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
   const double qw = P.qw[k];
@@ -103,7 +103,9 @@ __global__ void __launch_bounds__(256) k_particles64(Grid G, Parts64 P, int64_t 
   // straight 3-D move from (r st, 0, r ct), then back to phi = 0 (Sec. 3.3)
   const double ig = 1.0 / sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   const double X = r * st + u[0] * ig * G.dt, Y = u[1] * ig * G.dt, Z = r * ct + u[2] * ig * G.dt;
-  const double R = hypot(X, Y), phi = atan2(Y, X), rn = hypot(R, Z), thn = atan2(R, Z);
+  const double R = hypot(X, Y), rn = hypot(R, Z), thn = atan2(R, Z);
+  double phi = atan2(Y, X);
+  if (X < 0.0 && fabs(Y) <= AXIS_TIE * -X) phi = axis_tie(ties, P.id[k], phi);  // rare: see AxisTies
   const double cp = R > 0.0 ? X / R : 1.0, sp = R > 0.0 ? Y / R : 0.0;
   const double ux = cp * u[0] + sp * u[1], uy = -sp * u[0] + cp * u[1], uz = u[2];
   const double stn = rn > 0.0 ? R / rn : 0.0, ctn = rn > 0.0 ? Z / rn : 1.0;
@@ -237,7 +239,8 @@ void particles64(pic_ctx *c, double t) {
   for (int k = 0; k < 6; ++k) F.f[k] = c->f[k];
   Flux64 D{c->F[0], c->F[1], c->F[2]};
   const int64_t blocks = (c->n_used + 255) / 256;
-  ++c->launches, k_particles64<<<(unsigned)blocks, 256, 0, c->stream>>>(c->G, c->p64, c->n_used, t, F, D, c->d_err, c->d_cnt);
+  ++c->launches, k_particles64<<<(unsigned)blocks, 256, 0, c->stream>>>(c->G, c->p64, c->n_used, t, F, D, c->d_err, c->d_cnt,
+                                                                          axis_ties(c));
 }
 
 int64_t compact64(pic_ctx *c) {

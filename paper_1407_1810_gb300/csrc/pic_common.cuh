@@ -215,6 +215,47 @@ __device__ inline void push(int pusher, T qmdt, const T E[3], const T B[3], T u[
   else push_vay(qmdt, E, B, u);
 }
 
+// ---- ties of the azimuth branch at the polar axis (Sec. 3.3, reading of the
+//      azimuthal flux) -------------------------------------------------------
+// A move that carries a particle across the polar axis sweeps an azimuth near
+// +pi or -pi, and the sign is that of u_ph.  When the sweep lies within
+// AXIS_TIE of +-pi (|Dp| <= AXIS_TIE |Px|, Px < 0 the displaced point's
+// coordinate along the old cylindrical radius) the sign is set by the
+// rounding of a nearly vanishing u_ph and either branch is a valid result;
+// the azimuthal flux of the two branches differs by the particle's whole
+// charge.  Such ties are counted and logged as (step, id, sign).  A table of
+// hints, taken from the log of another run, fixes the branch of the ties it
+// lists, so that a replay follows the run it is compared with.
+constexpr double AXIS_TIE = 1.0 / 8192;
+struct AxisTies {
+  const int64_t *hstep = nullptr, *hid = nullptr;  // hints, sorted by (step, id)
+  const int8_t *hsign = nullptr;
+  int64_t nh = 0;
+  int64_t *lstep = nullptr, *lid = nullptr;        // the log of this run
+  int8_t *lsign = nullptr;
+  int64_t lcap = 0;
+  long long *count = nullptr;                      // ties met (the log keeps the first lcap)
+  int64_t step = 0;                                // the step being taken
+};
+
+// the branch of a tie: the hinted sign if (step, id) is in the table, else
+// phi's own; logged; returns +-|phi|
+template <typename T>
+__device__ inline T axis_tie(const AxisTies &X, int64_t id, T phi) {
+  int sg = phi < T(0) ? -1 : 1;
+  int64_t lo = 0, hi = X.nh;
+  while (lo < hi) {  // first entry not below (step, id)
+    const int64_t mid = (lo + hi) >> 1;
+    const bool below = X.hstep[mid] < X.step || (X.hstep[mid] == X.step && X.hid[mid] < id);
+    if (below) lo = mid + 1;
+    else hi = mid;
+  }
+  if (lo < X.nh && X.hstep[lo] == X.step && X.hid[lo] == id) sg = X.hsign[lo] < 0 ? -1 : 1;
+  const long long n = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(X.count), 1ull);
+  if (n < X.lcap) { X.lstep[n] = X.step; X.lid[n] = id; X.lsign[n] = (int8_t)sg; }
+  return sg > 0 ? fabs(phi) : -fabs(phi);
+}
+
 __device__ inline void set_err(int *err, int bits) { atomicOr(err, bits); }
 // block-wide sums of (double, double, int) with one atomic per block:
 // warp shuffles, then the warp leaders through shared memory

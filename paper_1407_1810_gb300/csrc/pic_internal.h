@@ -28,7 +28,8 @@ constexpr int CELL_BIAS = 1024;
 
 // device counters (one int64 array)
 enum Counter { CNT_DELETED = 0, CNT_INJECTED = 1, CNT_LIVE = 2, CNT_SMAX = 3, CNT_GMAX = 4,
-               CNT_QMAX = 5, CNT_SORTED = 6, CNT_QEXP = 7, CNT_CAPPED = 8, CNT_N };
+               CNT_QMAX = 5, CNT_SORTED = 6, CNT_QEXP = 7, CNT_CAPPED = 8, CNT_TIES = 9, CNT_N };
+constexpr int64_t TIE_LOG = 1 << 16;  // axis-crossing ties logged per context
 
 // FP32 path fixed-point deposit.  One flux unit is 2^(e - KFIX) with e =
 // ceil(log2 max |qw|) over every charge the context has held (loaded or
@@ -114,6 +115,12 @@ struct pic_ctx {
   long long *d_cnt = nullptr;
   double *d_acc = nullptr;
   long long *h_pinned = nullptr;  // pinned host mirror for small reads
+  // axis-crossing ties: the log of this context and the hints it follows
+  int64_t *tie_step = nullptr, *tie_id = nullptr;
+  int8_t *tie_sign = nullptr;
+  int64_t *hint_step = nullptr, *hint_id = nullptr;
+  int8_t *hint_sign = nullptr;
+  int64_t nhint = 0;
   int64_t step = 0, next_id = 0;
   int64_t launches = 0;  // kernels launched by this context
   int host_err = 0;
@@ -158,7 +165,18 @@ void flux_from_acc(pic_ctx *c);        // fixed point -> FP64 fluxes, clears the
 int64_t sort32(pic_ctx *c);            // tile sort + removal; returns live count
 void charge32(pic_ctx *c, double *Q, double *Qa);
 void reduce_particles32(pic_ctx *c);
+// the tie log and hints of a context for the step it is taking
+inline AxisTies axis_ties(const pic_ctx *c);
 }  // namespace pic
+
+inline pic::AxisTies pic::axis_ties(const pic_ctx *c) {
+  AxisTies X;
+  X.hstep = c->hint_step; X.hid = c->hint_id; X.hsign = c->hint_sign; X.nh = c->nhint;
+  X.lstep = c->tie_step; X.lid = c->tie_id; X.lsign = c->tie_sign; X.lcap = TIE_LOG;
+  X.count = c->d_cnt + CNT_TIES;
+  X.step = c->step;
+  return X;
+}
 
 // error plumbing (api.cu)
 int pic_fail(int code, const std::string &msg);

@@ -520,6 +520,7 @@ extern "C" int pic_slabs_get_moments(pic_slabs *g, pic_moments *out) {
     out->deleted += cnt[CNT_DELETED];
     out->injected += cnt[CNT_INJECTED];
     out->inject_capped += cnt[CNT_CAPPED];
+    out->axis_ties += cnt[CNT_TIES];
     out->kinetic_energy += acc[ACC_KIN];
     out->field_energy += acc[ACC_FIELD];
     out->total_charge += acc[ACC_CHARGE];

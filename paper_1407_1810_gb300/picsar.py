@@ -30,7 +30,7 @@ EXPORTS = ["pic_init_grid", "pic_load_particles", "pic_step", "pic_get_fields", 
            "pic_get_particles", "pic_get_particles_noalloc", "pic_get_live", "pic_get_moments", "pic_get_luminosity",
            "pic_gauss_snapshot", "pic_set_clock", "pic_profile",
            "pic_get_profile", "pic_get_launches", "pic_ensemble_step", "pic_autotune", "pic_destroy", "pic_last_error",
-           "pic_struct_sizes", "pic_get_charge", "pic_grid_coords",
+           "pic_struct_sizes", "pic_get_charge", "pic_grid_coords", "pic_get_axis_ties", "pic_set_axis_hints",
            "pic_slabs_init", "pic_slabs_load_particles", "pic_slabs_step", "pic_slabs_get_fields",
            "pic_slabs_get_flux", "pic_slabs_get_particles", "pic_slabs_get_moments", "pic_slabs_destroy"]
 
@@ -60,7 +60,7 @@ class pic_moments(C.Structure):
         ("time", C.c_double), ("dt", C.c_double),
         ("kinetic_energy", C.c_double), ("field_energy", C.c_double),
         ("gauss_residual", C.c_double), ("total_charge", C.c_double),
-        ("inject_capped", C.c_int64),
+        ("inject_capped", C.c_int64), ("axis_ties", C.c_int64),
     ]
 
 
@@ -98,6 +98,8 @@ def lib():
         "pic_ensemble_step": [C.POINTER(C.c_void_p), I32, I32],
         "pic_autotune": [P, I32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
         "pic_destroy": [P],
+        "pic_get_axis_ties": [P, C.POINTER(C.c_int64), P, P, P],
+        "pic_set_axis_hints": [P, I64, P, P, P],
         "pic_slabs_init": [C.POINTER(C.c_void_p), C.POINTER(pic_desc), I32, C.POINTER(C.c_int32), P],
         "pic_slabs_load_particles": [P, I64, P, P, P, P, P, P, I32],
         "pic_slabs_step": [P, I32],
@@ -305,6 +307,24 @@ class Simulation:
         S, sh = C.c_int32(), C.c_int32()
         check(self.L.pic_autotune(self.h, trial_steps, C.byref(S), C.byref(sh)))
         return {"sort_interval": S.value, "tile_shape": sh.value}
+
+    def axis_ties(self):
+        """The logged ties of the azimuth branch at the polar axis: dict of
+        step, id (int64) and sign (+1 / -1, the branch taken)."""
+        n = C.c_int64(0)
+        check(self.L.pic_get_axis_ties(self.h, C.byref(n), None, None, None))
+        out = {"step": np.empty(n.value, dtype=np.int64), "id": np.empty(n.value, dtype=np.int64),
+               "sign": np.empty(n.value, dtype=np.int32)}
+        if n.value:
+            check(self.L.pic_get_axis_ties(self.h, C.byref(n), *[C.c_void_p(out[k].ctypes.data)
+                                                                  for k in ("step", "id", "sign")]))
+        return out
+
+    def set_axis_hints(self, ties):
+        """Follow another run's branches at the ties it logged (pic_set_axis_hints)."""
+        arr = [np.ascontiguousarray(ties[k], dtype=dt) for k, dt in (("step", np.int64), ("id", np.int64),
+                                                                      ("sign", np.int32))]
+        check(self.L.pic_set_axis_hints(self.h, len(arr[0]), *[C.c_void_p(a.ctypes.data) for a in arr]))
 
     def launches(self):
         n = C.c_int64()

@@ -184,3 +184,38 @@ def test_total_fields_add_the_analytic_field_at_each_stagger(oracle_mod):
         np.testing.assert_array_equal(tot[c], f[c])
     # outside a component's range nothing is added
     assert np.array_equal(tot[0, N, :], f[0, N, :]) and np.array_equal(tot[1, :, M], f[1, :, M])
+
+
+def _axis_crosser(uph, hints=None):
+    """A particle 0.1 cell from the north axis moving straight towards and
+    past it (u_th < 0; it moves 0.16 cell of arc), with a tiny azimuthal
+    momentum uph; no fields."""
+    o = _o(nr=16, nth=64, th_map="linear", vacuum="none")
+    if hints is not None:
+        o.set_axis_hints(hints)
+    qw = 0.37
+    o.load([7.3], [0.1], [0.0], [-3.0], [uph], [qw])
+    o.step(1)
+    return o, o.flux()[2].sum() / qw
+
+
+def test_axis_crossing_tie_branch_and_hints(oracle_mod):
+    """R15: the move crosses the axis (the displaced point lies past it), so
+    the azimuth swept is within 2^-13 of +-pi and its sign follows u_ph: the
+    two branches put +1/2 and -1/2 of the charge through the meridional
+    half-plane.  Both are ties; a hint fixes the branch; a crossing whose
+    azimuth is farther from pi is no tie and ignores the table."""
+    for uph, half in ((1e-9, 0.5), (-1e-9, -0.5)):
+        o, f = _axis_crosser(uph)
+        assert o.axis_ties() == 1
+        assert f == pytest.approx(half, abs=1e-6)
+        assert 0.0 < o.particles()["x2"][0] < 0.1  # reflected through the axis to the other side
+    step0 = {"step": [0], "id": [0], "sign": [1]}
+    o, f = _axis_crosser(-1e-9, hints=step0)
+    assert o.axis_ties() == 1 and f == pytest.approx(0.5, abs=1e-6)
+    # a hint for another step or particle leaves the branch alone
+    o, f = _axis_crosser(-1e-9, hints={"step": [1, 0], "id": [0, 5], "sign": [1, 1]})
+    assert f == pytest.approx(-0.5, abs=1e-6)
+    # u_ph large enough that the sweep is pi - 1e-2: no tie, hints ignored
+    o, f = _axis_crosser(-0.05, hints=step0)
+    assert o.axis_ties() == 0 and f < -0.49
