@@ -135,3 +135,54 @@ def test_tile_shapes_agree(shape):
     s1.step(25)
     s2.step(25)
     assert np.array_equal(s1.fields(), s2.fields())
+
+
+def test_members_keep_their_own_sort_intervals():
+    """Members with sort intervals 5, 13 and 40 in one ensemble: each runs its
+    own schedule (the same kernels as its independent run, counted launch by
+    launch) and its result is bit-identical."""
+    from paper_1407_1810_gb300 import picsar as P
+
+    ens, ref = [], []
+    for m, S in ((0, 5), (1, 13), (2, 40)):
+        cfg = dict(_member_cfg(m), sort_interval=S)
+        s1, _, plasma, _ = setup(cfg)
+        s2, _, _, _ = setup(cfg, plasma=plasma)
+        ens.append(s1)
+        ref.append(s2)
+    l0 = [s.launches() for s in ens]
+    P.ensemble_step(ens, 60)
+    for s in ref:
+        s.step(60)
+    for k, (a, b) in enumerate(zip(ens, ref)):
+        assert a.launches() - l0[k] == b.launches() - l0[k], k
+        assert np.array_equal(a.fields(), b.fields()), k
+        assert a.moments()["step"] == 60
+
+
+def test_ensemble_member_against_the_oracle():
+    """One member of a batched FP32 ensemble, 100 steps, against the FP64
+    oracle run from the same state (following the member's branches at
+    axis-crossing ties): fields within the FP32 bar of 1e-5, live count within
+    the near-ties."""
+    import oracle as O
+
+    from paper_1407_1810_gb300 import picsar as P
+
+    from gpu_common import maxnorm_rel, rel_l2
+
+    O.build_oracle()
+    ens, oracles = [], []
+    for m in (4, 8, 9):
+        s, o, _, _ = setup(_member_cfg(m))
+        ens.append(s)
+        oracles.append(o)
+    P.ensemble_step(ens, 100)
+    s, o = ens[1], oracles[1]
+    o.set_axis_hints(s.axis_ties())
+    o.step(100)
+    fs, fo = s.fields(), o.fields()
+    assert rel_l2(fs, fo) < 1e-5
+    assert maxnorm_rel(fs, fo) < 1e-4
+    n = o.num_particles()
+    assert abs(s.moments()["live"] - n) <= max(1, 1e-4 * n)
