@@ -247,13 +247,13 @@ int pic_get_profile(pic_ctx *c, double *ms6, int64_t *steps);
 
 /* Ties of the azimuth branch at the polar axis (Sec. 3.3; the azimuthal flux
  * of a move is qw times the swept azimuth over 2 pi).  A move that carries a
- * particle across the polar axis sweeps an azimuth near +pi or -pi with the
- * sign of u_ph; when it lies within 2^-13 of +-pi (|D_ph| <= 2^-13 |P_x|,
- * P_x < 0 the displaced point's coordinate along the old cylindrical radius)
- * the branch is set by the rounding of a nearly vanishing u_ph, either branch
- * is a valid result, and the two differ by the particle's whole charge in the
- * azimuthal flux.  Every context counts its ties (pic_moments.axis_ties) and
- * logs the first 65536 as (step, id, sign = +1 or -1, the branch taken).
+ * particle across the polar axis (P_x < 0, the displaced point's coordinate
+ * along the old cylindrical radius) sweeps an azimuth whose sign is that of
+ * u_ph, and the two signs differ by up to 2 pi, i.e. by up to the particle's
+ * whole charge in the azimuthal flux.  When |u_ph| <= 2^-13 |u| the sign is
+ * set by the rounding of a nearly vanishing u_ph and either branch is a valid
+ * result.  Every context counts its ties (pic_moments.axis_ties) and logs the
+ * first 65536 as (step, id, sign = +1 or -1, the branch taken).
  *
  * pic_get_axis_ties: *n in: capacity of the host arrays; out: ties logged.
  * steps == NULL only queries *n.  signs may be NULL.

@@ -59,13 +59,14 @@
  *      charge, E = -grad Phi, Phi = -(Omega mu r0^2 / 3 r^3)(3 cos^2 th - 1),
  *      which matches the inside potential's l = 2 part at r0.
  *   R15 Ties of the azimuth branch (adjudication, not arithmetic): a move that
- *      crosses the polar axis sweeps an azimuth near +pi or -pi with the sign
- *      of u_ph (R4); when |Y| <= 2^-13 (-X) (X < 0, the displaced point's
- *      coordinate along the old cylindrical radius) the sign is set by the
- *      rounding of a nearly vanishing u_ph and both branches are valid.  Such
- *      ties are counted; a table of hints (step, id -> sign) from another run
- *      fixes the branch of the ties it lists, so a replay follows that run.
- *      Without hints every tie keeps atan2's own branch.
+ *      crosses the polar axis (X < 0, the displaced point's coordinate along
+ *      the old cylindrical radius) sweeps the azimuth atan2(Y, X) (R4), whose
+ *      sign is that of u_ph; the two signs differ by up to 2 pi.  When
+ *      |u_ph| <= 2^-13 |u| that sign is set by the rounding of a nearly
+ *      vanishing u_ph and both branches are valid.  Such ties are counted; a
+ *      table of hints (step, id -> sign) from another run fixes the branch of
+ *      the ties it lists, so a replay follows that run.  Without hints every
+ *      tie keeps atan2's own branch.
  */
 #include "picsar_oracle.h"
 
@@ -718,7 +719,7 @@ static void particle_step(orc_sim *s, int64_t k, double t, int *del) {
   double g = sqrt(1.0 + dot(u, u));
   double X = r * st + u[0] / g * s->p.dt, Y = u[1] / g * s->p.dt, Z = r * ct + u[2] / g * s->p.dt;
   double R = hypot(X, Y), phi = atan2(Y, X), rn = hypot(R, Z), thn = atan2(R, Z);
-  if (X < 0 && fabs(Y) <= -X / 8192.0) phi = tie_branch(s, s->id[k], phi); /* R15 */
+  if (X < 0 && u[1] * u[1] <= dot(u, u) / (8192.0 * 8192.0)) phi = tie_branch(s, s->id[k], phi); /* R15 */
   double cp = R > 0 ? X / R : 1.0, sp = R > 0 ? Y / R : 0.0;
   double ux = cp * u[0] + sp * u[1], uy = -sp * u[0] + cp * u[1], uz = u[2];
   double stn = rn > 0 ? R / rn : 0.0, ctn = rn > 0 ? Z / rn : 1.0;

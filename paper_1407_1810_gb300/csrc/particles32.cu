@@ -115,13 +115,11 @@ struct GlobAcc {  // global-memory accessors (particles outside the window)
 // cs - h 2^SPLIT is exact (Sterbenz).  Only FP32 adds and integer ops, no
 // 64-bit conversions.
 __device__ inline void split_fix(float cs, int &h, int &l) {
-  const float MAGIC = 12582912.0f;
-  const float hf = cs * (1.0f / (float)(1 << SPLIT));
-  const float hm = hf + MAGIC;
-  h = __float_as_int(hm) - 0x4B400000;
-  const float hr = hm - MAGIC;
-  const float lf = cs - hr * (float)(1 << SPLIT);
-  l = __float_as_int(lf + MAGIC) - 0x4B400000;
+  const float MAGIC = 12582912.0f, MAGIC_H = 3298534883328.0f;  // 1.5 2^23, 1.5 2^41 (ulp 2^SPLIT)
+  const float hm = __fadd_rn(cs, MAGIC_H);                        // cs rounded to a multiple of 2^18
+  h = __float_as_int(hm) - 0x54400000;
+  const float lf = __fsub_rn(cs, __fsub_rn(hm, MAGIC_H));       // exact
+  l = __float_as_int(__fadd_rn(lf, MAGIC)) - 0x4B400000;
 }
 
 template <class W>
@@ -411,7 +409,8 @@ __device__ inline bool step32(const Args32 &A, const W &w, int64_t k, uint32_t &
   // area weights at the midpoint of the grid path
   {
     float phi = atan2_small(Dp, Px);
-    if (Px < 0.f && fabsf(Dp) <= (float)AXIS_TIE * -Px) phi = axis_tie(A.ties, A.ids[k], phi);  // rare
+    if (Px < 0.f && pp * pp <= (float)(AXIS_TIE * AXIS_TIE) * (pr * pr + pt * pt + pp * pp))
+      phi = axis_tie(A.ties, A.ids[k], phi);  // rare: see AxisTies
     const float v = scale * phi * 0.15915494309189535f;
     const float mx = 0.5f * (dx + (float)kx + nx), my = 0.5f * (dy + (float)ky + ny);
     const float fx = floorf(mx), fy = floorf(my);
@@ -447,13 +446,9 @@ __device__ inline bool step32_global(const Args32 &A, float fs, int64_t k, uint3
 }
 
 template <int SPEC, class SW>
-__device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, const SW &sw,
-                               int wi_lo, int wi_hi, int wj_lo, int wj_hi, int &dead) {
-  // every load first: the free-slot test would otherwise put a second memory
-  // round trip behind the first
-  const float qw = P.qw[k];
-  uint32_t cell = P.cell[k];
-  float dx = P.dx[k], dy = P.dy[k], ur = P.ur[k], ut = P.ut[k], up = P.up[k];
+__device__ inline void process_v(const Args32 &A, Parts32 P, int64_t k, bool win, const SW &sw,
+                                 int wi_lo, int wi_hi, int wj_lo, int wj_hi, int &dead, const float qw,
+                                 uint32_t cell, float dx, float dy, float ur, float ut, float up) {
   if (qw == 0.f) return;
   const int ci = (int)(cell >> 16) - CELL_BIAS, cj = (int)(cell & 0xffffu);
   bool alive;
@@ -466,6 +461,14 @@ __device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, 
   P.dx[k] = dx; P.dy[k] = dy;
   P.ur[k] = ur; P.ut[k] = ut; P.up[k] = up;
 }
+
+template <int SPEC, class SW>
+__device__ inline void process(const Args32 &A, Parts32 P, int64_t k, bool win, const SW &sw,
+                               int wi_lo, int wi_hi, int wj_lo, int wj_hi, int &dead) {
+  process_v<SPEC>(A, P, k, win, sw, wi_lo, wi_hi, wj_lo, wj_hi, dead, P.qw[k], P.cell[k], P.dx[k], P.dy[k], P.ur[k],
+                  P.ut[k], P.up[k]);
+}
+
 
 // ---- the field window through the tensor memory accelerator ---------------
 // Each FP32 field is a 2-D tensor (LD columns x rows of the padded grid).  A
@@ -492,6 +495,14 @@ struct TileMaps {  // the six field tensors for the current tile shape (kernel p
 };
 
 __device__ inline uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// per-thread asynchronous copy of 4 bytes global -> shared (no registers held)
+__device__ inline void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ inline void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ inline void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ inline void tma_window(float *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
   asm volatile(
@@ -520,6 +531,7 @@ __global__ void __launch_bounds__(NT, 4) k_tiles32(Args32 A, Parts32 P, const __
   using BX_ = Box<TI, TJ>;
   constexpr int WI = BX_::WI, WJ = BX_::WJ, WN = BX_::WN, WB = BX_::WB, SLOT = BX_::SLOT;
   __shared__ __align__(128) float sbuf[BX_::SF + BX_::U];
+  __shared__ __align__(16) uint32_t spf[2][7][NT];  // each thread's next particle, copied ahead
   float *const sf = sbuf;                                      // 6 WN: the window
   float *const stage = sbuf + BX_::SF;                         // 6 SLOT: the boxes, first
   int *const shi = reinterpret_cast<int *>(sbuf + BX_::SF);    // 3 WN: then the accumulators
@@ -567,8 +579,28 @@ __global__ void __launch_bounds__(NT, 4) k_tiles32(Args32 A, Parts32 P, const __
     for (int e = threadIdx.x; e < 3 * WN; e += NT) { shi[e] = 0; slo[e] = 0; }
     __syncthreads();
     const SmemAcc<WJ, WN> sw{sf, shi, slo, srn, wi0, wj0, fs};
-    for (int64_t k = b0 + threadIdx.x; k < b1; k += NT)
-      process<SPEC>(A, P, k, true, sw, i0 - H, i0 + TI + H, j0 - H, j0 + TJ + H, dead);
+    {
+      const int t = threadIdx.x;
+      auto fetch = [&](int buf, int64_t k) {
+        cp_async4(&spf[buf][0][t], P.qw + k); cp_async4(&spf[buf][1][t], P.cell + k);
+        cp_async4(&spf[buf][2][t], P.dx + k); cp_async4(&spf[buf][3][t], P.dy + k);
+        cp_async4(&spf[buf][4][t], P.ur + k); cp_async4(&spf[buf][5][t], P.ut + k);
+        cp_async4(&spf[buf][6][t], P.up + k);
+      };
+      int64_t k = b0 + t;
+      if (k < b1) fetch(0, k);
+      cp_commit();
+      for (int buf = 0; k < b1; k += NT, buf ^= 1) {
+        if (k + NT < b1) fetch(buf ^ 1, k + NT);
+        cp_commit();
+        cp_wait<1>();  // this particle's copies (the next one's may still be in flight)
+        process_v<SPEC>(A, P, k, true, sw, i0 - H, i0 + TI + H, j0 - H, j0 + TJ + H, dead,
+                        __uint_as_float(spf[buf][0][t]), spf[buf][1][t], __uint_as_float(spf[buf][2][t]),
+                        __uint_as_float(spf[buf][3][t]), __uint_as_float(spf[buf][4][t]),
+                        __uint_as_float(spf[buf][5][t]), __uint_as_float(spf[buf][6][t]));
+      }
+      cp_wait<0>();
+    }
     if (dead) atomicAdd(&sdead, dead);
     __syncthreads();
     for (int e = threadIdx.x; e < WN; e += NT) {

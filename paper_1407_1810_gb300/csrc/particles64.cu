@@ -105,7 +105,8 @@ __global__ void __launch_bounds__(256) k_particles64(Grid G, Parts64 P, int64_t 
   const double X = r * st + u[0] * ig * G.dt, Y = u[1] * ig * G.dt, Z = r * ct + u[2] * ig * G.dt;
   const double R = hypot(X, Y), rn = hypot(R, Z), thn = atan2(R, Z);
   double phi = atan2(Y, X);
-  if (X < 0.0 && fabs(Y) <= AXIS_TIE * -X) phi = axis_tie(ties, P.id[k], phi);  // rare: see AxisTies
+  if (X < 0.0 && u[1] * u[1] <= (AXIS_TIE * AXIS_TIE) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]))
+    phi = axis_tie(ties, P.id[k], phi);  // rare: see AxisTies
   const double cp = R > 0.0 ? X / R : 1.0, sp = R > 0.0 ? Y / R : 0.0;
   const double ux = cp * u[0] + sp * u[1], uy = -sp * u[0] + cp * u[1], uz = u[2];
   const double stn = rn > 0.0 ? R / rn : 0.0, ctn = rn > 0.0 ? Z / rn : 1.0;

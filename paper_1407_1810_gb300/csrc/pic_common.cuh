@@ -217,13 +217,13 @@ __device__ inline void push(int pusher, T qmdt, const T E[3], const T B[3], T u[
 
 // ---- ties of the azimuth branch at the polar axis (Sec. 3.3, reading of the
 //      azimuthal flux) -------------------------------------------------------
-// A move that carries a particle across the polar axis sweeps an azimuth near
-// +pi or -pi, and the sign is that of u_ph.  When the sweep lies within
-// AXIS_TIE of +-pi (|Dp| <= AXIS_TIE |Px|, Px < 0 the displaced point's
-// coordinate along the old cylindrical radius) the sign is set by the
-// rounding of a nearly vanishing u_ph and either branch is a valid result;
-// the azimuthal flux of the two branches differs by the particle's whole
-// charge.  Such ties are counted and logged as (step, id, sign).  A table of
+// A move that carries a particle across the polar axis (Px < 0, the
+// displaced point's coordinate along the old cylindrical radius) sweeps an
+// azimuth atan2(Dp, Px) whose sign is that of u_ph, and the two signs differ
+// by up to 2 pi: the azimuthal flux jumps by up to the particle's whole
+// charge as u_ph passes through zero.  When |u_ph| <= AXIS_TIE |u| the sign is
+// set by the rounding of a nearly vanishing u_ph and either branch is a valid
+// result.  Such ties are counted and logged as (step, id, sign).  A table of
 // hints, taken from the log of another run, fixes the branch of the ties it
 // lists, so that a replay follows the run it is compared with.
 constexpr double AXIS_TIE = 1.0 / 8192;

@@ -49,6 +49,28 @@ def setup(cfg: dict, plasma: dict | None = None, precision: str | None = None, *
     return s, o, plasma, dt
 
 
+# element-wise bars (per-component max-norm relative to that component's
+# largest value) beside the relative L2 bars of the two paths
+MAX_FP64 = 1e-11
+MAX_FP32 = 1e-4
+
+
+def close(a, b, l2, mx):
+    """Both checks of stacked planes (fields or fluxes) at once: relative L2
+    below l2 and the per-component max-norm below mx."""
+    e2, em = rel_l2(a, b), maxnorm_rel(a, b)
+    assert e2 < l2, ("rel_l2", e2, l2)
+    assert em < mx, ("maxnorm", em, mx)
+    return e2, em
+
+
+def follow_ties(src, dst):
+    """dst (an oracle or a GPU context) takes src's branch at every
+    axis-crossing tie src logged (reading R15 of the oracle): a replay of src
+    then follows src where the sign of a vanishing u_ph is set by rounding."""
+    dst.set_axis_hints(src.axis_ties())
+
+
 def by_id(d):
     order = np.argsort(d["id"])
     return {k: v[order] for k, v in d.items()}

@@ -44,10 +44,16 @@ class FakeSim:
         return np.ones((6, 3, 3))
 
     def moments(self):
-        return {"gauss_residual": 0.0}
+        return {"gauss_residual": 0.0, "live": 1000, "axis_ties": 0}
 
     def close(self):
         pass
+
+    def axis_ties(self):
+        return {"step": np.zeros(0, np.int64), "id": np.zeros(0, np.int64), "sign": np.zeros(0, np.int32)}
+
+    def set_axis_hints(self, ties):
+        self.hints = ties
 
 
 def test_fp64_leg_reads_the_profile_before_disabling_it(monkeypatch):
@@ -66,7 +72,7 @@ def test_fp64_leg_reads_the_profile_before_disabling_it(monkeypatch):
     monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
     monkeypatch.setattr(torch.cuda, "empty_cache", lambda *a, **k: None)
     cfg = {"nr": 4, "nth": 4, "pairs_per_cell": 1, "T": 0.3, "seed": 0}
-    args = bench.parse(["--fp64-steps", "20"])
+    args = bench.parse(["--fp64-steps", "20", "--compare-steps", "30"])
 
     class _S:
         cuda_stream = 0

@@ -4,7 +4,11 @@ Both sides start from the same FP32-representable state.  Bar: cells and
 removals exact in one-step replay except particles whose coordinate lies
 within TAU = 2e-6 cell of a grid line (counted, must be <= 1e-4 of all);
 positions within 2e-6 cell; Gauss residual <= 1e-6; fields after 100 steps
-within 1e-5 relative L2 on every plasma.  The step forms each change of the
+within 1e-5 relative L2 on every plasma and within 1e-4 of each component's
+largest value element by element.  Where a particle crosses the polar axis
+with |u_ph| <= 2^-13 |u| the sign of the swept azimuth is set by rounding
+(a tie, reading R15 of the oracle); the oracle follows the GPU's logged
+branch there.  The step forms each change of the
 momentum (push, frame rotation) as an increment, so its FP32 rounding scales
 with the change rather than with |u|: on the small noisy monopole plasma the
 100-step field error is 3.6e-6 (it was 1.6e-5 when u was rounded through
@@ -16,7 +20,7 @@ import pytest
 import oracle as O
 from paper_1407_1810_gb300 import configs
 
-from gpu_common import KEYS, rel_l2, replay_compare_fp32, setup
+from gpu_common import KEYS, MAX_FP32, close, follow_ties, rel_l2, replay_compare_fp32, setup
 
 pytestmark = pytest.mark.gpu
 TAU = 2e-6
@@ -64,10 +68,11 @@ def test_one_step_replay(r_map, th_map):
     s.step(7)
     o2 = _replay(s, o, 7, n0)
     s.step(1)
+    follow_ties(s, o2)
     o2.step(1)
     _replay_compare(s, o2)
     # fluxes of the replayed step (fixed-point sums of FP32 terms)
-    assert rel_l2(s.flux(), o2.flux()) < 1e-5
+    close(s.flux(), o2.flux(), 1e-5, MAX_FP32)
     assert s.moments()["deleted"] >= 0
 
 
@@ -76,8 +81,9 @@ def test_monopole_100_steps_fields_and_gauss():
     s, o, plasma, dt = setup(cfg)
     o.gauss_snapshot()
     s.step(100)
+    follow_ties(s, o)
     o.step(100)
-    assert rel_l2(s.fields(), o.fields()) < FIELD_TOL
+    close(s.fields(), o.fields(), FIELD_TOL, MAX_FP32)
     m = s.moments()
     assert m["gauss_residual"] < 1e-6
     assert abs(m["live"] - o.num_particles()) <= max(1, 1e-4 * o.num_particles())
@@ -91,8 +97,9 @@ def test_rotator_injection_filter_fp32(th_map):
     s, o, plasma, dt = setup(cfg)
     o.gauss_snapshot()
     s.step(100)
+    follow_ties(s, o)
     o.step(100)
-    assert rel_l2(s.fields(), o.fields()) < FIELD_TOL
+    close(s.fields(), o.fields(), FIELD_TOL, MAX_FP32)
     m, cnt = s.moments(), o.counters()
     assert m["injected"] == cnt["injected"]
     assert abs(m["live"] - cnt["live"]) <= 2
@@ -106,8 +113,9 @@ def test_window_and_global_paths_agree(sort_interval):
     cfg = _cfg(T=1.0, sort_interval=sort_interval)
     s, o, plasma, dt = setup(cfg)
     s.step(40)
+    follow_ties(s, o)
     o.step(40)
-    assert rel_l2(s.fields(), o.fields()) < FIELD_TOL
+    close(s.fields(), o.fields(), FIELD_TOL, MAX_FP32)
 
 
 def test_window_and_global_paths_are_bit_identical():
@@ -141,8 +149,9 @@ def test_fp32_against_fp64_gpu_path():
     s32, o, plasma, dt = setup(cfg)
     s64, _, _, _ = setup(cfg, plasma=plasma, precision="fp64")
     s32.step(100)
+    follow_ties(s32, s64)
     s64.step(100)
-    assert rel_l2(s32.fields(), s64.fields()) < FIELD_TOL
+    close(s32.fields(), s64.fields(), FIELD_TOL, MAX_FP32)
 
 
 def test_fixed_point_unit_follows_the_charges():
@@ -197,13 +206,15 @@ def test_specialised_monopole_kernel_replay_and_30_steps():
     s.step(7)
     o2 = _replay(s, o, 7, n0)
     s.step(1)
+    follow_ties(s, o2)
     o2.step(1)
     _replay_compare(s, o2)
-    assert rel_l2(s.flux(), o2.flux()) < 1e-5
+    close(s.flux(), o2.flux(), 1e-5, MAX_FP32)
     s2, o3, _, _ = setup(cfg, plasma=plasma)
     s2.step(30)
+    follow_ties(s2, o3)
     o3.step(30)
-    assert rel_l2(s2.fields(), o3.fields()) < FIELD_TOL
+    close(s2.fields(), o3.fields(), FIELD_TOL, MAX_FP32)
     assert s2.moments()["gauss_residual"] < 1e-6
 
 
@@ -212,8 +223,9 @@ def test_specialised_rotator_kernel_injection_filter():
     s, o, plasma, dt = setup(cfg)
     o.gauss_snapshot()
     s.step(50)
+    follow_ties(s, o)
     o.step(50)
-    assert rel_l2(s.fields(), o.fields()) < FIELD_TOL
+    close(s.fields(), o.fields(), FIELD_TOL, MAX_FP32)
     m, cnt = s.moments(), o.counters()
     assert m["injected"] == cnt["injected"] > 0
     assert abs(m["live"] - cnt["live"]) <= 2

@@ -1,7 +1,8 @@
 """GPU parity of the plain FP64 path against the FP64 oracle (through the C-ABI).
 
 Bar (FP64 path): fields, fluxes and momenta within 1e-12 relative after 100
-steps; particle counts, cells, injections and removals exact.
+steps (relative L2; element by element within 1e-11 of each component's
+largest value); particle counts, cells, injections and removals exact.
 """
 import numpy as np
 import pytest
@@ -9,7 +10,7 @@ import pytest
 import oracle as O
 from paper_1407_1810_gb300 import configs
 
-from gpu_common import KEYS, by_id, rel_l2, setup
+from gpu_common import KEYS, MAX_FP64, by_id, close, follow_ties, rel_l2, setup
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -53,10 +54,11 @@ def test_monopole_64x64_100_steps():
     assert len(plasma["x1"]) == 98304
     o.gauss_snapshot()
     s.step(cfg["steps"])
+    follow_ties(s, o)
     o.step(cfg["steps"])
     assert o.error() == 0
-    assert rel_l2(s.fields(), o.fields()) < TOL
-    assert rel_l2(s.flux(), o.flux()) < TOL
+    close(s.fields(), o.fields(), TOL, MAX_FP64)
+    close(s.flux(), o.flux(), TOL, MAX_FP64)
     m = s.moments()
     cnt = o.counters()
     assert m["live"] == cnt["live"] and m["deleted"] == cnt["deleted"]
@@ -78,8 +80,9 @@ def test_rotator_injection_filter(pusher, th_map):
     o.gauss_snapshot()
     for _ in range(3):
         s.step(20)
+        follow_ties(s, o)
         o.step(20)
-        assert rel_l2(s.fields(), o.fields()) < TOL
+        close(s.fields(), o.fields(), TOL, MAX_FP64)
     cnt, m = o.counters(), s.moments()
     assert cnt["injected"] > 0 and cnt["deleted"] > 0
     assert m["injected"] == cnt["injected"] and m["deleted"] == cnt["deleted"] and m["live"] == cnt["live"]
@@ -100,9 +103,10 @@ def test_one_step_replay_from_gpu_state():
     m = s.moments()
     o2.set_clock(15, o.counters()["next_id"] + 15 * 2 * 2 * 32)
     s.step(1)
+    follow_ties(s, o2)
     o2.step(1)
-    assert rel_l2(s.flux(), o2.flux()) < TOL
-    assert rel_l2(s.fields(), o2.fields()) < TOL
+    close(s.flux(), o2.flux(), TOL, MAX_FP64)
+    close(s.fields(), o2.fields(), TOL, MAX_FP64)
     _compare_particles(s, o2)
 
 

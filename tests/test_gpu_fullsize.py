@@ -14,6 +14,9 @@ the next step on both sides:
     one by one.  Then the FP32 path against the FP64 GPU path (itself held
     to the oracle) over 100 steps at the same size: fields and fluxes
     within 1e-5.
+  - the same 4096^2 workload on both paths for 100 steps, whole grid.
+In every comparison the second run follows the first run's branches at its
+axis-crossing ties (reading R15 of the oracle).
   - 4096 x 4096 monopole, 1e9 particles, FP32 path (the benchmark's
     workload): a whole-step oracle replay would take minutes, so the oracle
     replays every 1000th particle on the GPU's own fields, compared one by
@@ -26,7 +29,7 @@ import pytest
 import oracle as O
 from paper_1407_1810_gb300 import configs, synthetic, workload
 
-from gpu_common import KEYS, by_id, rel_l2, replay_compare_fp32
+from gpu_common import KEYS, MAX_FP32, MAX_FP64, by_id, close, follow_ties, rel_l2, replay_compare_fp32
 
 pytestmark = pytest.mark.gpu
 TAU = 2e-6
@@ -83,6 +86,7 @@ def _full_replay(cfg, warm, precision=None):
     nid = _next_id(cfg, n, warm)
     o.set_clock(warm, nid)
     sim.step(1)
+    follow_ties(sim, o)
     assert o.step(1) == 0
     return sim, o, m0, nid
 
@@ -97,8 +101,8 @@ def _every(d, stride, below=None):
 def test_rotator_512_fp64_full_step_replay():
     cfg = dict(configs.CONFIGS["rotator-512x512"])
     sim, o, m0, nid = _full_replay(cfg, warm=15)
-    assert rel_l2(sim.flux(), o.flux()) < 1e-12
-    assert rel_l2(sim.fields(), o.fields()) < 1e-12
+    close(sim.flux(), o.flux(), 1e-12, MAX_FP64)
+    close(sim.fields(), o.fields(), 1e-12, MAX_FP64)
     m, c = sim.moments(), o.counters()
     assert m["live"] == c["live"]
     assert m["deleted"] - m0["deleted"] == c["deleted"]
@@ -121,8 +125,8 @@ def test_rotator_512_fp64_full_step_replay():
 def test_rotator_1024_fp32_full_step_replay():
     cfg = dict(configs.CONFIGS["rotator-1024x1024"])
     sim, o, m0, nid = _full_replay(cfg, warm=10)
-    assert rel_l2(sim.flux(), o.flux()) < 1e-5
-    assert rel_l2(sim.fields(), o.fields()) < 1e-5
+    close(sim.flux(), o.flux(), 1e-5, MAX_FP32)
+    close(sim.fields(), o.fields(), 1e-5, MAX_FP32)
     m, c = sim.moments(), o.counters()
     # removals decided within rounding of the boundary may differ: near-ties only
     assert abs((m["deleted"] - m0["deleted"]) - c["deleted"]) <= max(1, 1e-4 * c["live"])
@@ -131,13 +135,15 @@ def test_rotator_1024_fp32_full_step_replay():
     replay_compare_fp32(_every(g, 64, nid), _every(r, 64, nid), TAU)
     # injected this step: same ids, positions and signs; the charges follow
     # the surface E_r, which on the FP32 path carries the deposit's rounding:
-    # held to the FP32 field bar
+    # held to the FP32 field bar relative to the largest injected charge, as
+    # the field bar is relative to the field's size (per particle, cells whose
+    # surface charge passes through zero near the equator would divide by ~0)
     gi, ri = by_id(_every(g, 1, None)), by_id(_every(r, 1, None))
     gi = {k: v[gi["id"] >= nid] for k, v in gi.items()}
     ri = {k: v[ri["id"] >= nid] for k, v in ri.items()}
     assert np.array_equal(gi["id"], ri["id"])
     assert np.array_equal(gi["x2"], ri["x2"])
-    assert np.max(np.abs(gi["qw"] - ri["qw"]) / np.abs(ri["qw"])) < 1e-5
+    assert np.max(np.abs(gi["qw"] - ri["qw"])) < 1e-5 * np.max(np.abs(ri["qw"]))
     assert m["gauss_residual"] <= GAUSS_FP32, m["gauss_residual"]
     sim.close()
 
@@ -167,14 +173,13 @@ def test_rotator_1024_fp32_against_fp64_100_steps():
     _load_fp32_state(s64, cfg, qw)
     torch.cuda.synchronize()
     s32.step(100)
+    follow_ties(s32, s64)
     s64.step(100)
     m32, m64 = s32.moments(), s64.moments()
     assert m32["gauss_residual"] <= GAUSS_FP32, m32["gauss_residual"]
     assert m64["gauss_residual"] <= GAUSS_FP64, m64["gauss_residual"]
-    e = rel_l2(s32.fields(), s64.fields())
-    assert e < 1e-5, e
-    fx = rel_l2(s32.flux(), s64.flux())
-    assert fx < 1e-5, fx
+    close(s32.fields(), s64.fields(), 1e-5, MAX_FP32)
+    close(s32.flux(), s64.flux(), 1e-5, MAX_FP32)
     assert abs(m32["live"] - m64["live"]) <= 1e-5 * m64["live"]
     s64.close()
     s32.close()
@@ -196,33 +201,37 @@ def _sample(sim, stride, keep=None):
     return out
 
 
-def test_monopole_4096_fp32_against_fp64_away_from_the_axis():
-    """Both paths for 22 steps from one FP32-rounded state at full size.  At
-    least 32 cells from the poles the fields agree to 1e-5 (measured 1.4e-6).
-    Nearer the poles an axis crossing whose u_ph lies within rounding of zero
-    sweeps +pi on one path and -pi on the other, a jump of the azimuthal
-    deposit that the tiny polar cells magnify (measured 3.9e-3 over the whole
-    grid); Gauss's law holds on both."""
+def test_monopole_4096_fp32_against_fp64_100_steps():
+    """The benchmark's workload on both paths for 100 steps from one
+    FP32-rounded state, on the whole grid, the FP64 run following the FP32
+    run's branches at its axis-crossing ties (|u_ph| <= 2^-13 |u|, where the
+    sign of the swept azimuth is set by rounding): fields within the FP32 bar
+    of 1e-5 relative L2 and 1e-4 element by element; ties at most 1e-4 of the
+    particle-steps; equal live counts; Gauss's law on both."""
     import gc
 
     import torch
 
     cfg = dict(configs.CONFIGS["monopole-4096x4096"])
     n = cfg["nr"] * cfg["nth"] * cfg["pairs_per_cell"] * 2
-    out = {}
-    for prec in ("fp64", "fp32"):
+    out, ties = {}, None
+    for prec in ("fp32", "fp64"):
         sim, qw, _, _ = workload.make_sim(cfg, prec, capacity=n + (1 << 20))
         workload.load_plasma(sim, cfg, qw, "cuda", fp32_state=True)
-        sim.step(22)
+        if ties is not None:
+            sim.set_axis_hints(ties)
+        sim.step(100)
         out[prec] = (sim.fields(), sim.moments())
+        if ties is None:
+            ties = sim.axis_ties()
         sim.close()
         del sim
         gc.collect()
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
     (f32, m32), (f64, m64) = out["fp32"], out["fp64"]
-    band = slice(32, cfg["nth"] + 1 - 32)
-    assert rel_l2(f32[:, :, band], f64[:, :, band]) < 1e-5
+    close(f32, f64, 1e-5, MAX_FP32)
+    assert m32["axis_ties"] == len(ties["id"]) <= 1e-4 * n * 100
     assert m32["live"] == m64["live"]
     assert m32["gauss_residual"] <= GAUSS_FP32 and m64["gauss_residual"] <= GAUSS_FP64
 

@@ -200,11 +200,11 @@ def _axis_crosser(uph, hints=None):
 
 
 def test_axis_crossing_tie_branch_and_hints(oracle_mod):
-    """R15: the move crosses the axis (the displaced point lies past it), so
-    the azimuth swept is within 2^-13 of +-pi and its sign follows u_ph: the
-    two branches put +1/2 and -1/2 of the charge through the meridional
-    half-plane.  Both are ties; a hint fixes the branch; a crossing whose
-    azimuth is farther from pi is no tie and ignores the table."""
+    """R15: the move crosses the axis (the displaced point lies past it) with
+    |u_ph| far below 2^-13 |u|, so the swept azimuth is +-pi with the sign of
+    u_ph: the two branches put +1/2 and -1/2 of the charge through the
+    meridional half-plane.  Both are ties; a hint fixes the branch; a
+    crossing with a larger u_ph is no tie and ignores the table."""
     for uph, half in ((1e-9, 0.5), (-1e-9, -0.5)):
         o, f = _axis_crosser(uph)
         assert o.axis_ties() == 1
@@ -216,6 +216,6 @@ def test_axis_crossing_tie_branch_and_hints(oracle_mod):
     # a hint for another step or particle leaves the branch alone
     o, f = _axis_crosser(-1e-9, hints={"step": [1, 0], "id": [0, 5], "sign": [1, 1]})
     assert f == pytest.approx(-0.5, abs=1e-6)
-    # u_ph large enough that the sweep is pi - 1e-2: no tie, hints ignored
+    # |u_ph| = 0.017 |u|: no tie, hints ignored
     o, f = _axis_crosser(-0.05, hints=step0)
     assert o.axis_ties() == 0 and f < -0.49
