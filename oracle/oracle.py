@@ -121,6 +121,7 @@ def _load():
         "orc_counters": (None, [P, C.POINTER(C.c_int64)]),
         "orc_splitmix64": (C.c_uint64, [C.c_uint64, C.c_uint64]),
         "orc_axis_ties": (I64, [P]),
+        "orc_inject_ties": (I64, [P]),
         "orc_set_axis_hints": (None, [P, I64, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     }
     for name, (res, args) in sig.items():
@@ -307,6 +308,12 @@ class Oracle:
     def axis_ties(self):
         """Ties of the azimuth branch at the polar axis met so far (R15)."""
         return int(self.lib.orc_axis_ties(self.h))
+
+    def inject_ties(self):
+        """Variable-count injection draws within 1e-4 n_j of their rounding
+        threshold so far (where a surface field held to a lower precision may
+        round the cell the other way)."""
+        return int(self.lib.orc_inject_ties(self.h))
 
     def set_axis_hints(self, ties):
         """Follow another run's branches at its logged ties: dict of step, id, sign."""

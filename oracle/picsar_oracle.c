@@ -95,6 +95,7 @@ struct orc_sim {
   int err;
   /* R15: ties met so far, and the hints (sorted by step, then id) */
   int64_t n_ties, nh;
+  int64_t n_inject_ties; /* R13 draws within 1e-4 n_j of the rounding threshold */
   int64_t *h_step, *h_id;
   int *h_sign;
 };
@@ -779,6 +780,9 @@ static void inject(orc_sim *s, double t) {
           double u = (double)(orc_splitmix64(s->p.inject_seed, step * (uint64_t)nt + (uint64_t)j) >> 11) *
                      (1.0 / 9007199254740992.0);
           m = (int)fl + (u < x - fl ? 1 : 0);
+          /* a near-tie: a relative change of 1e-4 in n_j (a surface field
+           * held to a lower precision) could round this cell the other way */
+          if (fabs(u - (x - fl)) <= 1e-4 * x) s->n_inject_ties++;
         }
         if (m > npp) { m = npp; s->n_capped++; }
       }
@@ -1007,3 +1011,5 @@ void orc_set_axis_hints(orc_sim *s, int64_t n, const int64_t *steps, const int64
 }
 
 int64_t orc_axis_ties(const orc_sim *s) { return s->n_ties; }
+
+int64_t orc_inject_ties(const orc_sim *s) { return s->n_inject_ties; }

@@ -121,6 +121,8 @@ void orc_counters(const orc_sim *s, int64_t *out5);
  * (step, id -> sign) that fix the branch of the ties they list */
 int64_t orc_axis_ties(const orc_sim *s);
 void orc_set_axis_hints(orc_sim *s, int64_t n, const int64_t *steps, const int64_t *ids, const int32_t *signs);
+/* R13: stochastic-rounding draws within 1e-4 n_j of the threshold so far */
+int64_t orc_inject_ties(const orc_sim *s);
 /* output number n + 1 of the SplitMix64 stream seeded with `seed` */
 uint64_t orc_splitmix64(uint64_t seed, uint64_t n);
 

@@ -83,10 +83,13 @@ def test_variable_count_injection_against_oracle(precision):
         assert np.array_equal(g["qw"], r["qw"])  # every injected charge is exactly -+q
         assert m["gauss_residual"] < 1e-11
     else:
-        # the surface E_r carries the FP32 path's rounding (~1e-7): a cell whose
-        # expected count lies that close to the uniform draw may round the
-        # other way; over 60 steps x 32 cells none is expected
-        assert abs(m["injected"] - c["injected"]) <= 2 and abs(m["inject_capped"] - c["capped"]) <= 1
+        # the surface E_r carries the FP32 path's rounding: a cell whose
+        # expected count n_j lies within 1e-4 n_j of the uniform draw (a
+        # near-tie the oracle counts) may round the other way, changing the
+        # count by one pair; every other decision is exact
+        ties = o.inject_ties()
+        assert abs(m["injected"] - c["injected"]) <= 2 * ties, (m["injected"], c["injected"], ties)
+        assert abs(m["inject_capped"] - c["capped"]) <= ties
         assert m["gauss_residual"] < 1e-6
     d = s.particles()
     q = cfg["inject_q"] if precision == "fp64" else float(np.float32(cfg["inject_q"]))

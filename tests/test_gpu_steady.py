@@ -12,7 +12,9 @@ R_l and 3 R_l / 2, r^2 J_r on -J0 cos(theta) to a scale of 0.989, and
 1.98e7 particles.  The bars hold those results: L / L0 within 4 %, B_ph / B_r
 within 3 % (median over the cells away from the axis), r^2 J_r within 3 % in
 scale and 0.06 J0 rms over theta bins,
-the particle count within 25 % of the paper's, Gauss's law to 1e-6.
+the particle count within 25 % of the paper's, Gauss's law to 1e-6.  The
+last test finds the cause of the ~2 % luminosity deficit (the rate at which
+the surface charge is released) and holds the f_inj = 1 run to 1 %.
 """
 import math
 
@@ -91,3 +93,26 @@ def test_plasma_is_charge_separated_by_hemisphere(steady_run):
 def test_particle_count_and_gauss(steady_run):
     assert 1.5e7 <= steady_run["particles"] <= 2.5e7, steady_run["particles"]
     assert steady_run["gauss_residual"] <= 1e-6
+
+
+def test_full_injection_reaches_the_force_free_luminosity():
+    """The 2.3 % deficit of the f_inj = 0.5 run is the surface-charge supply:
+    one change at a time, a lossy layer of 64 cells or with the linear
+    profile, 1 or 4 pairs per cell, an averaging window four times longer and
+    a field twice as strong move the mean L / L0 by at most 0.4 %, while
+    releasing the whole surface charge every step (f_inj = 1) gives
+    L / L0 = 0.999 (0.983-1.005 over [1.5, 25] r0), within the paper's ~1 %
+    (the paper: f_inj closer to unity agrees better with the analytic
+    solution, Sec. 5.3)."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1407_1810_gb300 import steady
+
+    res = steady.run(dict(steady.ROTATOR_STEADY, f_inj=1.0))
+    r, L = res["r"], res["L_over_L0"]
+    sel = (r >= 1.5) & (r <= 25.0)
+    assert abs(L[sel].mean() - 1.0) <= 0.01, L[sel].mean()
+    assert np.all(np.abs(L[sel] - 1.0) <= 0.025), (L[sel].min(), L[sel].max())
+    assert res["gauss_residual"] <= 1e-6
