@@ -264,6 +264,17 @@ int pic_get_profile(pic_ctx *c, double *ms6, int64_t *steps);
 int pic_get_axis_ties(pic_ctx *c, int64_t *n, int64_t *steps, int64_t *ids, int32_t *signs);
 int pic_set_axis_hints(pic_ctx *c, int64_t n, const int64_t *steps, const int64_t *ids, const int32_t *signs);
 
+/* Failure detection without a fault: the device-side waits of the library
+ * (the tile kernel's wait for its field window, Sec. 3 of the design's
+ * hot path) poll a bounded number of times and then latch PIC_ETIMEOUT
+ * instead of hanging.  This runs that wait on its own in one small kernel on
+ * `stream`: with arrive_first = 0 nothing completes the awaited phase, the
+ * wait gives up after `polls` polls and the call returns PIC_ETIMEOUT; with
+ * arrive_first = 1 the phase completes first and the call returns PIC_OK.
+ * Either way the kernel ends and no context is affected.  The paper has no
+ * counterpart; it serves callers and tests that check the failure path. */
+int pic_wait_selftest(int64_t polls, int32_t arrive_first, void *stream);
+
 /* Number of kernels this context has launched so far (every launch of the
  * library's own kernels, all phases); *n receives the count. */
 int pic_get_launches(pic_ctx *c, int64_t *n);

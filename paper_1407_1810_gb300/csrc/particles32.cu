@@ -526,6 +526,24 @@ __device__ inline bool window_wait(uint64_t *bar, long long limit) {
   return false;
 }
 
+// Self-test of the bounded wait above: thread 0 of a one-warp block arms an
+// mbarrier for 16 bytes that no copy will deliver (arrive_first = 0) or
+// completes its phase itself first (arrive_first = 1), then waits at most
+// `limit` polls; on giving up it sets ERR_TIMEOUT, as the tile kernel does.
+// Nothing is in flight, so the block can leave after a timeout.
+__global__ void k_wait_selftest(long long limit, int arrive_first, int *err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (arrive_first) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+  } else {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)), "r"(16u) : "memory");
+  }
+  if (!window_wait(&bar, limit)) atomicOr(err, ERR_TIMEOUT);
+}
+
 template <int TI, int TJ, int SPEC>
 __global__ void __launch_bounds__(NT, 4) k_tiles32(Args32 A, Parts32 P, const __grid_constant__ TileMaps maps) {
   using BX_ = Box<TI, TJ>;
@@ -937,6 +955,32 @@ void particles32(pic_ctx *c, double t) {
   else if (spec == SPEC_ROTATOR) launch_tiles<SPEC_ROTATOR>(c, A, blocks);
   else launch_tiles<SPEC_GENERIC>(c, A, blocks);
 }
+
+}  // namespace pic
+
+// The bounded device-side wait of the tile kernel, exercised on its own (see
+// include/picsar.h): PIC_ETIMEOUT when the wait gave up, PIC_OK when it saw
+// its phase complete.
+extern "C" int pic_wait_selftest(int64_t polls, int32_t arrive_first, void *stream) {
+  if (polls < 1) return pic_fail(PIC_EINVAL, "polls must be >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  int *d = nullptr;
+  PIC_CUDA(cudaMalloc((void **)&d, sizeof(int)));
+  int h = 0;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    pic::k_wait_selftest<<<1, 32, 0, st>>>((long long)polls, arrive_first ? 1 : 0, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return pic_cuda_check(e, "wait self-test");
+  if (h & pic::ERR_TIMEOUT) return pic_fail(PIC_ETIMEOUT, "the bounded wait gave up (as intended when nothing arrives)");
+  return PIC_OK;
+}
+
+namespace pic {
 
 void flux_from_acc(pic_ctx *c) {
   const Grid &G = c->G;

@@ -30,7 +30,7 @@ EXPORTS = ["pic_init_grid", "pic_load_particles", "pic_step", "pic_get_fields", 
            "pic_get_particles", "pic_get_particles_noalloc", "pic_get_live", "pic_get_moments", "pic_get_luminosity",
            "pic_gauss_snapshot", "pic_set_clock", "pic_profile",
            "pic_get_profile", "pic_get_launches", "pic_ensemble_step", "pic_autotune", "pic_destroy", "pic_last_error",
-           "pic_struct_sizes", "pic_get_charge", "pic_grid_coords", "pic_get_axis_ties", "pic_set_axis_hints",
+           "pic_struct_sizes", "pic_get_charge", "pic_grid_coords", "pic_get_axis_ties", "pic_set_axis_hints", "pic_wait_selftest",
            "pic_slabs_init", "pic_slabs_load_particles", "pic_slabs_step", "pic_slabs_get_fields",
            "pic_slabs_get_flux", "pic_slabs_get_particles", "pic_slabs_get_moments", "pic_slabs_destroy"]
 
@@ -99,6 +99,7 @@ def lib():
         "pic_autotune": [P, I32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
         "pic_destroy": [P],
         "pic_get_axis_ties": [P, C.POINTER(C.c_int64), P, P, P],
+        "pic_wait_selftest": [I64, I32, P],
         "pic_set_axis_hints": [P, I64, P, P, P],
         "pic_slabs_init": [C.POINTER(C.c_void_p), C.POINTER(pic_desc), I32, C.POINTER(C.c_int32), P],
         "pic_slabs_load_particles": [P, I64, P, P, P, P, P, P, I32],
@@ -408,6 +409,11 @@ class Slabs:
         m = pic_moments()
         check(self.L.pic_slabs_get_moments(self.h, C.byref(m)))
         return {k: getattr(m, k) for k, _ in pic_moments._fields_}
+
+
+def wait_selftest(polls, arrive_first, stream=0):
+    """Return code of pic_wait_selftest (PIC_ETIMEOUT or PIC_OK expected)."""
+    return lib().pic_wait_selftest(polls, 1 if arrive_first else 0, C.c_void_p(stream))
 
 
 def ensemble_step(sims, nsteps):
