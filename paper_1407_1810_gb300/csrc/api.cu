@@ -1046,22 +1046,20 @@ extern "C" int pic_ensemble_step(pic_ctx *const *ctxs, int32_t n, int32_t nsteps
   // members' own streams finish their earlier work before the first graph
   for (int k = 0; k < n; ++k) PIC_CUDA(cudaStreamSynchronize(ctxs[k]->stream));
   cudaGraphExec_t exec = nullptr;
-  int err = PIC_OK;
-  // Each member advances on its own schedule: a graph holds, for every
-  // member, its steps up to its own next sort (or to the end), so members
-  // with longer sort intervals take longer branches and sort less often.
-  std::vector<int> done(n, 0), blk(n, 0);
-  for (;;) {
-    bool any = false;
+  int err = PIC_OK, done = 0;
+  // A graph holds every member's steps up to the next sort of any member, so
+  // each graph keeps all members on parallel branches; a member sorts only
+  // when its own interval comes due.  (Letting each member's branch run to its
+  // own next sort measured 13 % slower on the 64-member ensemble: the later
+  // graphs hold fewer members.)
+  while (done < nsteps && !err) {
+    int block = nsteps - done;
     for (int k = 0; k < n; ++k) {
       pic_ctx *c = ctxs[k];
-      blk[k] = std::min(nsteps - done[k], std::max(1, c->d.sort_interval - c->steps_since_sort));
-      any = any || blk[k] > 0;
+      block = std::min(block, std::max(1, c->d.sort_interval - c->steps_since_sort));
     }
-    if (!any || err) break;
     for (int k = 0; k < n && !err; ++k) {
-      if (blk[k] == 0) continue;
-      err = prepare_steps(ctxs[k], blk[k]);
+      err = prepare_steps(ctxs[k], block);
       if (!err) cudaStreamSynchronize(ctxs[k]->stream);
     }
     if (err) break;
@@ -1071,14 +1069,13 @@ extern "C" int pic_ensemble_step(pic_ctx *const *ctxs, int32_t n, int32_t nsteps
     cudaError_t ce = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
     if (ce == cudaSuccess) ce = cudaEventRecord(fork, origin);
     for (int k = 0; k < n && ce == cudaSuccess; ++k) {
-      if (blk[k] == 0) continue;
       pic_ctx *c = ctxs[k];
       ce = cudaStreamWaitEvent(br[k], fork, 0);
       own[k] = c->stream;
       prof[k] = c->prof;
       c->stream = br[k];
       c->prof = false;
-      for (int s = 0; s < blk[k]; ++s) step_body(c);
+      for (int s = 0; s < block; ++s) step_body(c);
       c->stream = own[k];
       c->prof = prof[k];
       if (ce == cudaSuccess) ce = cudaEventRecord(join[k], br[k]);
@@ -1103,10 +1100,9 @@ extern "C" int pic_ensemble_step(pic_ctx *const *ctxs, int32_t n, int32_t nsteps
     }
     if (graph) cudaGraphDestroy(graph);
     if (ce != cudaSuccess) { err = pic_cuda_check(ce, "ensemble graph"); break; }
+    done += block;
     for (int k = 0; k < n && !err; ++k) {
-      if (blk[k] == 0) continue;
       pic_ctx *c = ctxs[k];
-      done[k] += blk[k];
       cudaStreamWaitEvent(c->stream, after, 0);
       if (c->steps_since_sort >= c->d.sort_interval) err = compact(c);
     }
