@@ -280,13 +280,31 @@ int pic_wait_selftest(int64_t polls, int32_t arrive_first, void *stream);
 int pic_get_launches(pic_ctx *c, int64_t *n);
 
 /* Advance n independent contexts by nsteps each, batched (an ensemble of
- * independent simulations): the members' steps are captured into one CUDA
- * graph, each member on its own parallel branch with its own kernels and
- * grid, and the graph is launched once per block of steps; a member's tile
- * sort (FP32) or compaction (FP64) runs between graphs when its own sort
- * interval comes due.  All contexts must be on one device; each member's own
- * stream waits for the graph.  Errors latched in any member are returned. */
-int pic_ensemble_step(pic_ctx *const *ctxs, int32_t n, int32_t nsteps);
+ * independent simulations with uneven grids and particle counts).
+ *
+ * All FP32 members: each phase of a step is ONE kernel launch over the blocks
+ * of every member that takes part in it -- the tile kernel once per tile
+ * shape and specialisation present, then the flux conversion, each filter
+ * pass, the three Yee sub-steps, the lossy layer, the axis ghosts and FP32
+ * copies, and the injection phases -- with the members' arguments for each
+ * step in a device table; the steps up to the next sort of any member are
+ * captured into one CUDA graph, launched once.  Each member's tile sort runs
+ * between graphs when its own sort interval comes due, so every member takes
+ * the same steps and sorts as in its own pic_step run, with bit-identical
+ * results.
+ *
+ * Any FP64 member: every member's steps are captured into the graph on a
+ * parallel branch of their own (one kernel launch per phase per member).
+ *
+ * ctxs: n distinct contexts on one device (host array of handles, read during
+ * the call only).  kernels: may be NULL; receives the number of kernel
+ * launches the call enqueued (graph kernel nodes and sorts).  Each member's
+ * own launch count (pic_get_launches) advances by the launches its own
+ * pic_step run would take: a batched launch counts once for every member it
+ * serves.  Each member's own stream waits for the graph.  Errors: PIC_EINVAL
+ * (NULL or repeated members, several devices, nsteps < 0), PIC_ENOMEM,
+ * PIC_ECUDA; errors latched in any member are returned. */
+int pic_ensemble_step(pic_ctx *const *ctxs, int32_t n, int32_t nsteps, int64_t *kernels);
 
 /* Pick the FP32 path's tile shape and sort interval by measurement: every
  * candidate (3 tile shapes x sort intervals 5, 10, 20, 40) runs trial_steps

@@ -1,6 +1,7 @@
 // api.cu -- the C-ABI of include/picsar.h: context set-up, the metric tables,
 // particle loading, the step sequence and the getters.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -481,7 +482,8 @@ static int alloc_bins(pic_ctx *c, int shape) {
   const int64_t nblk = T.nbins / SCAN_CHUNK + 2;
   int e;
   if ((e = dalloc(&T.start, (size_t)T.nbins + 1)) || (e = dalloc(&T.cursor, (size_t)T.nbins + 1)) ||
-      (e = dalloc(&T.bsum, 2 * (size_t)nblk)))
+      (e = dalloc(&T.bsum, 2 * (size_t)nblk)) || (e = dalloc(&T.ucount, (size_t)T.ntiles + 1)) ||
+      (e = dalloc(&T.usum, 2 * ((size_t)T.ntiles / SCAN_CHUNK + 2))))
     return e;
   PIC_CUDA(cudaMemset(T.start, 0, (T.nbins + 1) * sizeof(int64_t)));
   return PIC_OK;
@@ -1020,18 +1022,12 @@ extern "C" int pic_get_launches(pic_ctx *c, int64_t *n) {
   return PIC_OK;
 }
 
-// Batched ensemble: every member's steps up to its next sort are captured,
-// members on parallel branches (one forked stream each), into one CUDA graph
-// that is launched once; the sorts run between graphs.  A captured graph is
-// applied to the previous executable graph when its topology allows
-// (cudaGraphExecUpdate), otherwise instantiated anew.
-extern "C" int pic_ensemble_step(pic_ctx *const *ctxs, int32_t n, int32_t nsteps) {
-  if (!ctxs || n <= 0 || nsteps < 0) return pic_fail(PIC_EINVAL, "bad ensemble arguments");
-  for (int k = 0; k < n; ++k)
-    if (!ctxs[k]) return pic_fail(PIC_EINVAL, "null ensemble member");
-  const int dev = ctxs[0]->device;
-  for (int k = 1; k < n; ++k)
-    if (ctxs[k]->device != dev) return pic_fail(PIC_EINVAL, "ensemble members on different devices");
+// Ensemble with FP64 members: every member's steps up to the next sort of any
+// member are captured, members on parallel branches (one forked stream each),
+// into one CUDA graph that is launched once; the sorts run between graphs.  A
+// captured graph is applied to the previous executable graph when its
+// topology allows (cudaGraphExecUpdate), otherwise instantiated anew.
+static int ensemble_branches(pic_ctx *const *ctxs, int n, int nsteps) {
   cudaStream_t origin;
   PIC_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
   std::vector<cudaStream_t> br(n);
@@ -1113,6 +1109,260 @@ extern "C" int pic_ensemble_step(pic_ctx *const *ctxs, int32_t n, int32_t nsteps
   cudaEventDestroy(fork);
   cudaEventDestroy(after);
   cudaStreamDestroy(origin);
+  return err;
+}
+
+// ---- FP32 ensemble: one launch per phase for all members --------------------
+// Each phase of a step is one kernel over the blocks of every member that
+// takes part in it (a block finds its member by binary search over the
+// launch's block offsets); the members' arguments for each step sit in a
+// device table uploaded once per graph.  The kernels run the same per-block
+// and per-node code as a single context's, so every member's result is
+// bit-identical to its own pic_step run.  Steps up to the next sort of any
+// member are captured into one CUDA graph; each member sorts when its own
+// interval comes due.
+namespace {
+
+constexpr int ENS_MAX_BLOCK = 64;  // steps per graph at most
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// one step's block lists, built on the host, and the tile kernel's member
+// arguments (passed as kernel parameters) per kind
+struct StepLists {
+  std::vector<std::vector<int>> off, mem;  // per list: offsets (slots + 1), member entries
+  std::vector<unsigned char> targ[ENS_TILE_KINDS];
+  std::vector<int64_t> tblk[ENS_TILE_KINDS];
+  void reset(int nlists) {
+    off.assign(nlists, std::vector<int>(1, 0));
+    mem.assign(nlists, std::vector<int>());
+    for (int q = 0; q < ENS_TILE_KINDS; ++q) { targ[q].clear(); tblk[q].clear(); }
+  }
+  void add(int list, int member, int64_t blocks) {
+    if (blocks <= 0) return;
+    mem[list].push_back(member);
+    off[list].push_back(off[list].back() + (int)blocks);
+  }
+};
+
+}  // namespace
+
+static int ensemble_batched(pic_ctx *const *ctxs, int n, int nsteps, int64_t *kernels) {
+  int max_filt = 0, max_smooth = 0;
+  for (int k = 0; k < n; ++k) {
+    max_filt = std::max(max_filt, ctxs[k]->d.n_filt);
+    if (ctxs[k]->d.inject) max_smooth = std::max(max_smooth, ctxs[k]->d.inject_smooth);
+  }
+  // lists of one step: the grid phases in launch order
+  const int L_FLUX = 0, L_FILT = L_FLUX + 1, L_NODES = L_FILT + max_filt,
+            L_LOSSY = L_NODES + 1, L_GHOSTS = L_LOSSY + 1, L_COPY = L_GHOSTS + 1, L_SIGMA = L_COPY + 1,
+            L_SMOOTH = L_SIGMA + 1, L_WRITE = L_SMOOTH + max_smooth, NLISTS = L_WRITE + 1;
+  const size_t tile_bytes = ens_tile_arg_bytes();
+  const size_t field_sz = align_up((size_t)n * sizeof(EnsFieldArg), 256);
+  const size_t list_ints = (size_t)NLISTS * (2 * (size_t)n + 1);
+  const size_t step_sz = field_sz + align_up(list_ints * sizeof(int), 256);
+  unsigned char *h_tab = nullptr, *d_tab = nullptr;
+  PIC_CUDA(cudaMallocHost((void **)&h_tab, step_sz * ENS_MAX_BLOCK));
+  if (cudaMalloc((void **)&d_tab, step_sz * ENS_MAX_BLOCK) != cudaSuccess) {
+    cudaFreeHost(h_tab);
+    return pic_fail(PIC_ENOMEM, "ensemble argument tables");
+  }
+  cudaStream_t origin = nullptr;
+  cudaEvent_t after = nullptr;
+  int err = PIC_OK;
+  if (cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&after, cudaEventDisableTiming) != cudaSuccess)
+    err = pic_fail(PIC_ECUDA, "ensemble stream");
+  for (int k = 0; k < n && !err; ++k) {
+    cudaError_t ce = cudaStreamSynchronize(ctxs[k]->stream);  // earlier work of each member first
+    if (ce != cudaSuccess) err = pic_cuda_check(ce, "ensemble member stream");
+  }
+  // per member, the blocks of each grid phase (fixed for the call)
+  std::vector<std::array<int, ENS_NKIND>> nb(n);
+  for (int k = 0; k < n; ++k)
+    for (int q = 0; q < ENS_NKIND; ++q) nb[k][q] = ens_blocks(ctxs[k], q);
+  std::vector<StepLists> lists(ENS_MAX_BLOCK);
+  cudaGraphExec_t exec = nullptr;
+  int64_t launched = 0;
+  int done = 0;
+  while (done < nsteps && !err) {
+    int block = std::min(nsteps - done, ENS_MAX_BLOCK);
+    for (int k = 0; k < n; ++k) {
+      pic_ctx *c = ctxs[k];
+      block = std::min(block, std::max(1, c->d.sort_interval - c->steps_since_sort));
+    }
+    for (int k = 0; k < n && !err; ++k) {
+      const int64_t l0 = ctxs[k]->launches;
+      err = prepare_steps(ctxs[k], block);
+      launched += ctxs[k]->launches - l0;
+      if (!err) cudaStreamSynchronize(ctxs[k]->stream);
+    }
+    if (err) break;
+    // the members' arguments and block lists for each step; the host state
+    // advances as step_body advances it
+    for (int st = 0; st < block; ++st) {
+      unsigned char *base = h_tab + (size_t)st * step_sz;
+      EnsFieldArg *fa = reinterpret_cast<EnsFieldArg *>(base);
+      StepLists &SL = lists[st];
+      SL.reset(NLISTS);
+      for (int k = 0; k < n; ++k) {
+        pic_ctx *c = ctxs[k];
+        const Grid &G = c->G;
+        const int64_t tb = ens_tile_blocks(c);
+        if (tb > 0) {
+          const int kind = ens_tile_kind(c);
+          std::vector<unsigned char> &ta = SL.targ[kind];
+          ta.resize(ta.size() + tile_bytes);
+          ens_tile_arg(c, c->step * G.dt, ta.data() + ta.size() - tile_bytes);
+          SL.tblk[kind].push_back(tb);
+          ++c->launches;
+        }
+        ens_fill_field_arg(c, &fa[k]);
+        SL.add(L_FLUX, k, nb[k][ENS_FLUX]);
+        ++c->launches;
+        for (int p = 0; p < c->d.n_filt; ++p) SL.add(L_FILT + p, k, nb[k][ENS_FILTER]);
+        c->launches += 3 * (int64_t)std::max(0, c->d.n_filt);
+        if (c->d.n_filt & 1)
+          for (int q = 0; q < 3; ++q) std::swap(c->F[q], c->Ft[q]);
+        SL.add(L_NODES, k, nb[k][ENS_NODES]);
+        c->launches += 3;
+        if (nb[k][ENS_LOSSY] > 0) { SL.add(L_LOSSY, k, nb[k][ENS_LOSSY]); ++c->launches; }
+        SL.add(L_GHOSTS, k, nb[k][ENS_GHOSTS]);
+        SL.add(L_COPY, k, nb[k][ENS_COPY32]);
+        c->launches += 2;
+        c->step += 1;
+        if (c->d.inject) {
+          fa[k].t_inj = c->step * G.dt;
+          fa[k].inj_base = c->n_used;
+          fa[k].inj_id0 = c->next_id;
+          fa[k].inj_step = (uint64_t)c->step;
+          SL.add(L_SIGMA, k, nb[k][ENS_SIGMA]);
+          for (int p = 0; p < c->d.inject_smooth; ++p) SL.add(L_SMOOTH + p, k, nb[k][ENS_SIGMA]);
+          SL.add(L_WRITE, k, nb[k][ENS_WRITE]);
+          c->launches += 2 + c->d.inject_smooth;
+          const int64_t nslots = (int64_t)G.nth * c->d.pairs_per_cell * 2;
+          c->n_used += nslots;
+          c->next_id += nslots;
+        }
+        c->steps_since_sort += 1;
+      }
+      int *li = reinterpret_cast<int *>(base + field_sz);
+      for (int q = 0; q < NLISTS; ++q) {
+        int *o = li + (size_t)q * (2 * n + 1);
+        std::copy(SL.off[q].begin(), SL.off[q].end(), o);
+        std::copy(SL.mem[q].begin(), SL.mem[q].end(), o + n + 1);
+      }
+    }
+    cudaError_t ce = cudaMemcpyAsync(d_tab, h_tab, step_sz * block, cudaMemcpyHostToDevice, origin);
+    cudaGraph_t graph = nullptr;
+    int64_t nodes = 0;
+    if (ce == cudaSuccess) ce = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+      for (int st = 0; st < block; ++st) {
+        unsigned char *dbase = d_tab + (size_t)st * step_sz;
+        const EnsFieldArg *dfa = reinterpret_cast<const EnsFieldArg *>(dbase);
+        const int *dli = reinterpret_cast<const int *>(dbase + field_sz);
+        const StepLists &SL = lists[st];
+        auto L = [&](int q) {
+          EnsList x;
+          x.off = dli + (size_t)q * (2 * n + 1);
+          x.mem = x.off + n + 1;
+          x.n = (int)SL.mem[q].size();
+          return x;
+        };
+        auto blocks = [&](int q) { return SL.off[q].back(); };
+        for (int kind = 0; kind < ENS_TILE_KINDS; ++kind)
+          if (!SL.tblk[kind].empty())
+            nodes += ens_tiles32(kind, SL.targ[kind].data(), SL.tblk[kind].data(), (int)SL.tblk[kind].size(), origin);
+        ens_flux_from_acc(dfa, L(L_FLUX), blocks(L_FLUX), origin), ++nodes;
+        for (int p = 0; p < max_filt; ++p)
+          if (blocks(L_FILT + p) > 0) ens_filter(dfa, L(L_FILT + p), blocks(L_FILT + p), p, origin), ++nodes;
+        ens_b_half(dfa, L(L_NODES), blocks(L_NODES), origin);
+        ens_e_full(dfa, L(L_NODES), blocks(L_NODES), origin);
+        ens_b_half(dfa, L(L_NODES), blocks(L_NODES), origin);
+        nodes += 3;
+        if (blocks(L_LOSSY) > 0) ens_lossy(dfa, L(L_LOSSY), blocks(L_LOSSY), origin), ++nodes;
+        ens_ghosts(dfa, L(L_GHOSTS), blocks(L_GHOSTS), origin);
+        ens_copy32(dfa, L(L_COPY), blocks(L_COPY), origin);
+        nodes += 2;
+        if (blocks(L_SIGMA) > 0) {
+          ens_inject_sigma(dfa, L(L_SIGMA), blocks(L_SIGMA), origin), ++nodes;
+          for (int p = 0; p < max_smooth; ++p)
+            if (blocks(L_SMOOTH + p) > 0)
+              ens_inject_smooth(dfa, L(L_SMOOTH + p), blocks(L_SMOOTH + p), p, origin), ++nodes;
+          ens_inject_write(dfa, L(L_WRITE), blocks(L_WRITE), origin), ++nodes;
+        }
+      }
+      cudaError_t ce2 = cudaStreamEndCapture(origin, &graph);
+      if (ce == cudaSuccess) ce = ce2;
+    }
+    if (ce == cudaSuccess) {
+      bool fresh = exec == nullptr;
+      if (!fresh) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(exec, graph, &info) != cudaSuccess) {
+          cudaGetLastError();
+          cudaGraphExecDestroy(exec);
+          exec = nullptr;
+          fresh = true;
+        }
+      }
+      if (fresh) ce = cudaGraphInstantiate(&exec, graph, 0);
+      if (ce == cudaSuccess) ce = cudaGraphLaunch(exec, origin);
+      if (ce == cudaSuccess) ce = cudaEventRecord(after, origin);
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) { err = pic_cuda_check(ce, "ensemble graph"); break; }
+    launched += nodes;
+    done += block;
+    for (int k = 0; k < n && !err; ++k) {
+      pic_ctx *c = ctxs[k];
+      cudaStreamWaitEvent(c->stream, after, 0);
+      if (c->steps_since_sort >= c->d.sort_interval) {
+        const int64_t l0 = c->launches;
+        err = compact(c);
+        launched += c->launches - l0;
+      }
+    }
+    // the staging table is refilled next: its copy must have completed
+    if (!err) cudaEventSynchronize(after);
+  }
+  if (origin) cudaStreamSynchronize(origin);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (after) cudaEventDestroy(after);
+  if (origin) cudaStreamDestroy(origin);
+  cudaFree(d_tab);
+  cudaFreeHost(h_tab);
+  if (kernels) *kernels = launched;
+  return err;
+}
+
+extern "C" int pic_ensemble_step(pic_ctx *const *ctxs, int32_t n, int32_t nsteps, int64_t *kernels) {
+  if (!ctxs || n <= 0 || nsteps < 0) return pic_fail(PIC_EINVAL, "bad ensemble arguments");
+  for (int k = 0; k < n; ++k)
+    if (!ctxs[k]) return pic_fail(PIC_EINVAL, "null ensemble member");
+  const int dev = ctxs[0]->device;
+  bool fp32 = true;
+  for (int k = 0; k < n; ++k) {
+    if (ctxs[k]->device != dev) return pic_fail(PIC_EINVAL, "ensemble members on different devices");
+    fp32 = fp32 && ctxs[k]->d.precision == PIC_FP32;
+  }
+  for (int k = 0; k < n; ++k)
+    for (int q = 0; q < k; ++q)
+      if (ctxs[q] == ctxs[k]) return pic_fail(PIC_EINVAL, "a context appears twice in the ensemble");
+  int err;
+  if (fp32) {
+    err = ensemble_batched(ctxs, n, nsteps, kernels);
+  } else {
+    int64_t l0 = 0;
+    for (int k = 0; k < n; ++k) l0 += ctxs[k]->launches;
+    err = ensemble_branches(ctxs, n, nsteps);
+    if (kernels) {
+      int64_t l1 = 0;
+      for (int k = 0; k < n; ++k) l1 += ctxs[k]->launches;
+      *kernels = l1 - l0;
+    }
+  }
   if (err) return err;
   for (int k = 0; k < n; ++k) {
     latch_errors(ctxs[k]);
@@ -1129,8 +1379,11 @@ static int set_tiles(pic_ctx *c, int shape) {
   cudaFree(T.start);
   cudaFree(T.cursor);
   cudaFree(T.bsum);
-  T.start = T.cursor = T.bsum = nullptr;
+  cudaFree(T.ucount);
+  cudaFree(T.usum);
+  T.start = T.cursor = T.bsum = T.ucount = T.usum = nullptr;
   T.sorted_end = 0;
+  T.nunits = 0;
   int e;
   if ((e = alloc_bins(c, shape))) return e;
   c->d.tile_shape = shape;
@@ -1220,10 +1473,12 @@ extern "C" int pic_destroy(pic_ctx *c) {
   cudaFree(c->metric_buf);
   for (int k = 0; k < 6; ++k) { cudaFree(c->f[k]); cudaFree(c->f32[k]); }
   cudaFree(c->r_n32);
+  cudaFree(c->d_tile_maps);
   for (int k = 0; k < 3; ++k) { cudaFree(c->F[k]); cudaFree(c->Ft[k]); cudaFree(c->acc[k]); }
   cudaFree(c->Q); cudaFree(c->Qa); cudaFree(c->Qt); cudaFree(c->gsnap); cudaFree(c->sig);
   cudaFree(c->d_err); cudaFree(c->d_cnt); cudaFree(c->d_acc);
   cudaFree(c->tiles.start); cudaFree(c->tiles.cursor); cudaFree(c->tiles.bsum);
+  cudaFree(c->tiles.ucount); cudaFree(c->tiles.usum); cudaFree(c->tiles.units);
   cudaFree(c->tie_step); cudaFree(c->tie_id); cudaFree(c->tie_sign);
   cudaFree(c->hint_step); cudaFree(c->hint_id); cudaFree(c->hint_sign);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);

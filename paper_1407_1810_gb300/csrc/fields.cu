@@ -6,6 +6,7 @@
 //   Eq. volinjeq) and the Gauss-law / energy diagnostics.
 // All metric factors are precomputed per row and per column (pic::Metric), so
 // the kernels are pure streaming stencils over the padded arrays.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 
@@ -24,10 +25,10 @@ inline dim3 grid2(int ni, int nj) { return dim3((nj + BX - 1) / BX, (ni + BY - 1
 // (the factors of dt / 2 and the metric are folded into the row and column
 // coefficient tables of Metric: a few FP64 FMAs per node, the rate that
 // limits this kernel)
-__global__ void k_b_half(Grid G, const double *__restrict__ Er, const double *__restrict__ Et,
-                         const double *__restrict__ Ep, double *__restrict__ Br, double *__restrict__ Bt,
-                         double *__restrict__ Bp) {
-  const int j = blockIdx.x * BX + threadIdx.x, i = blockIdx.y * BY + threadIdx.y;
+__device__ __forceinline__ void b_half_node(const Grid &G, int i, int j, const double *__restrict__ Er,
+                                            const double *__restrict__ Et, const double *__restrict__ Ep,
+                                            double *__restrict__ Br, double *__restrict__ Bt,
+                                            double *__restrict__ Bp) {
   if (i > G.nr || j > G.nth) return;
   const Metric &m = G.m;
   const int ri = i + G.PI, cj = j + G.PJ;
@@ -43,16 +44,22 @@ __global__ void k_b_half(Grid G, const double *__restrict__ Er, const double *__
   }
 }
 
+__global__ void k_b_half(Grid G, const double *__restrict__ Er, const double *__restrict__ Et,
+                         const double *__restrict__ Ep, double *__restrict__ Br, double *__restrict__ Bt,
+                         double *__restrict__ Bp) {
+  b_half_node(G, blockIdx.y * BY + threadIdx.y, blockIdx.x * BX + threadIdx.x, Er, Et, Ep, Br, Bt, Bp);
+}
+
 // E <- E + dt c curl B - F / dA over the faces of the dual grid (last three
 // lines of Eq. discreteeq; E_r on the axis by Eq. erpolarupdate, obtained here
 // from the same formula with sin(tb_{-1}) = sin(tb_{nth}) = 0 and the cap
 // areas in inv_dcos_tb).  E_th, E_ph stay 0 on the conductors (i = 0, nr) and
 // E_ph on the axis.
-__global__ void k_e_full(Grid G, double *__restrict__ Er, double *__restrict__ Et, double *__restrict__ Ep,
-                         const double *__restrict__ Br, const double *__restrict__ Bt,
-                         const double *__restrict__ Bp, const double *__restrict__ Fr,
-                         const double *__restrict__ Ft, const double *__restrict__ Fp) {
-  const int j = blockIdx.x * BX + threadIdx.x, i = blockIdx.y * BY + threadIdx.y;
+__device__ __forceinline__ void e_full_node(const Grid &G, int i, int j, double *__restrict__ Er,
+                                            double *__restrict__ Et, double *__restrict__ Ep,
+                                            const double *__restrict__ Br, const double *__restrict__ Bt,
+                                            const double *__restrict__ Bp, const double *__restrict__ Fr,
+                                            const double *__restrict__ Ft, const double *__restrict__ Fp) {
   if (i > G.nr || j > G.nth) return;
   const Metric &m = G.m;
   const int ri = i + G.PI, cj = j + G.PJ;
@@ -71,10 +78,17 @@ __global__ void k_e_full(Grid G, double *__restrict__ Er, double *__restrict__ E
   }
 }
 
+__global__ void k_e_full(Grid G, double *__restrict__ Er, double *__restrict__ Et, double *__restrict__ Ep,
+                         const double *__restrict__ Br, const double *__restrict__ Bt,
+                         const double *__restrict__ Bp, const double *__restrict__ Fr,
+                         const double *__restrict__ Ft, const double *__restrict__ Fp) {
+  e_full_node(G, blockIdx.y * BY + threadIdx.y, blockIdx.x * BX + threadIdx.x, Er, Et, Ep, Br, Bt, Bp, Fr, Ft, Fp);
+}
+
 // Lossy layer, Eq. (EBcond): every component times 1 - sigma* at its own
 // radial stagger, rows i0..nr.
-__global__ void k_lossy(Grid G, double *Er, double *Et, double *Ep, double *Br, double *Bt, double *Bp, int i0) {
-  const int j = blockIdx.x * BX + threadIdx.x, i = i0 + blockIdx.y * BY + threadIdx.y;
+__device__ __forceinline__ void lossy_node(const Grid &G, int i, int j, double *Er, double *Et, double *Ep,
+                                           double *Br, double *Bt, double *Bp) {
   if (i > G.nr || j > G.nth) return;
   const size_t o = gidx(G, i, j);
   const double kn = G.m.keep_n[i + G.PI], kh = G.m.keep_h[i + G.PI];
@@ -82,14 +96,21 @@ __global__ void k_lossy(Grid G, double *Er, double *Et, double *Ep, double *Br, 
   Et[o] *= kn; Ep[o] *= kn; Br[o] *= kn;
 }
 
+__global__ void k_lossy(Grid G, double *Er, double *Et, double *Ep, double *Br, double *Bt, double *Bp, int i0) {
+  lossy_node(G, i0 + blockIdx.y * BY + threadIdx.y, blockIdx.x * BX + threadIdx.x, Er, Et, Ep, Br, Bt, Bp);
+}
+
 // Axisymmetric continuation of the half-integer-j components into columns -1
 // and nth (B_r even; E_th, B_ph odd).
-__global__ void k_axis_ghosts(Grid G, double *Et, double *Br, double *Bp) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void ghost_row(const Grid &G, int i, double *Et, double *Br, double *Bp) {
   if (i > G.nr) return;
   const size_t n0 = gidx(G, i, -1), s0 = gidx(G, i, G.nth);
   Et[n0] = -Et[n0 + 1]; Br[n0] = Br[n0 + 1]; Bp[n0] = -Bp[n0 + 1];
   Et[s0] = -Et[s0 - 1]; Br[s0] = Br[s0 - 1]; Bp[s0] = -Bp[s0 - 1];
+}
+
+__global__ void k_axis_ghosts(Grid G, double *Et, double *Br, double *Bp) {
+  ghost_row(G, blockIdx.x * blockDim.x + threadIdx.x, Et, Br, Bp);
 }
 
 // FP32 gather copies of the six components over the whole padded array
@@ -108,8 +129,8 @@ __global__ void k_copy32(size_t n, const double *__restrict__ a0, const double *
 // fold the part that would leave through the axis back onto the mirror point,
 // + for integer-j arrays (F_r, F_ph, charge) and - for the half-integer-j F_th.
 // Rows outside the ghost band -g..nr+g are not kept.
-__global__ void k_filter(Grid G, const double *__restrict__ in, double *__restrict__ out, int half_j) {
-  const int j = blockIdx.x * BX + threadIdx.x, i = -G.g + (int)(blockIdx.y * BY + threadIdx.y);
+__device__ __forceinline__ void filter_node(const Grid &G, int i, int j, const double *__restrict__ in,
+                                            double *__restrict__ out, int half_j) {
   const int nj = half_j ? G.nth : G.nth + 1;
   if (i > G.nr + G.g || j >= nj) return;
   double vm, v0 = 0.5, vp;
@@ -135,11 +156,15 @@ __global__ void k_filter(Grid G, const double *__restrict__ in, double *__restri
   out[o] = s;
 }
 
+__global__ void k_filter(Grid G, const double *__restrict__ in, double *__restrict__ out, int half_j) {
+  filter_node(G, -G.g + (int)(blockIdx.y * BY + threadIdx.y), blockIdx.x * BX + threadIdx.x, in, out, half_j);
+}
+
 // Surface charge per meridional cell: the jump of E_r across the conductor,
 // total E_r at (1/2, j) minus the analytic inside field's E_r at (r0, theta_j)
 // (zero for the monopole fields), averaged over the cell's two nodes.
-__global__ void k_inject_sigma(Grid G, const double *__restrict__ Er, double t, double *sig, long long *smax) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void sigma_cell(const Grid &G, int j, const double *__restrict__ Er, double t, double *sig,
+                                           long long *smax) {
   if (j >= G.nth) return;
   const Metric &m = G.m;
   const double rb0 = m.r_h[G.PI];
@@ -158,15 +183,23 @@ __global__ void k_inject_sigma(Grid G, const double *__restrict__ Er, double t, 
   if (smax) atomicMax(smax, __double_as_longlong(fabs(s)));
 }
 
+__global__ void k_inject_sigma(Grid G, const double *__restrict__ Er, double t, double *sig, long long *smax) {
+  sigma_cell(G, blockIdx.x * blockDim.x + threadIdx.x, Er, t, sig, smax);
+}
+
 // One 1-2-1 pass over sigma along theta; each polar cell is its own mirror
 // image across the axis.
-__global__ void k_inject_smooth(int nth, const double *__restrict__ in, double *out, long long *smax) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void smooth_cell(int j, int nth, const double *__restrict__ in, double *out,
+                                            long long *smax) {
   if (j >= nth) return;
   const double a = in[j > 0 ? j - 1 : 0], c = in[j < nth - 1 ? j + 1 : nth - 1];
   const double s = ((a + 2.0 * in[j]) + c) * 0.25;
   out[j] = s;
   if (smax) atomicMax(smax, __double_as_longlong(fabs(s)));
+}
+
+__global__ void k_inject_smooth(int nth, const double *__restrict__ in, double *out, long long *smax) {
+  smooth_cell(blockIdx.x * blockDim.x + threadIdx.x, nth, in, out, smax);
 }
 
 // SplitMix64 (Steele, Lea and Flood 2014) as a counter-based generator:
@@ -211,11 +244,12 @@ __device__ inline int inject_count(const Grid &G, const InjectRule &R, int j, do
 
 // One thread per slot (j, k, sign) of the 2 npp nth reserved this step; slots
 // past a cell's count keep zero charge (free).
+// (every lane of a warp calls it: the exponent is raised warp-wide)
 template <bool FP32>
-__global__ void k_inject_write(Grid G, const double *__restrict__ sig, const long long *smax, Parts64 P,
-                               Parts32 Q, int64_t base, int64_t id0, InjectRule R, long long *cnt,
-                               long long *capped_cnt, long long *qexp) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void inject_slot(int64_t idx, const Grid &G, const double *__restrict__ sig,
+                                            const long long *smax, const Parts64 &P, const Parts32 &Q, int64_t base,
+                                            int64_t id0, const InjectRule &R, long long *cnt, long long *capped_cnt,
+                                            long long *qexp) {
   const int npp = R.npp;
   int qe = (int)QEXP_NONE;
   if (idx < (int64_t)G.nth * npp * 2) {
@@ -249,6 +283,14 @@ __global__ void k_inject_write(Grid G, const double *__restrict__ sig, const lon
     if (on) add_ll(cnt, 1LL);
   }
   if (FP32) raise_qexp(qexp, qe);  // every lane of the warp reaches this
+}
+
+template <bool FP32>
+__global__ void k_inject_write(Grid G, const double *__restrict__ sig, const long long *smax, Parts64 P,
+                               Parts32 Q, int64_t base, int64_t id0, InjectRule R, long long *cnt,
+                               long long *capped_cnt, long long *qexp) {
+  inject_slot<FP32>(blockIdx.x * (int64_t)blockDim.x + threadIdx.x, G, sig, smax, P, Q, base, id0, R, cnt,
+                    capped_cnt, qexp);
 }
 
 __device__ inline double warp_max(double v) {
@@ -313,7 +355,180 @@ __global__ void k_field_energy(Grid G, const double *f0, const double *f1, const
   if ((threadIdx.x & 31) == 0) atomicAdd(acc, e);
 }
 
+// ---- the same kernels over the members of an ensemble ----------------------
+// 256-thread blocks; a member's 2-D node blocks (32 x 8, as the kernels above
+// take them) are numbered row-major across its grid.
+struct Node2 {
+  int i, j;
+};
+__device__ inline Node2 node_of(unsigned b, int nj, int i_first) {
+  const unsigned gx = (unsigned)(nj + BX - 1) / BX;
+  return Node2{i_first + (int)((b / gx) * BY + (threadIdx.x >> 5)), (int)((b % gx) * BX + (threadIdx.x & 31))};
+}
+
+// pass `pass` of the filter on all three flux components: even passes read
+// the deposit's buffers and write the scratch, odd passes the reverse
+__global__ void k_ens_filter(const EnsFieldArg *__restrict__ tab, EnsList L, int pass) {
+  const int k = ens_slot(L, blockIdx.x);
+  const EnsFieldArg &E = tab[L.mem[k]];
+  const Grid &G = E.G;
+  const unsigned per = (unsigned)((G.nth + 1 + BX - 1) / BX) * (unsigned)((G.nr + 2 * G.g + 1 + BY - 1) / BY);
+  const unsigned b = blockIdx.x - (unsigned)L.off[k];
+  const int comp = (int)(b / per);
+  const Node2 n = node_of(b % per, G.nth + 1, -G.g);
+  const double *in = (pass & 1) ? E.Ftmp[comp] : E.Fin[comp];
+  double *out = (pass & 1) ? E.Fin[comp] : E.Ftmp[comp];
+  filter_node(G, n.i, n.j, in, out, comp == 1);
+}
+
+__global__ void k_ens_b_half(const EnsFieldArg *__restrict__ tab, EnsList L) {
+  const int k = ens_slot(L, blockIdx.x);
+  const EnsFieldArg &E = tab[L.mem[k]];
+  const Node2 n = node_of(blockIdx.x - (unsigned)L.off[k], E.G.nth + 1, 0);
+  b_half_node(E.G, n.i, n.j, E.f[ER], E.f[ETH], E.f[EPH], E.f[BR], E.f[BTH], E.f[BPH]);
+}
+
+__global__ void k_ens_e_full(const EnsFieldArg *__restrict__ tab, EnsList L) {
+  const int k = ens_slot(L, blockIdx.x);
+  const EnsFieldArg &E = tab[L.mem[k]];
+  const Node2 n = node_of(blockIdx.x - (unsigned)L.off[k], E.G.nth + 1, 0);
+  e_full_node(E.G, n.i, n.j, E.f[ER], E.f[ETH], E.f[EPH], E.f[BR], E.f[BTH], E.f[BPH], E.Fout[0], E.Fout[1],
+              E.Fout[2]);
+}
+
+__global__ void k_ens_lossy(const EnsFieldArg *__restrict__ tab, EnsList L) {
+  const int k = ens_slot(L, blockIdx.x);
+  const EnsFieldArg &E = tab[L.mem[k]];
+  const Node2 n = node_of(blockIdx.x - (unsigned)L.off[k], E.G.nth + 1, E.lossy_i0);
+  lossy_node(E.G, n.i, n.j, E.f[0], E.f[1], E.f[2], E.f[3], E.f[4], E.f[5]);
+}
+
+// axis ghosts; block 0 of a member that injects also clears the surface
+// charge maximum its injection will raise later in the step
+__global__ void k_ens_ghosts(const EnsFieldArg *__restrict__ tab, EnsList L) {
+  const int k = ens_slot(L, blockIdx.x);
+  const EnsFieldArg &E = tab[L.mem[k]];
+  const unsigned b = blockIdx.x - (unsigned)L.off[k];
+  if (b == 0 && threadIdx.x == 0 && E.inject) E.cnt[CNT_SMAX] = 0;
+  ghost_row(E.G, (int)(b * blockDim.x + threadIdx.x), E.f[ETH], E.f[BR], E.f[BPH]);
+}
+
+__global__ void k_ens_copy32(const EnsFieldArg *__restrict__ tab, EnsList L) {
+  const int k = ens_slot(L, blockIdx.x);
+  const EnsFieldArg &E = tab[L.mem[k]];
+  const size_t nb = (size_t)(L.off[k + 1] - L.off[k]), b = blockIdx.x - (unsigned)L.off[k];
+  for (size_t q = b * blockDim.x + threadIdx.x; q < E.grid_elems; q += nb * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) E.f32[c][q] = (float)E.f[c][q];
+  }
+}
+
+__device__ inline InjectRule ens_rule(const EnsFieldArg &E) {
+  return InjectRule{E.inject, E.npp, E.f_inj, E.inject_q, E.inject_seed, E.inj_step};
+}
+
+__global__ void k_ens_sigma(const EnsFieldArg *__restrict__ tab, EnsList L) {
+  const int k = ens_slot(L, blockIdx.x);
+  const EnsFieldArg &E = tab[L.mem[k]];
+  const int j = (int)((blockIdx.x - (unsigned)L.off[k]) * blockDim.x + threadIdx.x);
+  sigma_cell(E.G, j, E.f[ER], E.t_inj, E.sig, E.inject_smooth ? nullptr : E.cnt + CNT_SMAX);
+}
+
+__global__ void k_ens_smooth(const EnsFieldArg *__restrict__ tab, EnsList L, int pass) {
+  const int k = ens_slot(L, blockIdx.x);
+  const EnsFieldArg &E = tab[L.mem[k]];
+  const int j = (int)((blockIdx.x - (unsigned)L.off[k]) * blockDim.x + threadIdx.x), nth = E.G.nth;
+  const double *in = (pass & 1) ? E.sig + (nth + 1) : E.sig;
+  double *out = (pass & 1) ? E.sig : E.sig + (nth + 1);
+  smooth_cell(j, nth, in, out, pass == E.inject_smooth - 1 ? E.cnt + CNT_SMAX : nullptr);
+}
+
+__global__ void k_ens_write(const EnsFieldArg *__restrict__ tab, EnsList L) {
+  const int k = ens_slot(L, blockIdx.x);
+  const EnsFieldArg &E = tab[L.mem[k]];
+  const int64_t idx = (int64_t)(blockIdx.x - (unsigned)L.off[k]) * blockDim.x + threadIdx.x;
+  const double *sig = (E.inject_smooth & 1) ? E.sig + (E.G.nth + 1) : E.sig;
+  const Parts64 none;
+  inject_slot<true>(idx, E.G, sig, E.cnt + CNT_SMAX, none, E.p32, E.inj_base, E.inj_id0, ens_rule(E),
+                    E.cnt + CNT_INJECTED, E.cnt + CNT_CAPPED, E.cnt + CNT_QEXP);
+}
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
 }  // namespace
+
+int ens_blocks(const pic_ctx *c, int kind) {
+  const Grid &G = c->G;
+  const int gx = div_up(G.nth + 1, BX);
+  switch (kind) {
+    case ENS_FLUX: return gx * div_up(G.nr + 2 * G.g + 1, BY);
+    case ENS_FILTER: return c->d.n_filt > 0 ? 3 * gx * div_up(G.nr + 2 * G.g + 1, BY) : 0;
+    case ENS_NODES: return gx * div_up(G.nr + 1, BY);
+    case ENS_LOSSY: {
+      if (c->d.absorb_profile == PIC_ABSORB_NONE || c->d.absorb_cells <= 0) return 0;
+      const int i0 = std::max(0, G.nr - G.absorb_cells - 1);
+      return gx * div_up(G.nr + 1 - i0, BY);
+    }
+    case ENS_GHOSTS: return div_up(G.nr + 1, 256);
+    case ENS_COPY32: return (int)std::min<int64_t>(4 * 152, div_up((int64_t)c->grid_elems, 256));
+    case ENS_SIGMA: return c->d.inject ? div_up(G.nth, 256) : 0;
+    case ENS_WRITE: return c->d.inject ? div_up((int64_t)G.nth * c->d.pairs_per_cell * 2, 256) : 0;
+    default: return 0;
+  }
+}
+
+void ens_fill_field_arg(const pic_ctx *c, EnsFieldArg *a) {
+  memset(a, 0, sizeof *a);
+  a->G = c->G;
+  for (int k = 0; k < 6; ++k) { a->f[k] = c->f[k]; a->f32[k] = c->f32[k]; }
+  for (int k = 0; k < 3; ++k) {
+    a->Fin[k] = c->F[k];
+    a->Ftmp[k] = c->Ft[k];
+    a->Fout[k] = (c->d.n_filt & 1) ? c->Ft[k] : c->F[k];
+    a->acc[k] = c->acc[k];
+  }
+  a->grid_elems = c->grid_elems;
+  a->cnt = c->d_cnt;
+  a->sig = c->sig;
+  a->p32 = c->p32;
+  a->f_inj = c->d.f_inj;
+  a->inject_q = c->d.inject_q;
+  a->inject_seed = c->d.inject_seed;
+  a->inject = c->d.inject;
+  a->npp = c->d.pairs_per_cell;
+  a->inject_smooth = c->d.inject_smooth;
+  a->n_filt = c->d.n_filt;
+  a->lossy_i0 = (c->d.absorb_profile != PIC_ABSORB_NONE && c->d.absorb_cells > 0)
+                    ? std::max(0, c->G.nr - c->G.absorb_cells - 1) : -1;
+}
+
+void ens_filter(const EnsFieldArg *tab, const EnsList &L, int blocks, int pass, cudaStream_t s) {
+  k_ens_filter<<<(unsigned)blocks, 256, 0, s>>>(tab, L, pass);
+}
+void ens_b_half(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s) {
+  k_ens_b_half<<<(unsigned)blocks, 256, 0, s>>>(tab, L);
+}
+void ens_e_full(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s) {
+  k_ens_e_full<<<(unsigned)blocks, 256, 0, s>>>(tab, L);
+}
+void ens_lossy(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s) {
+  k_ens_lossy<<<(unsigned)blocks, 256, 0, s>>>(tab, L);
+}
+void ens_ghosts(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s) {
+  k_ens_ghosts<<<(unsigned)blocks, 256, 0, s>>>(tab, L);
+}
+void ens_copy32(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s) {
+  k_ens_copy32<<<(unsigned)blocks, 256, 0, s>>>(tab, L);
+}
+void ens_inject_sigma(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s) {
+  k_ens_sigma<<<(unsigned)blocks, 256, 0, s>>>(tab, L);
+}
+void ens_inject_smooth(const EnsFieldArg *tab, const EnsList &L, int blocks, int pass, cudaStream_t s) {
+  k_ens_smooth<<<(unsigned)blocks, 256, 0, s>>>(tab, L, pass);
+}
+void ens_inject_write(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s) {
+  k_ens_write<<<(unsigned)blocks, 256, 0, s>>>(tab, L);
+}
 
 void fields_b_half(pic_ctx *c) {
   const Grid &G = c->G;

@@ -15,6 +15,7 @@
 // relative displacement, the meridional one from the exact rotation angle of
 // the displaced point, so an offset keeps ~1e-7 cell accuracy anywhere on the
 // grid instead of the ~1e-4 cell an absolute FP32 r or theta would give.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -70,6 +71,8 @@ struct Args32 {
   int row0, ntj, ntiles, ti, tj, tc;
   int mix;                  // sort: 1 = by cell, bins stored transposed; 0 = by tile, order kept
   const int64_t *start;
+  const long long *units;   // work units: tile << 32 | index of the unit within its tile
+  int64_t nunits, unit;     // units of the binned particles; particles per unit
   int64_t sorted_end, n_used;
   // vacuum
   float b0, r_min, omega_t;
@@ -544,8 +547,19 @@ __global__ void k_wait_selftest(long long limit, int arrive_first, int *err) {
   if (!window_wait(&bar, limit)) atomicOr(err, ERR_TIMEOUT);
 }
 
-template <int TI, int TJ, int SPEC>
-__global__ void __launch_bounds__(NT, 4) k_tiles32(Args32 A, Parts32 P, const __grid_constant__ TileMaps maps) {
+// Tensor maps read by the TMA unit from global memory (the batched ensemble
+// kernel's per-member maps, written by a host copy before any launch) are
+// ordered after those writes by an acquire fence of the tensor-map proxy.
+__device__ inline void tensormap_acquire(const CUtensorMap *map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
+// One tile CTA (or one block of unbinned particles) of the FP32 step: block
+// `blk` of the member whose arguments are A and P, its six field tensor maps
+// at `maps` (kernel parameters, or global memory when GMAPS).
+template <int TI, int TJ, int SPEC, bool GMAPS>
+__device__ __forceinline__ void tiles32_block(const Args32 &A, const Parts32 &P, const CUtensorMap *maps,
+                                              unsigned blk) {
   using BX_ = Box<TI, TJ>;
   constexpr int WI = BX_::WI, WJ = BX_::WJ, WN = BX_::WN, WB = BX_::WB, SLOT = BX_::SLOT;
   __shared__ __align__(128) float sbuf[BX_::SF + BX_::U];
@@ -559,9 +573,11 @@ __global__ void __launch_bounds__(NT, 4) k_tiles32(Args32 A, Parts32 P, const __
   __shared__ __align__(8) uint64_t sbar;
   int dead = 0;
   const float fs = __int_as_float((127 + KFIX - qexp_value(A.qexp)) << 23);  // 2^(KFIX - e)
-  if (blockIdx.x < (unsigned)A.ntiles) {
-    const int t = blockIdx.x;
-    const int64_t b0 = A.start[(int64_t)t * A.tc], b1 = A.start[(int64_t)(t + 1) * A.tc];
+  if (blk < (uint64_t)A.nunits) {
+    const long long u = A.units[blk];
+    const int t = (int)(u >> 32);
+    const int64_t b0 = A.start[(int64_t)t * A.tc] + (u & 0xffffffffll) * A.unit;
+    const int64_t b1 = min(A.start[(int64_t)(t + 1) * A.tc], b0 + A.unit);
     if (b1 <= b0) return;
     const int i0 = A.row0 + (t / A.ntj) * TI, j0 = (t % A.ntj) * TJ;
     const int wi0 = i0 - H - 1, wj0 = j0 - H - 1;
@@ -573,8 +589,12 @@ __global__ void __launch_bounds__(NT, 4) k_tiles32(Args32 A, Parts32 P, const __
                    "r"((uint32_t)(6 * WI * WB * sizeof(float)))
                    : "memory");
       const int x = wj0 - WOFF + A.PJ, y = wi0 + A.PI;  // x: a multiple of 4 (static_assert above)
+      if (GMAPS) {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) tma_window(stage + c * SLOT, &maps.m[c], x, y, &sbar);
+        for (int c = 0; c < 6; ++c) tensormap_acquire(maps + c);
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) tma_window(stage + c * SLOT, maps + c, x, y, &sbar);
       // bounded wait: on a timeout the error is latched, the copies get a
       // second bounded wait (they write into this block's shared memory) and
       // the tile is skipped
@@ -634,10 +654,49 @@ __global__ void __launch_bounds__(NT, 4) k_tiles32(Args32 A, Parts32 P, const __
     if (threadIdx.x == 0 && sdead) add_ll(A.cnt + CNT_DELETED, sdead);
   } else {  // particles outside any bin (injected since the last sort)
     const SmemAcc<WJ, WN> none{nullptr, nullptr, nullptr, nullptr, 0, 0, fs};
-    const int64_t k = A.sorted_end + (int64_t)(blockIdx.x - A.ntiles) * NT + threadIdx.x;
+    const int64_t k = A.sorted_end + (int64_t)(blk - A.nunits) * NT + threadIdx.x;
     if (k < A.n_used) process<SPEC>(A, P, k, false, none, 0, 0, 0, 0, dead);
     if (dead) add_ll(A.cnt + CNT_DELETED, dead);
   }
+}
+
+template <int TI, int TJ, int SPEC>
+__global__ void __launch_bounds__(NT, 4) k_tiles32(Args32 A, Parts32 P, const __grid_constant__ TileMaps maps) {
+  tiles32_block<TI, TJ, SPEC, false>(A, P, maps.m, blockIdx.x);
+}
+
+// One member of a batched launch: its step's arguments and its six field
+// tensor maps (device memory) for its tile shape.
+struct EnsTileArg {
+  Args32 A;
+  Parts32 P;
+  const CUtensorMap *maps;
+};
+
+// Up to ENS_TILE_SLOTS members in one launch, passed as kernel parameters:
+// the arguments sit in the same immutable parameter memory as those of
+// k_tiles32, so the compiler treats them alike (loads it may hoist out of the
+// particle loop), which keeps every member's arithmetic bit-identical to its
+// own k_tiles32 launch.  Member k owns blocks [off[k], off[k + 1]).
+constexpr int ENS_TILE_SLOTS = 48;
+struct EnsTileBatch {
+  EnsTileArg a[ENS_TILE_SLOTS];
+  int off[ENS_TILE_SLOTS + 1];
+  int n;
+};
+static_assert(sizeof(EnsTileBatch) <= 32000, "kernel parameters are limited to 32 KB");
+
+// the tile kernel over several members of an ensemble in one grid
+template <int TI, int TJ, int SPEC>
+__global__ void __launch_bounds__(NT, 4) k_ens_tiles32(const __grid_constant__ EnsTileBatch B) {
+  int lo = 0, hi = B.n - 1;  // the member owning this block
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((unsigned)B.off[mid] <= blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const EnsTileArg &T = B.a[lo];
+  tiles32_block<TI, TJ, SPEC, true>(T.A, T.P, T.maps, blockIdx.x - (unsigned)B.off[lo]);
 }
 
 // (double)v * 2^s built on the integer pipes: v rounded to 53 bits (to
@@ -665,15 +724,34 @@ __device__ inline double fixed_to_f64(long long v, int s) {
 }
 
 // fixed point -> FP64 fluxes over the ghost band; clears the accumulators
-__global__ void k_flux_from_acc(int nr, int nth, int g, int PI, int PJ, int LD, const long long *qexp,
-                                long long *a0, long long *a1, long long *a2, double *F0, double *F1, double *F2) {
-  const int j = blockIdx.x * 32 + threadIdx.x, i = -g + (int)(blockIdx.y * 8 + threadIdx.y);
+// (node i, j of the band -g <= i <= nr + g, 0 <= j <= nth)
+__device__ __forceinline__ void flux_node(int i, int j, int nr, int nth, int g, int PI, int LD, int PJ,
+                                          const long long *qexp, long long *a0, long long *a1, long long *a2,
+                                          double *F0, double *F1, double *F2) {
   if (i > nr + g || j > nth) return;
   const int s = qexp_value(qexp) - KFIX;  // one flux unit is 2^s of charge
   const size_t o = (size_t)(i + PI) * LD + (size_t)(j + PJ);
   F0[o] = fixed_to_f64(a0[o], s); a0[o] = 0;
   F1[o] = fixed_to_f64(a1[o], s); a1[o] = 0;
   F2[o] = fixed_to_f64(a2[o], s); a2[o] = 0;
+}
+
+__global__ void k_flux_from_acc(int nr, int nth, int g, int PI, int PJ, int LD, const long long *qexp,
+                                long long *a0, long long *a1, long long *a2, double *F0, double *F1, double *F2) {
+  flux_node(-g + (int)(blockIdx.y * 8 + threadIdx.y), blockIdx.x * 32 + threadIdx.x, nr, nth, g, PI, LD, PJ, qexp,
+            a0, a1, a2, F0, F1, F2);
+}
+
+// the same over the members of an ensemble: 256-thread blocks, each member's
+// band covered by 32 x 8 node blocks as above
+__global__ void k_ens_flux(const EnsFieldArg *__restrict__ tab, EnsList L) {
+  const int k = ens_slot(L, blockIdx.x);
+  const EnsFieldArg &E = tab[L.mem[k]];
+  const Grid &G = E.G;
+  const unsigned b = blockIdx.x - (unsigned)L.off[k], gx = (unsigned)(G.nth + 1 + 31) / 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  flux_node(-G.g + (int)((b / gx) * 8 + ty), (int)((b % gx) * 32 + tx), G.nr, G.nth, G.g, G.PI, G.LD, G.PJ,
+            E.cnt + CNT_QEXP, E.acc[0], E.acc[1], E.acc[2], E.Fin[0], E.Fin[1], E.Fin[2]);
 }
 
 // ---- counting sort into tile bins (drops removed particles) ---------------
@@ -779,6 +857,21 @@ __global__ void k_scan_apply(int64_t *count, int64_t *start, int64_t nb, const i
   if (blockIdx.x == 0 && threadIdx.x == 0) start[nb] = offs[nblk];
 }
 
+// work units of each tile: ceil(n_t / unit), none for an empty tile
+__global__ void k_unit_count(const int64_t *start, int tc, int ntiles, int64_t unit, int64_t *ucount) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  const int64_t n = start[(int64_t)(t + 1) * tc] - start[(int64_t)t * tc];
+  ucount[t] = (n + unit - 1) / unit;
+}
+
+// the unit list from the exclusive scan of the counts (uoff[ntiles] = total)
+__global__ void k_unit_fill(const int64_t *uoff, int ntiles, long long *units) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  for (int64_t u = uoff[t]; u < uoff[t + 1]; ++u) units[u] = ((long long)t << 32) | (long long)(u - uoff[t]);
+}
+
 // Order inside a tile's bin.  The counting sort yields the tile's particles
 // cell by cell; they are stored transposed: the cell-ordered sequence fills
 // the columns of a matrix with TRW columns, and the bin holds its rows.  The
@@ -882,6 +975,9 @@ Args32 make_args(pic_ctx *c, double t) {
   A.ti = c->tiles.TI; A.tj = c->tiles.TJ; A.tc = c->tiles.tc;
   A.mix = 0;
   A.start = c->tiles.start;
+  A.units = c->tiles.units;
+  A.nunits = c->tiles.nunits;
+  A.unit = c->tiles.unit;
   A.sorted_end = c->tiles.sorted_end;
   A.n_used = c->n_used;
   A.b0 = (float)G.b0; A.r_min = (float)G.r_min;
@@ -937,20 +1033,33 @@ int tiles32_setup(pic_ctx *c) {
   if (encode_maps<16, 16>(c, fn, c->tile_maps[0]) || encode_maps<8, 32>(c, fn, c->tile_maps[1]) ||
       encode_maps<32, 8>(c, fn, c->tile_maps[2]))
     return -1;
+  // a device copy for the batched ensemble kernel (the arrays never move)
+  if (cudaMalloc((void **)&c->d_tile_maps, sizeof c->tile_maps) != cudaSuccess ||
+      cudaMemcpy(c->d_tile_maps, c->tile_maps, sizeof c->tile_maps, cudaMemcpyHostToDevice) != cudaSuccess)
+    return -1;
   return 0;
+}
+
+// the compile-time specialisation of the tile kernel a context takes
+static int tile_spec(const pic_ctx *c) {
+  const pic_desc &d = c->d;
+  return c->small_steps && d.r_map == PIC_R_LOG && d.pusher == PIC_VAY
+             ? (d.th_map == PIC_TH_LINEAR && d.vacuum == PIC_VAC_MONOPOLE ? SPEC_MONOPOLE
+                : d.th_map == PIC_TH_EQUAL_AREA && d.vacuum == PIC_VAC_MONOPOLE_ROTATOR ? SPEC_ROTATOR
+                                                                                         : SPEC_GENERIC)
+             : SPEC_GENERIC;
+}
+
+int64_t ens_tile_blocks(const pic_ctx *c) {
+  if (c->n_used == 0) return 0;
+  return c->tiles.nunits + (c->n_used - c->tiles.sorted_end + NT - 1) / NT;
 }
 
 void particles32(pic_ctx *c, double t) {
   if (c->n_used == 0) return;
   Args32 A = make_args(c, t);
-  const int64_t tail = c->n_used - c->tiles.sorted_end;
-  const int64_t blocks = c->tiles.ntiles + (tail + NT - 1) / NT;
-  const pic_desc &d = c->d;
-  const int spec = c->small_steps && d.r_map == PIC_R_LOG && d.pusher == PIC_VAY
-                       ? (d.th_map == PIC_TH_LINEAR && d.vacuum == PIC_VAC_MONOPOLE ? SPEC_MONOPOLE
-                          : d.th_map == PIC_TH_EQUAL_AREA && d.vacuum == PIC_VAC_MONOPOLE_ROTATOR ? SPEC_ROTATOR
-                                                                                                   : SPEC_GENERIC)
-                       : SPEC_GENERIC;
+  const int64_t blocks = ens_tile_blocks(c);
+  const int spec = tile_spec(c);
   if (spec == SPEC_MONOPOLE) launch_tiles<SPEC_MONOPOLE>(c, A, blocks);
   else if (spec == SPEC_ROTATOR) launch_tiles<SPEC_ROTATOR>(c, A, blocks);
   else launch_tiles<SPEC_GENERIC>(c, A, blocks);
@@ -982,6 +1091,56 @@ extern "C" int pic_wait_selftest(int64_t polls, int32_t arrive_first, void *stre
 
 namespace pic {
 
+size_t ens_tile_arg_bytes() { return sizeof(EnsTileArg); }
+
+// kind = 3 x specialisation + tile shape (0: 16 x 16, 1: 8 x 32, 2: 32 x 8)
+int ens_tile_kind(const pic_ctx *c) {
+  const int shape = c->tiles.TI == 8 ? 1 : (c->tiles.TI == 32 ? 2 : 0);
+  return 3 * tile_spec(c) + shape;
+}
+
+void ens_tile_arg(pic_ctx *c, double t, void *out) {
+  EnsTileArg a;
+  a.A = make_args(c, t);
+  a.P = c->p32;
+  const int shape = c->tiles.TI == 8 ? 1 : (c->tiles.TI == 32 ? 2 : 0);
+  a.maps = reinterpret_cast<const CUtensorMap *>(c->d_tile_maps + (size_t)shape * sizeof(TileMaps));
+  memcpy(out, &a, sizeof a);
+}
+
+template <int SPEC>
+static void ens_tiles_spec(int shape, const EnsTileBatch &B, unsigned blocks, cudaStream_t s) {
+  if (shape == 1) k_ens_tiles32<8, 32, SPEC><<<blocks, NT, 0, s>>>(B);
+  else if (shape == 2) k_ens_tiles32<32, 8, SPEC><<<blocks, NT, 0, s>>>(B);
+  else k_ens_tiles32<16, 16, SPEC><<<blocks, NT, 0, s>>>(B);
+}
+
+int ens_tiles32(int kind, const void *args, const int64_t *blocks, int n, cudaStream_t s) {
+  const EnsTileArg *T = static_cast<const EnsTileArg *>(args);
+  const int spec = kind / 3, shape = kind % 3;
+  int launches = 0;
+  static thread_local EnsTileBatch B;  // 20 KB: kept off the stack
+  for (int first = 0; first < n; first += ENS_TILE_SLOTS) {
+    const int m = std::min(ENS_TILE_SLOTS, n - first);
+    B.n = m;
+    B.off[0] = 0;
+    for (int k = 0; k < m; ++k) {
+      B.a[k] = T[first + k];
+      B.off[k + 1] = B.off[k] + (int)blocks[first + k];
+    }
+    const unsigned g = (unsigned)B.off[m];
+    if (spec == SPEC_MONOPOLE) ens_tiles_spec<SPEC_MONOPOLE>(shape, B, g, s);
+    else if (spec == SPEC_ROTATOR) ens_tiles_spec<SPEC_ROTATOR>(shape, B, g, s);
+    else ens_tiles_spec<SPEC_GENERIC>(shape, B, g, s);
+    ++launches;
+  }
+  return launches;
+}
+
+void ens_flux_from_acc(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s) {
+  k_ens_flux<<<(unsigned)blocks, 256, 0, s>>>(tab, L);
+}
+
 void flux_from_acc(pic_ctx *c) {
   const Grid &G = c->G;
   dim3 gr((G.nth + 1 + 31) / 32, (G.nr + 2 * G.g + 1 + 7) / 8);
@@ -989,13 +1148,39 @@ void flux_from_acc(pic_ctx *c) {
                                                      c->acc[0], c->acc[1], c->acc[2], c->F[0], c->F[1], c->F[2]);
 }
 
+// Particles per work unit: at least UNIT_MIN, and large enough that a run
+// holds no more than about UNIT_TARGET units besides one per tile (two waves of
+// 4 CTAs on each of the 152 SMs): a large run keeps one unit per tile, while
+// the dense tiles of a small plasma are spread over many CTAs instead of
+// holding the whole kernel back on one.
+constexpr int64_t UNIT_MIN = 4096, UNIT_TARGET = 2 * 4 * 152;
+
 int64_t sort32(pic_ctx *c) {
   Tiles &T = c->tiles;
   const int64_t n = c->n_used;
+  T.nunits = 0;
   if (n == 0) {
     T.sorted_end = 0;
     cudaMemsetAsync(T.start, 0, (T.nbins + 1) * sizeof(int64_t), c->stream);
     return 0;
+  }
+  // room for the work units first: on failure no particle has moved, every
+  // particle takes the unbinned path until a sort succeeds, and the context
+  // reports the error
+  T.unit = std::max(UNIT_MIN, (n + UNIT_TARGET - 1) / UNIT_TARGET);
+  const int64_t ucap = T.ntiles + n / T.unit + 1;
+  if (ucap > T.units_cap) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(T.units);
+    T.units = nullptr;
+    T.units_cap = 0;
+    T.sorted_end = 0;
+    if (cudaMalloc((void **)&T.units, (size_t)ucap * sizeof(long long)) != cudaSuccess) {
+      cudaGetLastError();
+      c->host_err |= ERR_CAPACITY;
+      return -1;
+    }
+    T.units_cap = ucap;
   }
   Args32 A = make_args(c, 0.0);
   A.mix = c->mix_sort ? 1 : 0;
@@ -1009,10 +1194,20 @@ int64_t sort32(pic_ctx *c) {
   ++c->launches, k_scan_bins<<<1, 1024, 0, c->stream>>>(T.bsum, T.bsum + nblk + 1, nblk);
   ++c->launches, k_scan_apply<<<nblk, 256, 0, c->stream>>>(count, T.start, T.nbins, T.bsum + nblk + 1, nblk);
   ++c->launches, k_scatter_cells<<<blocks, 256, 0, c->stream>>>(A, c->p32, c->q32, n, count);
-  // particles in cell bins: everything before the bin of removed ones
+  // the work units of the tile kernel (n bounds the live count from above)
+  const unsigned tb = (unsigned)((T.ntiles + 255) / 256);
+  const int ublk = (int)((T.ntiles + SCAN_CHUNK - 1) / SCAN_CHUNK);
+  ++c->launches, k_unit_count<<<tb, 256, 0, c->stream>>>(T.start, T.tc, T.ntiles, T.unit, T.ucount);
+  ++c->launches, k_scan_sums<<<ublk, 256, 0, c->stream>>>(T.ucount, T.ntiles, T.usum);
+  ++c->launches, k_scan_bins<<<1, 1024, 0, c->stream>>>(T.usum, T.usum + ublk + 1, ublk);
+  ++c->launches, k_scan_apply<<<ublk, 256, 0, c->stream>>>(T.ucount, T.ucount, T.ntiles, T.usum + ublk + 1, ublk);
+  ++c->launches, k_unit_fill<<<tb, 256, 0, c->stream>>>(T.ucount, T.ntiles, T.units);
+  // particles in cell bins: everything before the bin of removed ones; units
   cudaMemcpyAsync(c->h_pinned, T.start + (int64_t)T.ntiles * T.tc, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(c->h_pinned + 1, T.ucount + T.ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
   cudaStreamSynchronize(c->stream);
-  const int64_t live = *c->h_pinned;
+  const int64_t live = c->h_pinned[0];
+  T.nunits = c->h_pinned[1];
   Parts32 tmp = c->p32;
   c->p32 = c->q32;
   c->q32 = tmp;

@@ -79,11 +79,65 @@ struct Tiles {
   int64_t *cursor = nullptr;      // nbins + 1 counts, then scatter cursors
   int64_t *bsum = nullptr;        // 2 (nbins / SCAN_CHUNK + 2) partial sums of the scan
   int64_t sorted_end = 0;         // particles [0, sorted_end) are binned
+  // work units of the tile kernel: each sort splits a tile's bin into units
+  // of at most `unit` particles, one CTA each (the deposit sums are exact, so
+  // the split changes no result)
+  int64_t unit = 0;               // particles per work unit
+  int64_t nunits = 0;             // work units of the binned particles
+  long long *units = nullptr;     // per unit: tile << 32 | index of the unit within its tile
+  int64_t units_cap = 0;
+  int64_t *ucount = nullptr;      // per tile: its units, then their exclusive scan (ntiles + 1)
+  int64_t *usum = nullptr;        // partial sums of that scan
 };
 constexpr int SCAN_CHUNK = 4096;  // bins per block of the multi-block scan
 
+// ---- batched launches over the members of an ensemble ------------------------
+// One launch covers the blocks of several members: slot k owns blocks
+// [off[k], off[k + 1]) of the grid and serves entry mem[k] of the step's
+// argument table.  off (n + 1 entries) and mem (n) live in device memory.
+struct EnsList {
+  const int *off = nullptr;
+  const int *mem = nullptr;
+  int n = 0;
+};
+// the slot of block b (binary search; every block of the grid has one)
+__device__ inline int ens_slot(const EnsList &L, unsigned b) {
+  int lo = 0, hi = L.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((unsigned)L.off[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 enum ProfSlot { PROF_PARTICLES = 0, PROF_REDUCE = 1, PROF_FILTER = 2, PROF_FIELDS = 3, PROF_INJECT = 4,
                 PROF_SORT = 5, PROF_N };
+
+// One FP32 member at one step as the batched grid kernels read it: the
+// member's grid and arrays, the flux buffers as the step starts, after its
+// filter passes and their scratch, and the step's injection.
+struct EnsFieldArg {
+  Grid G;
+  double *f[6];
+  double *Fin[3], *Ftmp[3], *Fout[3];  // flux written by the deposit; filter scratch; flux the E update reads
+  float *f32[6];
+  long long *acc[3];
+  size_t grid_elems;
+  long long *cnt;
+  double *sig;                         // two buffers of nth + 1
+  Parts32 p32;
+  int64_t inj_base, inj_id0;           // first slot and id of the step's injected pairs
+  double t_inj;                        // time at which the injection reads the field
+  double f_inj, inject_q;
+  uint64_t inject_seed, inj_step;
+  int inject, npp, inject_smooth, n_filt;
+  int lossy_i0;                        // first row of the lossy layer (-1: none)
+};
+
+// kinds of batched grid launch (block counts per member: ens_blocks)
+enum EnsKind { ENS_FLUX = 0, ENS_FILTER, ENS_NODES, ENS_LOSSY, ENS_GHOSTS, ENS_COPY32, ENS_SIGMA, ENS_WRITE,
+               ENS_NKIND };
 
 }  // namespace pic
 
@@ -101,6 +155,7 @@ struct pic_ctx {
   float *r_n32 = nullptr; // f_r(i) per padded row, FP32 (FP32 path)
   long long *acc[3] = {}; // fixed-point flux accumulators (FP32 path)
   alignas(64) unsigned char tile_maps[3][6 * 128] = {}; // FP32: field tensor maps per tile shape (TMA)
+  unsigned char *d_tile_maps = nullptr;  // the same maps in device memory (batched ensemble launches)
   double *Q = nullptr, *Qa = nullptr, *Qt = nullptr, *gsnap = nullptr;
   bool have_snap = false;
   double *sig = nullptr;  // injection: surface charge per cell, two buffers of nth + 1 (smoothing)
@@ -158,8 +213,31 @@ void particles64(pic_ctx *c, double t);
 int64_t compact64(pic_ctx *c);         // stable removal of dead slots; returns live count
 void charge64(pic_ctx *c, double *Q, double *Qa);
 void reduce_particles64(pic_ctx *c);   // kinetic energy, live count, total charge
+// batched launches over ensemble members (fields.cu); blocks: the launch's grid
+int ens_blocks(const pic_ctx *c, int kind);  // blocks one member needs in a launch of that kind
+void ens_fill_field_arg(const pic_ctx *c, EnsFieldArg *a);  // the member's arrays (not the step's values)
+void ens_filter(const EnsFieldArg *tab, const EnsList &L, int blocks, int pass, cudaStream_t s);
+void ens_b_half(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s);
+void ens_e_full(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s);
+void ens_lossy(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s);
+void ens_ghosts(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s);
+void ens_copy32(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s);
+void ens_inject_sigma(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s);
+void ens_inject_smooth(const EnsFieldArg *tab, const EnsList &L, int blocks, int pass, cudaStream_t s);
+void ens_inject_write(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s);
 // particles32.cu
 int tiles32_setup(pic_ctx *c);         // tensor maps of the field window (FP32 path, at creation)
+// batched tile kernel: members grouped by kind (specialisation x tile shape)
+constexpr int ENS_TILE_KINDS = 9;
+size_t ens_tile_arg_bytes();
+int ens_tile_kind(const pic_ctx *c);
+int64_t ens_tile_blocks(const pic_ctx *c);           // 0 when the member holds no particles
+void ens_tile_arg(pic_ctx *c, double t, void *out);  // the member's tile-kernel arguments at time t
+// launches the tile kernel of one kind over n members (host array of their
+// arguments, ens_tile_arg_bytes() each, and their block counts); returns the
+// number of kernels launched (members are taken in groups of up to 48)
+int ens_tiles32(int kind, const void *args, const int64_t *blocks, int n, cudaStream_t s);
+void ens_flux_from_acc(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s);
 void particles32(pic_ctx *c, double t);
 void flux_from_acc(pic_ctx *c);        // fixed point -> FP64 fluxes, clears the accumulators
 int64_t sort32(pic_ctx *c);            // tile sort + removal; returns live count

@@ -95,7 +95,7 @@ def lib():
         "pic_profile": [P, I32],
         "pic_get_profile": [P, D, C.POINTER(C.c_int64)],
         "pic_get_launches": [P, C.POINTER(C.c_int64)],
-        "pic_ensemble_step": [C.POINTER(C.c_void_p), I32, I32],
+        "pic_ensemble_step": [C.POINTER(C.c_void_p), I32, I32, C.POINTER(C.c_int64)],
         "pic_autotune": [P, I32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
         "pic_destroy": [P],
         "pic_get_axis_ties": [P, C.POINTER(C.c_int64), P, P, P],
@@ -417,5 +417,9 @@ def wait_selftest(polls, arrive_first, stream=0):
 
 
 def ensemble_step(sims, nsteps):
+    """Advance the simulations together (pic_ensemble_step); returns the
+    number of kernel launches the call enqueued."""
     arr = (C.c_void_p * len(sims))(*[s.h for s in sims])
-    return check(lib().pic_ensemble_step(arr, len(sims), nsteps))
+    k = C.c_int64(0)
+    check(lib().pic_ensemble_step(arr, len(sims), nsteps, C.byref(k)))
+    return k.value

@@ -160,6 +160,43 @@ def test_members_keep_their_own_sort_intervals():
         assert a.moments()["step"] == 60
 
 
+def test_one_launch_per_phase_for_all_members():
+    """FP32 members on all three tile shapes: each phase of a step is one
+    kernel launch for every member (one per tile shape for the tile kernel),
+    so the call enqueues a few launches per step however many members there
+    are, while each member's own count advances as in its pic_step run; every
+    member's result equals that run's bit for bit."""
+    from paper_1407_1810_gb300 import picsar as P
+
+    ens, ref = [], []
+    for m, shape in ((0, 0), (1, 1), (2, 2), (3, 0), (4, 1), (6, 2)):
+        cfg = _member_cfg(m)
+        s1, _, plasma, _ = setup(cfg, tile_shape=shape)
+        s2, _, _, _ = setup(cfg, plasma=plasma, tile_shape=shape)
+        ens.append(s1)
+        ref.append(s2)
+    l0 = [s.launches() for s in ens]
+    r0 = [s.launches() for s in ref]
+    kernels = P.ensemble_step(ens, 30)
+    for s in ref:
+        s.step(30)
+    member_launches = sum(s.launches() for s in ens) - sum(l0)
+    assert member_launches == sum(s.launches() for s in ref) - sum(r0)
+    # 3 tile shapes + flux + 3 Yee sub-steps + lossy + ghosts + copies per
+    # step; between graphs the sorts of the members (10 kernels each) and
+    # each member's Gauss-law snapshot before its first step (3 at most)
+    sorts = sum(30 // s.desc.sort_interval + 1 for s in ens)
+    assert kernels <= 30 * 10 + 10 * sorts + 3 * len(ens)
+    assert kernels < member_launches / 2
+    for k, (a, b) in enumerate(zip(ens, ref)):
+        assert np.array_equal(a.fields(), b.fields()), k
+        assert np.array_equal(a.flux(), b.flux()), k
+        pa, pb = a.particles(), b.particles()
+        oa, ob = np.argsort(pa["id"]), np.argsort(pb["id"])
+        for key in ("x1", "x2", "ur", "uth", "uph", "qw"):
+            assert np.array_equal(pa[key][oa], pb[key][ob]), (k, key)
+
+
 def test_ensemble_member_against_the_oracle():
     """One member of a batched FP32 ensemble, 100 steps, against the FP64
     oracle run from the same state (following the member's branches at

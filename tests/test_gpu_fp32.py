@@ -107,6 +107,28 @@ def test_rotator_injection_filter_fp32(th_map):
     assert m["gauss_residual"] < 1e-6
 
 
+def test_dense_tiles_split_into_work_units():
+    """About 300 particles per cell, one bin of ~70 000 particles per tile:
+    each bin is split into work units of 4096 particles, one CTA each.  The
+    units partition the bin, so the result matches the oracle at the FP32 bar
+    and every tile shape (other splits) bit for bit."""
+    cfg = _cfg(nr=16, nth=16, pairs_per_cell=150, T=0.3)
+    s, o, plasma, dt = setup(cfg)
+    o.gauss_snapshot()
+    s.step(30)
+    follow_ties(s, o)
+    o.step(30)
+    close(s.fields(), o.fields(), FIELD_TOL, MAX_FP32)
+    m = s.moments()
+    assert m["gauss_residual"] < 1e-6
+    assert abs(m["live"] - o.num_particles()) <= max(1, 1e-4 * o.num_particles())
+    for shape in (1, 2):
+        s2, _, _, _ = setup(cfg, plasma=plasma, tile_shape=shape)
+        s2.step(30)
+        assert np.array_equal(s2.fields(), s.fields()), shape
+        s2.close()
+
+
 @pytest.mark.parametrize("sort_interval", [1, 1000])
 def test_window_and_global_paths_agree(sort_interval):
     """sort_interval 1000: particles drift out of their tile windows and take
