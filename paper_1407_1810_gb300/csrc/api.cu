@@ -1127,21 +1127,23 @@ constexpr int ENS_MAX_BLOCK = 64;  // steps per graph at most
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// one step's block lists, built on the host, and the tile kernel's member
-// arguments (passed as kernel parameters) per kind
-struct StepLists {
-  std::vector<std::vector<int>> off, mem;  // per list: offsets (slots + 1), member entries
-  std::vector<unsigned char> targ[ENS_TILE_KINDS];
-  std::vector<int64_t> tblk[ENS_TILE_KINDS];
-  void reset(int nlists) {
-    off.assign(nlists, std::vector<int>(1, 0));
-    mem.assign(nlists, std::vector<int>());
-    for (int q = 0; q < ENS_TILE_KINDS; ++q) { targ[q].clear(); tblk[q].clear(); }
+// Block maps of the grid phases: for each launch, every block's member and
+// its block within that member ({member, block}); fixed for the call.
+struct PhaseMaps {
+  std::vector<std::vector<int2>> blk;
+  explicit PhaseMaps(int nlists) : blk(nlists) {}
+  void add(int list, int member, int blocks) {
+    for (int b = 0; b < blocks; ++b) blk[list].push_back(make_int2(member, b));
   }
-  void add(int list, int member, int64_t blocks) {
-    if (blocks <= 0) return;
-    mem[list].push_back(member);
-    off[list].push_back(off[list].back() + (int)blocks);
+  int blocks(int list) const { return (int)blk[list].size(); }
+};
+
+// the tile kernel's member arguments (kernel parameters) of one step, per kind
+struct StepTiles {
+  std::vector<unsigned char> arg[ENS_TILE_KINDS];
+  std::vector<int64_t> blocks[ENS_TILE_KINDS];
+  void reset() {
+    for (int q = 0; q < ENS_TILE_KINDS; ++q) { arg[q].clear(); blocks[q].clear(); }
   }
 };
 
@@ -1153,17 +1155,36 @@ static int ensemble_batched(pic_ctx *const *ctxs, int n, int nsteps, int64_t *ke
     max_filt = std::max(max_filt, ctxs[k]->d.n_filt);
     if (ctxs[k]->d.inject) max_smooth = std::max(max_smooth, ctxs[k]->d.inject_smooth);
   }
-  // lists of one step: the grid phases in launch order
-  const int L_FLUX = 0, L_FILT = L_FLUX + 1, L_NODES = L_FILT + max_filt,
-            L_LOSSY = L_NODES + 1, L_GHOSTS = L_LOSSY + 1, L_COPY = L_GHOSTS + 1, L_SIGMA = L_COPY + 1,
-            L_SMOOTH = L_SIGMA + 1, L_WRITE = L_SMOOTH + max_smooth, NLISTS = L_WRITE + 1;
+  // the grid phases in launch order, and which members take part in each
+  const int L_FLUX = 0, L_FILT = L_FLUX + 1, L_NODES = L_FILT + max_filt, L_LOSSY = L_NODES + 1,
+            L_GHOSTS = L_LOSSY + 1, L_COPY = L_GHOSTS + 1, L_SIGMA = L_COPY + 1, L_SMOOTH = L_SIGMA + 1,
+            L_WRITE = L_SMOOTH + max_smooth, NLISTS = L_WRITE + 1;
+  PhaseMaps maps(NLISTS);
+  for (int k = 0; k < n; ++k) {
+    const pic_ctx *c = ctxs[k];
+    maps.add(L_FLUX, k, ens_blocks(c, ENS_FLUX));
+    for (int p = 0; p < c->d.n_filt; ++p) maps.add(L_FILT + p, k, ens_blocks(c, ENS_FILTER));
+    maps.add(L_NODES, k, ens_blocks(c, ENS_NODES));
+    maps.add(L_LOSSY, k, ens_blocks(c, ENS_LOSSY));
+    maps.add(L_GHOSTS, k, ens_blocks(c, ENS_GHOSTS));
+    maps.add(L_COPY, k, ens_blocks(c, ENS_COPY32));
+    if (c->d.inject) {
+      maps.add(L_SIGMA, k, ens_blocks(c, ENS_SIGMA));
+      for (int p = 0; p < c->d.inject_smooth; ++p) maps.add(L_SMOOTH + p, k, ens_blocks(c, ENS_SIGMA));
+      maps.add(L_WRITE, k, ens_blocks(c, ENS_WRITE));
+    }
+  }
+  std::vector<size_t> map_at(NLISTS + 1, 0);
+  for (int q = 0; q < NLISTS; ++q) map_at[q + 1] = map_at[q] + maps.blk[q].size();
   const size_t tile_bytes = ens_tile_arg_bytes();
-  const size_t field_sz = align_up((size_t)n * sizeof(EnsFieldArg), 256);
-  const size_t list_ints = (size_t)NLISTS * (2 * (size_t)n + 1);
-  const size_t step_sz = field_sz + align_up(list_ints * sizeof(int), 256);
+  const size_t step_sz = align_up((size_t)n * sizeof(EnsFieldArg), 256);
   unsigned char *h_tab = nullptr, *d_tab = nullptr;
+  int2 *d_maps = nullptr;
   PIC_CUDA(cudaMallocHost((void **)&h_tab, step_sz * ENS_MAX_BLOCK));
-  if (cudaMalloc((void **)&d_tab, step_sz * ENS_MAX_BLOCK) != cudaSuccess) {
+  if (cudaMalloc((void **)&d_tab, step_sz * ENS_MAX_BLOCK) != cudaSuccess ||
+      cudaMalloc((void **)&d_maps, std::max<size_t>(1, map_at[NLISTS]) * sizeof(int2)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(d_tab);
     cudaFreeHost(h_tab);
     return pic_fail(PIC_ENOMEM, "ensemble argument tables");
   }
@@ -1173,15 +1194,16 @@ static int ensemble_batched(pic_ctx *const *ctxs, int n, int nsteps, int64_t *ke
   if (cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&after, cudaEventDisableTiming) != cudaSuccess)
     err = pic_fail(PIC_ECUDA, "ensemble stream");
+  for (int q = 0; q < NLISTS && !err; ++q)
+    if (!maps.blk[q].empty() &&
+        cudaMemcpy(d_maps + map_at[q], maps.blk[q].data(), maps.blk[q].size() * sizeof(int2),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      err = pic_fail(PIC_ECUDA, "ensemble block maps");
   for (int k = 0; k < n && !err; ++k) {
     cudaError_t ce = cudaStreamSynchronize(ctxs[k]->stream);  // earlier work of each member first
     if (ce != cudaSuccess) err = pic_cuda_check(ce, "ensemble member stream");
   }
-  // per member, the blocks of each grid phase (fixed for the call)
-  std::vector<std::array<int, ENS_NKIND>> nb(n);
-  for (int k = 0; k < n; ++k)
-    for (int q = 0; q < ENS_NKIND; ++q) nb[k][q] = ens_blocks(ctxs[k], q);
-  std::vector<StepLists> lists(ENS_MAX_BLOCK);
+  std::vector<StepTiles> tiles(ENS_MAX_BLOCK);
   cudaGraphExec_t exec = nullptr;
   int64_t launched = 0;
   int done = 0;
@@ -1198,47 +1220,35 @@ static int ensemble_batched(pic_ctx *const *ctxs, int n, int nsteps, int64_t *ke
       if (!err) cudaStreamSynchronize(ctxs[k]->stream);
     }
     if (err) break;
-    // the members' arguments and block lists for each step; the host state
-    // advances as step_body advances it
+    // the members' arguments for each step; the host state advances as
+    // step_body advances it (each member's launch count by the launches its
+    // own step takes)
     for (int st = 0; st < block; ++st) {
-      unsigned char *base = h_tab + (size_t)st * step_sz;
-      EnsFieldArg *fa = reinterpret_cast<EnsFieldArg *>(base);
-      StepLists &SL = lists[st];
-      SL.reset(NLISTS);
+      EnsFieldArg *fa = reinterpret_cast<EnsFieldArg *>(h_tab + (size_t)st * step_sz);
+      StepTiles &T = tiles[st];
+      T.reset();
       for (int k = 0; k < n; ++k) {
         pic_ctx *c = ctxs[k];
         const Grid &G = c->G;
         const int64_t tb = ens_tile_blocks(c);
         if (tb > 0) {
           const int kind = ens_tile_kind(c);
-          std::vector<unsigned char> &ta = SL.targ[kind];
+          std::vector<unsigned char> &ta = T.arg[kind];
           ta.resize(ta.size() + tile_bytes);
           ens_tile_arg(c, c->step * G.dt, ta.data() + ta.size() - tile_bytes);
-          SL.tblk[kind].push_back(tb);
+          T.blocks[kind].push_back(tb);
           ++c->launches;
         }
         ens_fill_field_arg(c, &fa[k]);
-        SL.add(L_FLUX, k, nb[k][ENS_FLUX]);
-        ++c->launches;
-        for (int p = 0; p < c->d.n_filt; ++p) SL.add(L_FILT + p, k, nb[k][ENS_FILTER]);
-        c->launches += 3 * (int64_t)std::max(0, c->d.n_filt);
+        c->launches += 1 + 3 * (int64_t)c->d.n_filt + 3 + (ens_blocks(c, ENS_LOSSY) > 0) + 2;
         if (c->d.n_filt & 1)
           for (int q = 0; q < 3; ++q) std::swap(c->F[q], c->Ft[q]);
-        SL.add(L_NODES, k, nb[k][ENS_NODES]);
-        c->launches += 3;
-        if (nb[k][ENS_LOSSY] > 0) { SL.add(L_LOSSY, k, nb[k][ENS_LOSSY]); ++c->launches; }
-        SL.add(L_GHOSTS, k, nb[k][ENS_GHOSTS]);
-        SL.add(L_COPY, k, nb[k][ENS_COPY32]);
-        c->launches += 2;
         c->step += 1;
         if (c->d.inject) {
           fa[k].t_inj = c->step * G.dt;
           fa[k].inj_base = c->n_used;
           fa[k].inj_id0 = c->next_id;
           fa[k].inj_step = (uint64_t)c->step;
-          SL.add(L_SIGMA, k, nb[k][ENS_SIGMA]);
-          for (int p = 0; p < c->d.inject_smooth; ++p) SL.add(L_SMOOTH + p, k, nb[k][ENS_SIGMA]);
-          SL.add(L_WRITE, k, nb[k][ENS_WRITE]);
           c->launches += 2 + c->d.inject_smooth;
           const int64_t nslots = (int64_t)G.nth * c->d.pairs_per_cell * 2;
           c->n_used += nslots;
@@ -1246,51 +1256,40 @@ static int ensemble_batched(pic_ctx *const *ctxs, int n, int nsteps, int64_t *ke
         }
         c->steps_since_sort += 1;
       }
-      int *li = reinterpret_cast<int *>(base + field_sz);
-      for (int q = 0; q < NLISTS; ++q) {
-        int *o = li + (size_t)q * (2 * n + 1);
-        std::copy(SL.off[q].begin(), SL.off[q].end(), o);
-        std::copy(SL.mem[q].begin(), SL.mem[q].end(), o + n + 1);
-      }
     }
     cudaError_t ce = cudaMemcpyAsync(d_tab, h_tab, step_sz * block, cudaMemcpyHostToDevice, origin);
     cudaGraph_t graph = nullptr;
     int64_t nodes = 0;
     if (ce == cudaSuccess) ce = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
     if (ce == cudaSuccess) {
+      auto L = [&](int q) {
+        EnsList x;
+        x.blk = d_maps + map_at[q];
+        return x;
+      };
       for (int st = 0; st < block; ++st) {
-        unsigned char *dbase = d_tab + (size_t)st * step_sz;
-        const EnsFieldArg *dfa = reinterpret_cast<const EnsFieldArg *>(dbase);
-        const int *dli = reinterpret_cast<const int *>(dbase + field_sz);
-        const StepLists &SL = lists[st];
-        auto L = [&](int q) {
-          EnsList x;
-          x.off = dli + (size_t)q * (2 * n + 1);
-          x.mem = x.off + n + 1;
-          x.n = (int)SL.mem[q].size();
-          return x;
-        };
-        auto blocks = [&](int q) { return SL.off[q].back(); };
+        const EnsFieldArg *dfa = reinterpret_cast<const EnsFieldArg *>(d_tab + (size_t)st * step_sz);
+        const StepTiles &T = tiles[st];
         for (int kind = 0; kind < ENS_TILE_KINDS; ++kind)
-          if (!SL.tblk[kind].empty())
-            nodes += ens_tiles32(kind, SL.targ[kind].data(), SL.tblk[kind].data(), (int)SL.tblk[kind].size(), origin);
-        ens_flux_from_acc(dfa, L(L_FLUX), blocks(L_FLUX), origin), ++nodes;
+          if (!T.blocks[kind].empty())
+            nodes += ens_tiles32(kind, T.arg[kind].data(), T.blocks[kind].data(), (int)T.blocks[kind].size(), origin);
+        ens_flux_from_acc(dfa, L(L_FLUX), maps.blocks(L_FLUX), origin), ++nodes;
         for (int p = 0; p < max_filt; ++p)
-          if (blocks(L_FILT + p) > 0) ens_filter(dfa, L(L_FILT + p), blocks(L_FILT + p), p, origin), ++nodes;
-        ens_b_half(dfa, L(L_NODES), blocks(L_NODES), origin);
-        ens_e_full(dfa, L(L_NODES), blocks(L_NODES), origin);
-        ens_b_half(dfa, L(L_NODES), blocks(L_NODES), origin);
+          if (maps.blocks(L_FILT + p) > 0) ens_filter(dfa, L(L_FILT + p), maps.blocks(L_FILT + p), p, origin), ++nodes;
+        ens_b_half(dfa, L(L_NODES), maps.blocks(L_NODES), origin);
+        ens_e_full(dfa, L(L_NODES), maps.blocks(L_NODES), origin);
+        ens_b_half(dfa, L(L_NODES), maps.blocks(L_NODES), origin);
         nodes += 3;
-        if (blocks(L_LOSSY) > 0) ens_lossy(dfa, L(L_LOSSY), blocks(L_LOSSY), origin), ++nodes;
-        ens_ghosts(dfa, L(L_GHOSTS), blocks(L_GHOSTS), origin);
-        ens_copy32(dfa, L(L_COPY), blocks(L_COPY), origin);
+        if (maps.blocks(L_LOSSY) > 0) ens_lossy(dfa, L(L_LOSSY), maps.blocks(L_LOSSY), origin), ++nodes;
+        ens_ghosts(dfa, L(L_GHOSTS), maps.blocks(L_GHOSTS), origin);
+        ens_copy32(dfa, L(L_COPY), maps.blocks(L_COPY), origin);
         nodes += 2;
-        if (blocks(L_SIGMA) > 0) {
-          ens_inject_sigma(dfa, L(L_SIGMA), blocks(L_SIGMA), origin), ++nodes;
+        if (maps.blocks(L_SIGMA) > 0) {
+          ens_inject_sigma(dfa, L(L_SIGMA), maps.blocks(L_SIGMA), origin), ++nodes;
           for (int p = 0; p < max_smooth; ++p)
-            if (blocks(L_SMOOTH + p) > 0)
-              ens_inject_smooth(dfa, L(L_SMOOTH + p), blocks(L_SMOOTH + p), p, origin), ++nodes;
-          ens_inject_write(dfa, L(L_WRITE), blocks(L_WRITE), origin), ++nodes;
+            if (maps.blocks(L_SMOOTH + p) > 0)
+              ens_inject_smooth(dfa, L(L_SMOOTH + p), maps.blocks(L_SMOOTH + p), p, origin), ++nodes;
+          ens_inject_write(dfa, L(L_WRITE), maps.blocks(L_WRITE), origin), ++nodes;
         }
       }
       cudaError_t ce2 = cudaStreamEndCapture(origin, &graph);
@@ -1331,6 +1330,7 @@ static int ensemble_batched(pic_ctx *const *ctxs, int n, int nsteps, int64_t *ke
   if (exec) cudaGraphExecDestroy(exec);
   if (after) cudaEventDestroy(after);
   if (origin) cudaStreamDestroy(origin);
+  cudaFree(d_maps);
   cudaFree(d_tab);
   cudaFreeHost(h_tab);
   if (kernels) *kernels = launched;

@@ -113,16 +113,28 @@ __global__ void k_axis_ghosts(Grid G, double *Et, double *Br, double *Bp) {
   ghost_row(G, blockIdx.x * blockDim.x + threadIdx.x, Et, Br, Bp);
 }
 
-// FP32 gather copies of the six components over the whole padded array
-// (the gather-prep step of the FP32 path).
-__global__ void k_copy32(size_t n, const double *__restrict__ a0, const double *__restrict__ a1,
+// FP32 gather copies of the six components (the gather-prep step of the FP32
+// path) over rows -g..nr+g and columns -1..nth: every node the gather can
+// read.  The FP64 fields are zero outside rows 0..nr and columns -1..nth (no
+// kernel writes there), and so are the FP32 copies from their allocation, so
+// the padding beyond needs no copy.
+__device__ __forceinline__ void copy32_node(const Grid &G, int i, int j, const double *__restrict__ a0,
+                                            const double *__restrict__ a1, const double *__restrict__ a2,
+                                            const double *__restrict__ a3, const double *__restrict__ a4,
+                                            const double *__restrict__ a5, float *b0, float *b1, float *b2,
+                                            float *b3, float *b4, float *b5) {
+  if (i > G.nr + G.g || j > G.nth) return;
+  const size_t k = gidx(G, i, j);
+  b0[k] = (float)a0[k]; b1[k] = (float)a1[k]; b2[k] = (float)a2[k];
+  b3[k] = (float)a3[k]; b4[k] = (float)a4[k]; b5[k] = (float)a5[k];
+}
+
+__global__ void k_copy32(Grid G, const double *__restrict__ a0, const double *__restrict__ a1,
                          const double *__restrict__ a2, const double *__restrict__ a3,
                          const double *__restrict__ a4, const double *__restrict__ a5, float *b0, float *b1,
                          float *b2, float *b3, float *b4, float *b5) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    b0[k] = (float)a0[k]; b1[k] = (float)a1[k]; b2[k] = (float)a2[k];
-    b3[k] = (float)a3[k]; b4[k] = (float)a4[k]; b5[k] = (float)a5[k];
-  }
+  copy32_node(G, -G.g + (int)(blockIdx.y * BY + threadIdx.y), (int)(blockIdx.x * BX + threadIdx.x) - 1, a0, a1, a2,
+              a3, a4, a5, b0, b1, b2, b3, b4, b5);
 }
 
 // One 1-2-1 pass (Eq. filtereq) with the polar remap of App. B: weights V_l(j)
@@ -369,11 +381,11 @@ __device__ inline Node2 node_of(unsigned b, int nj, int i_first) {
 // pass `pass` of the filter on all three flux components: even passes read
 // the deposit's buffers and write the scratch, odd passes the reverse
 __global__ void k_ens_filter(const EnsFieldArg *__restrict__ tab, EnsList L, int pass) {
-  const int k = ens_slot(L, blockIdx.x);
-  const EnsFieldArg &E = tab[L.mem[k]];
+  const int2 e = L.blk[blockIdx.x];
+  const EnsFieldArg &E = tab[e.x];
   const Grid &G = E.G;
   const unsigned per = (unsigned)((G.nth + 1 + BX - 1) / BX) * (unsigned)((G.nr + 2 * G.g + 1 + BY - 1) / BY);
-  const unsigned b = blockIdx.x - (unsigned)L.off[k];
+  const unsigned b = (unsigned)e.y;
   const int comp = (int)(b / per);
   const Node2 n = node_of(b % per, G.nth + 1, -G.g);
   const double *in = (pass & 1) ? E.Ftmp[comp] : E.Fin[comp];
@@ -382,45 +394,43 @@ __global__ void k_ens_filter(const EnsFieldArg *__restrict__ tab, EnsList L, int
 }
 
 __global__ void k_ens_b_half(const EnsFieldArg *__restrict__ tab, EnsList L) {
-  const int k = ens_slot(L, blockIdx.x);
-  const EnsFieldArg &E = tab[L.mem[k]];
-  const Node2 n = node_of(blockIdx.x - (unsigned)L.off[k], E.G.nth + 1, 0);
+  const int2 e = L.blk[blockIdx.x];
+  const EnsFieldArg &E = tab[e.x];
+  const Node2 n = node_of((unsigned)e.y, E.G.nth + 1, 0);
   b_half_node(E.G, n.i, n.j, E.f[ER], E.f[ETH], E.f[EPH], E.f[BR], E.f[BTH], E.f[BPH]);
 }
 
 __global__ void k_ens_e_full(const EnsFieldArg *__restrict__ tab, EnsList L) {
-  const int k = ens_slot(L, blockIdx.x);
-  const EnsFieldArg &E = tab[L.mem[k]];
-  const Node2 n = node_of(blockIdx.x - (unsigned)L.off[k], E.G.nth + 1, 0);
+  const int2 e = L.blk[blockIdx.x];
+  const EnsFieldArg &E = tab[e.x];
+  const Node2 n = node_of((unsigned)e.y, E.G.nth + 1, 0);
   e_full_node(E.G, n.i, n.j, E.f[ER], E.f[ETH], E.f[EPH], E.f[BR], E.f[BTH], E.f[BPH], E.Fout[0], E.Fout[1],
               E.Fout[2]);
 }
 
 __global__ void k_ens_lossy(const EnsFieldArg *__restrict__ tab, EnsList L) {
-  const int k = ens_slot(L, blockIdx.x);
-  const EnsFieldArg &E = tab[L.mem[k]];
-  const Node2 n = node_of(blockIdx.x - (unsigned)L.off[k], E.G.nth + 1, E.lossy_i0);
+  const int2 e = L.blk[blockIdx.x];
+  const EnsFieldArg &E = tab[e.x];
+  const Node2 n = node_of((unsigned)e.y, E.G.nth + 1, E.lossy_i0);
   lossy_node(E.G, n.i, n.j, E.f[0], E.f[1], E.f[2], E.f[3], E.f[4], E.f[5]);
 }
 
 // axis ghosts; block 0 of a member that injects also clears the surface
 // charge maximum its injection will raise later in the step
 __global__ void k_ens_ghosts(const EnsFieldArg *__restrict__ tab, EnsList L) {
-  const int k = ens_slot(L, blockIdx.x);
-  const EnsFieldArg &E = tab[L.mem[k]];
-  const unsigned b = blockIdx.x - (unsigned)L.off[k];
+  const int2 e = L.blk[blockIdx.x];
+  const EnsFieldArg &E = tab[e.x];
+  const unsigned b = (unsigned)e.y;
   if (b == 0 && threadIdx.x == 0 && E.inject) E.cnt[CNT_SMAX] = 0;
   ghost_row(E.G, (int)(b * blockDim.x + threadIdx.x), E.f[ETH], E.f[BR], E.f[BPH]);
 }
 
 __global__ void k_ens_copy32(const EnsFieldArg *__restrict__ tab, EnsList L) {
-  const int k = ens_slot(L, blockIdx.x);
-  const EnsFieldArg &E = tab[L.mem[k]];
-  const size_t nb = (size_t)(L.off[k + 1] - L.off[k]), b = blockIdx.x - (unsigned)L.off[k];
-  for (size_t q = b * blockDim.x + threadIdx.x; q < E.grid_elems; q += nb * blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < 6; ++c) E.f32[c][q] = (float)E.f[c][q];
-  }
+  const int2 e = L.blk[blockIdx.x];
+  const EnsFieldArg &E = tab[e.x];
+  const Node2 n = node_of((unsigned)e.y, E.G.nth + 2, -E.G.g);
+  copy32_node(E.G, n.i, n.j - 1, E.f[0], E.f[1], E.f[2], E.f[3], E.f[4], E.f[5], E.f32[0], E.f32[1], E.f32[2],
+              E.f32[3], E.f32[4], E.f32[5]);
 }
 
 __device__ inline InjectRule ens_rule(const EnsFieldArg &E) {
@@ -428,25 +438,25 @@ __device__ inline InjectRule ens_rule(const EnsFieldArg &E) {
 }
 
 __global__ void k_ens_sigma(const EnsFieldArg *__restrict__ tab, EnsList L) {
-  const int k = ens_slot(L, blockIdx.x);
-  const EnsFieldArg &E = tab[L.mem[k]];
-  const int j = (int)((blockIdx.x - (unsigned)L.off[k]) * blockDim.x + threadIdx.x);
+  const int2 e = L.blk[blockIdx.x];
+  const EnsFieldArg &E = tab[e.x];
+  const int j = (int)(((unsigned)e.y) * blockDim.x + threadIdx.x);
   sigma_cell(E.G, j, E.f[ER], E.t_inj, E.sig, E.inject_smooth ? nullptr : E.cnt + CNT_SMAX);
 }
 
 __global__ void k_ens_smooth(const EnsFieldArg *__restrict__ tab, EnsList L, int pass) {
-  const int k = ens_slot(L, blockIdx.x);
-  const EnsFieldArg &E = tab[L.mem[k]];
-  const int j = (int)((blockIdx.x - (unsigned)L.off[k]) * blockDim.x + threadIdx.x), nth = E.G.nth;
+  const int2 e = L.blk[blockIdx.x];
+  const EnsFieldArg &E = tab[e.x];
+  const int j = (int)(((unsigned)e.y) * blockDim.x + threadIdx.x), nth = E.G.nth;
   const double *in = (pass & 1) ? E.sig + (nth + 1) : E.sig;
   double *out = (pass & 1) ? E.sig : E.sig + (nth + 1);
   smooth_cell(j, nth, in, out, pass == E.inject_smooth - 1 ? E.cnt + CNT_SMAX : nullptr);
 }
 
 __global__ void k_ens_write(const EnsFieldArg *__restrict__ tab, EnsList L) {
-  const int k = ens_slot(L, blockIdx.x);
-  const EnsFieldArg &E = tab[L.mem[k]];
-  const int64_t idx = (int64_t)(blockIdx.x - (unsigned)L.off[k]) * blockDim.x + threadIdx.x;
+  const int2 e = L.blk[blockIdx.x];
+  const EnsFieldArg &E = tab[e.x];
+  const int64_t idx = (int64_t)((unsigned)e.y) * blockDim.x + threadIdx.x;
   const double *sig = (E.inject_smooth & 1) ? E.sig + (E.G.nth + 1) : E.sig;
   const Parts64 none;
   inject_slot<true>(idx, E.G, sig, E.cnt + CNT_SMAX, none, E.p32, E.inj_base, E.inj_id0, ens_rule(E),
@@ -470,7 +480,7 @@ int ens_blocks(const pic_ctx *c, int kind) {
       return gx * div_up(G.nr + 1 - i0, BY);
     }
     case ENS_GHOSTS: return div_up(G.nr + 1, 256);
-    case ENS_COPY32: return (int)std::min<int64_t>(4 * 152, div_up((int64_t)c->grid_elems, 256));
+    case ENS_COPY32: return div_up(G.nth + 2, BX) * div_up(G.nr + 2 * G.g + 1, BY);
     case ENS_SIGMA: return c->d.inject ? div_up(G.nth, 256) : 0;
     case ENS_WRITE: return c->d.inject ? div_up((int64_t)G.nth * c->d.pairs_per_cell * 2, 256) : 0;
     default: return 0;
@@ -546,8 +556,9 @@ void fields_fill_ghosts(pic_ctx *c) {
   const Grid &G = c->G;
   ++c->launches, k_axis_ghosts<<<(G.nr + 1 + 127) / 128, 128, 0, c->stream>>>(G, c->f[ETH], c->f[BR], c->f[BPH]);
   if (c->d.precision == PIC_FP32) {
-    ++c->launches, k_copy32<<<4 * 152, 256, 0, c->stream>>>(c->grid_elems, c->f[0], c->f[1], c->f[2], c->f[3], c->f[4], c->f[5],
-                                            c->f32[0], c->f32[1], c->f32[2], c->f32[3], c->f32[4], c->f32[5]);
+    ++c->launches, k_copy32<<<grid2(G.nr + 2 * G.g + 1, G.nth + 2), dim3(BX, BY), 0, c->stream>>>(
+        G, c->f[0], c->f[1], c->f[2], c->f[3], c->f[4], c->f[5], c->f32[0], c->f32[1], c->f32[2], c->f32[3], c->f32[4],
+        c->f32[5]);
   }
 }
 

@@ -745,10 +745,10 @@ __global__ void k_flux_from_acc(int nr, int nth, int g, int PI, int PJ, int LD, 
 // the same over the members of an ensemble: 256-thread blocks, each member's
 // band covered by 32 x 8 node blocks as above
 __global__ void k_ens_flux(const EnsFieldArg *__restrict__ tab, EnsList L) {
-  const int k = ens_slot(L, blockIdx.x);
-  const EnsFieldArg &E = tab[L.mem[k]];
+  const int2 e = L.blk[blockIdx.x];
+  const EnsFieldArg &E = tab[e.x];
   const Grid &G = E.G;
-  const unsigned b = blockIdx.x - (unsigned)L.off[k], gx = (unsigned)(G.nth + 1 + 31) / 32;
+  const unsigned b = (unsigned)e.y, gx = (unsigned)(G.nth + 1 + 31) / 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   flux_node(-G.g + (int)((b / gx) * 8 + ty), (int)((b % gx) * 32 + tx), G.nr, G.nth, G.g, G.PI, G.LD, G.PJ,
             E.cnt + CNT_QEXP, E.acc[0], E.acc[1], E.acc[2], E.Fin[0], E.Fin[1], E.Fin[2]);

@@ -92,24 +92,12 @@ struct Tiles {
 constexpr int SCAN_CHUNK = 4096;  // bins per block of the multi-block scan
 
 // ---- batched launches over the members of an ensemble ------------------------
-// One launch covers the blocks of several members: slot k owns blocks
-// [off[k], off[k + 1]) of the grid and serves entry mem[k] of the step's
-// argument table.  off (n + 1 entries) and mem (n) live in device memory.
+// One launch covers the blocks of several members: block b of the grid serves
+// entry blk[b].x of the step's argument table as that member's block blk[b].y
+// (one load per block; the map lives in device memory).
 struct EnsList {
-  const int *off = nullptr;
-  const int *mem = nullptr;
-  int n = 0;
+  const int2 *blk = nullptr;
 };
-// the slot of block b (binary search; every block of the grid has one)
-__device__ inline int ens_slot(const EnsList &L, unsigned b) {
-  int lo = 0, hi = L.n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if ((unsigned)L.off[mid] <= b) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
 
 enum ProfSlot { PROF_PARTICLES = 0, PROF_REDUCE = 1, PROF_FILTER = 2, PROF_FIELDS = 3, PROF_INJECT = 4,
                 PROF_SORT = 5, PROF_N };
