@@ -315,6 +315,19 @@ int pic_ensemble_step(pic_ctx *const *ctxs, int32_t n, int32_t nsteps, int64_t *
  * small members of an ensemble.  FP64 contexts: PIC_EINVAL. */
 int pic_autotune(pic_ctx *c, int32_t trial_steps, int32_t *sort_interval, int32_t *tile_shape);
 
+/* The same choice for an ensemble as a whole: every candidate (3 tile shapes x
+ * sort intervals 10, 20, 40) runs on clones of all n members through
+ * pic_ensemble_step (one sort cycle of warm-up, then max(trial_steps, 2 x
+ * interval) steps timed on the host clock, which includes the batched step's
+ * host work), and the fastest pair is applied to every member: one shape and
+ * one interval keep each step's tile launches and sorts to one batch each.
+ * The members do not advance.  Holds a clone of every member at once (about
+ * twice the ensemble's device memory).  ctxs: n distinct FP32 contexts on one
+ * device.  Errors: PIC_EINVAL (NULL, repeated or FP64 members, trial_steps <
+ * 1), PIC_ENOMEM, PIC_ECUDA. */
+int pic_autotune_ensemble(pic_ctx *const *ctxs, int32_t n, int32_t trial_steps, int32_t *sort_interval,
+                          int32_t *tile_shape);
+
 /* Release every device buffer of the context.  NULL is allowed. */
 int pic_destroy(pic_ctx *c);
 

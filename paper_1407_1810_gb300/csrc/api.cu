@@ -2,6 +2,7 @@
 // particle loading, the step sequence and the getters.
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1204,6 +1205,8 @@ static int ensemble_batched(pic_ctx *const *ctxs, int n, int nsteps, int64_t *ke
     if (ce != cudaSuccess) err = pic_cuda_check(ce, "ensemble member stream");
   }
   std::vector<StepTiles> tiles(ENS_MAX_BLOCK);
+  std::vector<pic_ctx *> due;
+  EnsSortScratch sort_scratch;
   cudaGraphExec_t exec = nullptr;
   int64_t launched = 0;
   int done = 0;
@@ -1314,14 +1317,17 @@ static int ensemble_batched(pic_ctx *const *ctxs, int n, int nsteps, int64_t *ke
     if (ce != cudaSuccess) { err = pic_cuda_check(ce, "ensemble graph"); break; }
     launched += nodes;
     done += block;
-    for (int k = 0; k < n && !err; ++k) {
+    // the members whose sort is due, sorted together after the graph
+    due.clear();
+    for (int k = 0; k < n; ++k) {
       pic_ctx *c = ctxs[k];
       cudaStreamWaitEvent(c->stream, after, 0);
-      if (c->steps_since_sort >= c->d.sort_interval) {
-        const int64_t l0 = c->launches;
-        err = compact(c);
-        launched += c->launches - l0;
-      }
+      if (c->steps_since_sort >= c->d.sort_interval) due.push_back(c);
+    }
+    if (!due.empty()) {
+      int64_t nk = 0;
+      err = ens_sort32(due.data(), (int)due.size(), origin, sort_scratch, &nk);
+      launched += nk;
     }
     // the staging table is refilled next: its copy must have completed
     if (!err) cudaEventSynchronize(after);
@@ -1330,6 +1336,7 @@ static int ensemble_batched(pic_ctx *const *ctxs, int n, int nsteps, int64_t *ke
   if (exec) cudaGraphExecDestroy(exec);
   if (after) cudaEventDestroy(after);
   if (origin) cudaStreamDestroy(origin);
+  ens_sort_scratch_free(sort_scratch);
   cudaFree(d_maps);
   cudaFree(d_tab);
   cudaFreeHost(h_tab);
@@ -1460,6 +1467,63 @@ extern "C" int pic_autotune(pic_ctx *c, int32_t trial_steps, int32_t *sort_inter
   if (err) return err;
   c->d.sort_interval = best_s;
   if (best_shape != c->d.tile_shape && (err = set_tiles(c, best_shape))) return err;
+  if (sort_interval) *sort_interval = best_s;
+  if (tile_shape) *tile_shape = best_shape;
+  return PIC_OK;
+}
+
+// One tile shape and sort interval for every member of an ensemble, by
+// measurement of the batched step itself: each candidate runs on clones of all
+// members through pic_ensemble_step, timed on the host clock (the batched
+// step's cost includes its host work), and the fastest is applied to every
+// member.  A shape and an interval shared by all members keep each step's tile
+// launches and sorts to one batch each.
+extern "C" int pic_autotune_ensemble(pic_ctx *const *ctxs, int32_t n, int32_t trial_steps, int32_t *sort_interval,
+                                     int32_t *tile_shape) {
+  if (!ctxs || n <= 0 || trial_steps < 1) return pic_fail(PIC_EINVAL, "bad autotune arguments");
+  for (int k = 0; k < n; ++k) {
+    if (!ctxs[k]) return pic_fail(PIC_EINVAL, "null ensemble member");
+    if (ctxs[k]->d.precision != PIC_FP32) return pic_fail(PIC_EINVAL, "autotune applies to the FP32 path");
+    for (int q = 0; q < k; ++q)
+      if (ctxs[q] == ctxs[k]) return pic_fail(PIC_EINVAL, "a context appears twice in the ensemble");
+  }
+  const int shapes[3] = {0, 1, 2}, intervals[3] = {10, 20, 40};
+  double best = 1e300;
+  int best_shape = ctxs[0]->d.tile_shape, best_s = ctxs[0]->d.sort_interval;
+  int err = PIC_OK;
+  std::vector<pic_ctx *> cl(n, nullptr);
+  for (int sh : shapes) {
+    for (int S : intervals) {
+      for (int k = 0; k < n && !err; ++k) {
+        err = clone_context(ctxs[k], &cl[k]);
+        if (!err) {
+          cl[k]->d.sort_interval = S;
+          if (sh != cl[k]->d.tile_shape) err = set_tiles(cl[k], sh);
+        }
+      }
+      if (!err) err = pic_ensemble_step(cl.data(), n, S, nullptr);  // warm-up: one full sort cycle
+      const int m = std::max(trial_steps, 2 * S);
+      double ms = 0.0;
+      if (!err) {
+        const auto t0 = std::chrono::steady_clock::now();
+        err = pic_ensemble_step(cl.data(), n, m, nullptr);
+        ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      }
+      for (int k = 0; k < n; ++k) {
+        pic_destroy(cl[k]);
+        cl[k] = nullptr;
+      }
+      if (err) break;
+      if (ms / m < best) { best = ms / m; best_shape = sh; best_s = S; }
+    }
+    if (err) break;
+  }
+  if (err) return err;
+  for (int k = 0; k < n; ++k) {
+    pic_ctx *c = ctxs[k];
+    c->d.sort_interval = best_s;
+    if (best_shape != c->d.tile_shape && (err = set_tiles(c, best_shape))) return err;
+  }
   if (sort_interval) *sort_interval = best_s;
   if (tile_shape) *tile_shape = best_shape;
   return PIC_OK;

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime's driver entry point)
 
@@ -772,8 +773,9 @@ __device__ inline int cell_key(const Args32 &A, uint32_t cell, float qw) {
   return A.mix ? tile + (ci % A.ti) * A.tj + cj % A.tj : tile;
 }
 
-__global__ void k_hist(Args32 A, Parts32 P, int64_t n, int64_t *count) {
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void hist_block(const Args32 &A, const Parts32 &P, int64_t n, int64_t *count,
+                                           unsigned blk) {
+  const int64_t k = blk * (int64_t)blockDim.x + threadIdx.x;
   const int key = k < n ? cell_key(A, P.cell[k], P.qw[k]) : -1;
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   const int lane = threadIdx.x & 31;
@@ -781,9 +783,11 @@ __global__ void k_hist(Args32 A, Parts32 P, int64_t n, int64_t *count) {
     atomicAdd(reinterpret_cast<unsigned long long *>(count + key), (unsigned long long)__popc(peers));
 }
 
-// exclusive scan of nb counts by one block (the top level of the scan below);
-// count becomes the cursor and start[nb] the total
-__global__ void k_scan_bins(int64_t *count, int64_t *start, int nb) {
+__global__ void k_hist(Args32 A, Parts32 P, int64_t n, int64_t *count) { hist_block(A, P, n, count, blockIdx.x); }
+
+// exclusive scan of nb counts by one block of 1024 threads (the top level of
+// the scan below); count becomes the cursor and start[nb] the total
+__device__ __forceinline__ void scan_bins_block(int64_t *count, int64_t *start, int nb) {
   __shared__ int64_t part[1024];
   const int t = threadIdx.x;
   const int per = (nb + 1023) / 1024, a = t * per, b = min(nb, a + per);
@@ -807,6 +811,8 @@ __global__ void k_scan_bins(int64_t *count, int64_t *start, int nb) {
   if (t == 1023) start[nb] = part[1023];
 }
 
+__global__ void k_scan_bins(int64_t *count, int64_t *start, int nb) { scan_bins_block(count, start, nb); }
+
 // block sum of 256 values (all threads get it)
 __device__ inline int64_t block_sum256(int64_t v, int64_t *sm) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -821,19 +827,24 @@ __device__ inline int64_t block_sum256(int64_t v, int64_t *sm) {
 // multi-block exclusive scan over nb bins, SCAN_CHUNK bins per block of 256
 // threads: sums of each chunk, a one-block scan of the sums, then each chunk
 // scanned from its offset (16 consecutive bins per thread)
-__global__ void k_scan_sums(const int64_t *count, int64_t nb, int64_t *sums) {
+__device__ __forceinline__ void scan_sums_block(const int64_t *count, int64_t nb, int64_t *sums, unsigned blk) {
   __shared__ int64_t sm[8];
-  const int64_t a = blockIdx.x * (int64_t)SCAN_CHUNK;
+  const int64_t a = blk * (int64_t)SCAN_CHUNK;
   int64_t s = 0;
   for (int k = threadIdx.x; k < SCAN_CHUNK; k += 256)
     if (a + k < nb) s += count[a + k];
   s = block_sum256(s, sm);
-  if (threadIdx.x == 0) sums[blockIdx.x] = s;
+  if (threadIdx.x == 0) sums[blk] = s;
 }
 
-__global__ void k_scan_apply(int64_t *count, int64_t *start, int64_t nb, const int64_t *offs, int nblk) {
+__global__ void k_scan_sums(const int64_t *count, int64_t nb, int64_t *sums) {
+  scan_sums_block(count, nb, sums, blockIdx.x);
+}
+
+__device__ __forceinline__ void scan_apply_block(int64_t *count, int64_t *start, int64_t nb, const int64_t *offs,
+                                                 int nblk, unsigned blk) {
   __shared__ int64_t sm[8];
-  const int64_t a = blockIdx.x * (int64_t)SCAN_CHUNK + threadIdx.x * 16;
+  const int64_t a = blk * (int64_t)SCAN_CHUNK + threadIdx.x * 16;
   int64_t v[16], s = 0;
 #pragma unroll
   for (int i = 0; i < 16; ++i) { v[i] = a + i < nb ? count[a + i] : 0; s += v[i]; }
@@ -846,7 +857,7 @@ __global__ void k_scan_apply(int64_t *count, int64_t *start, int64_t nb, const i
   }
   if (lane == 31) sm[w] = x;
   __syncthreads();
-  int64_t base = offs[blockIdx.x];
+  int64_t base = offs[blk];
   for (int k = 0; k < w; ++k) base += sm[k];
   int64_t run = base + x - s;
 #pragma unroll
@@ -854,22 +865,33 @@ __global__ void k_scan_apply(int64_t *count, int64_t *start, int64_t nb, const i
     if (a + i < nb) { start[a + i] = run; count[a + i] = run; }
     run += v[i];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) start[nb] = offs[nblk];
+  if (blk == 0 && threadIdx.x == 0) start[nb] = offs[nblk];
+}
+
+__global__ void k_scan_apply(int64_t *count, int64_t *start, int64_t nb, const int64_t *offs, int nblk) {
+  scan_apply_block(count, start, nb, offs, nblk, blockIdx.x);
 }
 
 // work units of each tile: ceil(n_t / unit), none for an empty tile
-__global__ void k_unit_count(const int64_t *start, int tc, int ntiles, int64_t unit, int64_t *ucount) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void unit_count_at(int t, const int64_t *start, int tc, int ntiles, int64_t unit,
+                                              int64_t *ucount) {
   if (t >= ntiles) return;
   const int64_t n = start[(int64_t)(t + 1) * tc] - start[(int64_t)t * tc];
   ucount[t] = (n + unit - 1) / unit;
 }
 
+__global__ void k_unit_count(const int64_t *start, int tc, int ntiles, int64_t unit, int64_t *ucount) {
+  unit_count_at(blockIdx.x * blockDim.x + threadIdx.x, start, tc, ntiles, unit, ucount);
+}
+
 // the unit list from the exclusive scan of the counts (uoff[ntiles] = total)
-__global__ void k_unit_fill(const int64_t *uoff, int ntiles, long long *units) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void unit_fill_at(int t, const int64_t *uoff, int ntiles, long long *units) {
   if (t >= ntiles) return;
   for (int64_t u = uoff[t]; u < uoff[t + 1]; ++u) units[u] = ((long long)t << 32) | (long long)(u - uoff[t]);
+}
+
+__global__ void k_unit_fill(const int64_t *uoff, int ntiles, long long *units) {
+  unit_fill_at(blockIdx.x * blockDim.x + threadIdx.x, uoff, ntiles, units);
 }
 
 // Order inside a tile's bin.  The counting sort yields the tile's particles
@@ -890,8 +912,9 @@ __device__ inline int64_t transposed_slot(int64_t q, int64_t n) {
   return r * TRW + c;
 }
 
-__global__ void k_scatter_cells(Args32 A, Parts32 S, Parts32 D, int64_t n, int64_t *cursor) {
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void scatter_block(const Args32 &A, const Parts32 &S, const Parts32 &D, int64_t n,
+                                              int64_t *cursor, unsigned blk) {
+  const int64_t k = blk * (int64_t)blockDim.x + threadIdx.x;
   const int trash = A.ntiles * A.tc;
   // every load issued before the cursor atomic, whose round trip they overlap
   const int64_t kk = k < n ? k : 0;
@@ -915,6 +938,82 @@ __global__ void k_scatter_cells(Args32 A, Parts32 S, Parts32 D, int64_t n, int64
   D.cell[d] = cell; D.dx[d] = dx; D.dy[d] = dy;
   D.ur[d] = ur; D.ut[d] = ut; D.up[d] = up;
   D.qw[d] = qw; D.id[d] = id;
+}
+
+__global__ void k_scatter_cells(Args32 A, Parts32 S, Parts32 D, int64_t n, int64_t *cursor) {
+  scatter_block(A, S, D, n, cursor, blockIdx.x);
+}
+
+// ---- the tile sort of several ensemble members at once ---------------------
+// One member's sort as the batched kernels read it (device table): the same
+// arrays and the same kernel bodies as sort32, every phase one launch for all
+// members due, and one read-back of their live counts, unit counts and error
+// words.
+struct EnsSortArg {
+  Args32 A;                   // keys and tile geometry; A.mix: this sort's order
+  Parts32 S, D;               // particles before and after the sort
+  int64_t n;                  // particles before the sort
+  int64_t *count, *start, *bsum;
+  int64_t nbins;
+  int nblk, ublk, ntiles, tc;
+  int64_t *ucount, *usum;
+  long long *units;
+  int64_t unit;
+  const int *err;
+  int64_t *out;               // live, units, error bits (for the host)
+};
+
+__global__ void k_ens_sort_zero(const EnsSortArg *__restrict__ tab, EnsList L) {
+  const int2 e = L.blk[blockIdx.x];
+  const EnsSortArg &E = tab[e.x];
+  const int64_t q = (int64_t)e.y * blockDim.x + threadIdx.x;
+  if (q <= E.nbins) E.count[q] = 0;
+}
+__global__ void k_ens_hist(const EnsSortArg *__restrict__ tab, EnsList L) {
+  const int2 e = L.blk[blockIdx.x];
+  const EnsSortArg &E = tab[e.x];
+  hist_block(E.A, E.S, E.n, E.count, (unsigned)e.y);
+}
+// units = 0: the scan of the bin counts; 1: of the per-tile unit counts
+__global__ void k_ens_scan_sums(const EnsSortArg *__restrict__ tab, EnsList L, int units) {
+  const int2 e = L.blk[blockIdx.x];
+  const EnsSortArg &E = tab[e.x];
+  if (units) scan_sums_block(E.ucount, E.ntiles, E.usum, (unsigned)e.y);
+  else scan_sums_block(E.count, E.nbins, E.bsum, (unsigned)e.y);
+}
+__global__ void k_ens_scan_bins(const EnsSortArg *__restrict__ tab, EnsList L, int units) {
+  const EnsSortArg &E = tab[L.blk[blockIdx.x].x];
+  if (units) scan_bins_block(E.usum, E.usum + E.ublk + 1, E.ublk);
+  else scan_bins_block(E.bsum, E.bsum + E.nblk + 1, E.nblk);
+}
+__global__ void k_ens_scan_apply(const EnsSortArg *__restrict__ tab, EnsList L, int units) {
+  const int2 e = L.blk[blockIdx.x];
+  const EnsSortArg &E = tab[e.x];
+  if (units) scan_apply_block(E.ucount, E.ucount, E.ntiles, E.usum + E.ublk + 1, E.ublk, (unsigned)e.y);
+  else scan_apply_block(E.count, E.start, E.nbins, E.bsum + E.nblk + 1, E.nblk, (unsigned)e.y);
+}
+__global__ void k_ens_scatter(const EnsSortArg *__restrict__ tab, EnsList L) {
+  const int2 e = L.blk[blockIdx.x];
+  const EnsSortArg &E = tab[e.x];
+  scatter_block(E.A, E.S, E.D, E.n, E.count, (unsigned)e.y);
+}
+__global__ void k_ens_unit_count(const EnsSortArg *__restrict__ tab, EnsList L) {
+  const int2 e = L.blk[blockIdx.x];
+  const EnsSortArg &E = tab[e.x];
+  unit_count_at(e.y * blockDim.x + threadIdx.x, E.start, E.tc, E.ntiles, E.unit, E.ucount);
+}
+__global__ void k_ens_unit_fill(const EnsSortArg *__restrict__ tab, EnsList L) {
+  const int2 e = L.blk[blockIdx.x];
+  const EnsSortArg &E = tab[e.x];
+  unit_fill_at(e.y * blockDim.x + threadIdx.x, E.ucount, E.ntiles, E.units);
+}
+__global__ void k_ens_sort_out(const EnsSortArg *__restrict__ tab, int m) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const EnsSortArg &E = tab[k];
+  E.out[0] = E.start[(int64_t)E.ntiles * E.tc];
+  E.out[1] = E.ucount[E.ntiles];
+  E.out[2] = *E.err;
 }
 
 __global__ void k_charge32(int PI, int PJ, int LD, Parts32 P, int64_t n, double *Q, double *Qa) {
@@ -1214,6 +1313,136 @@ int64_t sort32(pic_ctx *c) {
   c->n_used = live;
   T.sorted_end = live;
   return live;
+}
+
+void ens_sort_scratch_free(EnsSortScratch &sc) {
+  if (sc.h) cudaFreeHost(sc.h);
+  if (sc.d) cudaFree(sc.d);
+  sc = EnsSortScratch{};
+}
+
+int ens_sort32(pic_ctx *const *cs, int m, cudaStream_t st, EnsSortScratch &sc, int64_t *kernels) {
+  *kernels = 0;
+  std::vector<pic_ctx *> due;
+  for (int k = 0; k < m; ++k) {
+    pic_ctx *c = cs[k];
+    if (c->n_used == 0) {  // nothing to order: as sort32
+      sort32(c);
+      c->steps_since_sort = 0;
+      continue;
+    }
+    due.push_back(c);
+  }
+  const int nd = (int)due.size();
+  if (nd == 0) return PIC_OK;
+  // room for each member's work units (reallocated after the device is idle
+  // on the stream: a previous graph may still read the old list)
+  bool synced = false;
+  for (pic_ctx *c : due) {
+    Tiles &T = c->tiles;
+    T.unit = std::max(UNIT_MIN, (c->n_used + UNIT_TARGET - 1) / UNIT_TARGET);
+    const int64_t ucap = T.ntiles + c->n_used / T.unit + 1;
+    if (ucap <= T.units_cap) continue;
+    if (!synced) { PIC_CUDA(cudaStreamSynchronize(st)); synced = true; }
+    cudaFree(T.units);
+    T.units = nullptr;
+    T.units_cap = 0;
+    T.sorted_end = 0;
+    T.nunits = 0;
+    PIC_CUDA(cudaMalloc((void **)&T.units, (size_t)ucap * sizeof(long long)));
+    T.units_cap = ucap;
+  }
+  // phase maps: {member, block} per block of each launch
+  enum { M_ZERO, M_PART, M_BINS, M_TOP, M_TILE, M_UBINS, M_UTOP, M_N };
+  std::vector<int2> mp[M_N];
+  auto add = [&](int q, int k, int64_t blocks) {
+    for (int64_t b = 0; b < blocks; ++b) mp[q].push_back(make_int2(k, (int)b));
+  };
+  std::vector<EnsSortArg> tab(nd);
+  const size_t tab_bytes = (size_t)nd * sizeof(EnsSortArg);
+  for (int k = 0; k < nd; ++k) {
+    pic_ctx *c = due[k];
+    Tiles &T = c->tiles;
+    EnsSortArg &E = tab[k];
+    E.A = make_args(c, 0.0);
+    E.A.mix = c->mix_sort ? 1 : 0;
+    c->mix_sort = false;
+    E.S = c->p32;
+    E.D = c->q32;
+    E.n = c->n_used;
+    E.count = T.cursor;
+    E.start = T.start;
+    E.bsum = T.bsum;
+    E.nbins = T.nbins;
+    E.nblk = (int)((T.nbins + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    E.ublk = (int)((T.ntiles + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    E.ntiles = T.ntiles;
+    E.tc = T.tc;
+    E.ucount = T.ucount;
+    E.usum = T.usum;
+    E.units = T.units;
+    E.unit = T.unit;
+    E.err = c->d_err;
+    add(M_ZERO, k, (T.nbins + 1 + 255) / 256);
+    add(M_PART, k, (E.n + 255) / 256);
+    add(M_BINS, k, E.nblk);
+    add(M_TOP, k, 1);
+    add(M_TILE, k, (T.ntiles + 255) / 256);
+    add(M_UBINS, k, E.ublk);
+    add(M_UTOP, k, 1);
+  }
+  // one buffer: the table, the maps and the read-back values
+  size_t at[M_N + 1];
+  at[0] = (tab_bytes + 255) / 256 * 256;
+  for (int q = 0; q < M_N; ++q) at[q + 1] = at[q] + (mp[q].size() * sizeof(int2) + 255) / 256 * 256;
+  const size_t out_at = at[M_N], bytes = out_at + (size_t)nd * 3 * sizeof(int64_t);
+  if (bytes > sc.cap) {
+    PIC_CUDA(cudaStreamSynchronize(st));
+    ens_sort_scratch_free(sc);
+    PIC_CUDA(cudaMallocHost((void **)&sc.h, bytes));
+    PIC_CUDA(cudaMalloc((void **)&sc.d, bytes));
+    sc.cap = bytes;
+  }
+  for (int k = 0; k < nd; ++k) tab[k].out = reinterpret_cast<int64_t *>(sc.d + out_at) + 3 * k;
+  memcpy(sc.h, tab.data(), tab_bytes);
+  for (int q = 0; q < M_N; ++q) memcpy(sc.h + at[q], mp[q].data(), mp[q].size() * sizeof(int2));
+  PIC_CUDA(cudaMemcpyAsync(sc.d, sc.h, out_at, cudaMemcpyHostToDevice, st));
+  const EnsSortArg *dt = reinterpret_cast<const EnsSortArg *>(sc.d);
+  auto L = [&](int q) {
+    EnsList x;
+    x.blk = reinterpret_cast<const int2 *>(sc.d + at[q]);
+    return x;
+  };
+  auto nb = [&](int q) { return (unsigned)mp[q].size(); };
+  k_ens_sort_zero<<<nb(M_ZERO), 256, 0, st>>>(dt, L(M_ZERO));
+  k_ens_hist<<<nb(M_PART), 256, 0, st>>>(dt, L(M_PART));
+  k_ens_scan_sums<<<nb(M_BINS), 256, 0, st>>>(dt, L(M_BINS), 0);
+  k_ens_scan_bins<<<nb(M_TOP), 1024, 0, st>>>(dt, L(M_TOP), 0);
+  k_ens_scan_apply<<<nb(M_BINS), 256, 0, st>>>(dt, L(M_BINS), 0);
+  k_ens_scatter<<<nb(M_PART), 256, 0, st>>>(dt, L(M_PART));
+  k_ens_unit_count<<<nb(M_TILE), 256, 0, st>>>(dt, L(M_TILE));
+  k_ens_scan_sums<<<nb(M_UBINS), 256, 0, st>>>(dt, L(M_UBINS), 1);
+  k_ens_scan_bins<<<nb(M_UTOP), 1024, 0, st>>>(dt, L(M_UTOP), 1);
+  k_ens_scan_apply<<<nb(M_UBINS), 256, 0, st>>>(dt, L(M_UBINS), 1);
+  k_ens_unit_fill<<<nb(M_TILE), 256, 0, st>>>(dt, L(M_TILE));
+  k_ens_sort_out<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(dt, nd);
+  PIC_CUDA(cudaGetLastError());
+  PIC_CUDA(cudaMemcpyAsync(sc.h + out_at, sc.d + out_at, (size_t)nd * 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  PIC_CUDA(cudaStreamSynchronize(st));
+  *kernels = 12;
+  const int64_t *out = reinterpret_cast<const int64_t *>(sc.h + out_at);
+  for (int k = 0; k < nd; ++k) {
+    pic_ctx *c = due[k];
+    Tiles &T = c->tiles;
+    std::swap(c->p32, c->q32);
+    c->n_used = out[3 * k];
+    T.sorted_end = out[3 * k];
+    T.nunits = out[3 * k + 1];
+    c->host_err |= (int)out[3 * k + 2];
+    c->steps_since_sort = 0;
+    c->launches += 10;  // the kernels of its own sort (sort32)
+  }
+  return PIC_OK;
 }
 
 void charge32(pic_ctx *c, double *Q, double *Qa) {

@@ -226,6 +226,15 @@ void ens_tile_arg(pic_ctx *c, double t, void *out);  // the member's tile-kernel
 // number of kernels launched (members are taken in groups of up to 48)
 int ens_tiles32(int kind, const void *args, const int64_t *blocks, int n, cudaStream_t s);
 void ens_flux_from_acc(const EnsFieldArg *tab, const EnsList &L, int blocks, cudaStream_t s);
+// the tile sort of m FP32 contexts at once on stream st (each launch serves
+// every member; one read-back, one synchronisation); the staging buffers
+// persist in sc between calls.  *kernels: the kernels launched.
+struct EnsSortScratch {
+  unsigned char *h = nullptr, *d = nullptr;
+  size_t cap = 0;
+};
+int ens_sort32(pic_ctx *const *cs, int m, cudaStream_t st, EnsSortScratch &sc, int64_t *kernels);
+void ens_sort_scratch_free(EnsSortScratch &sc);
 void particles32(pic_ctx *c, double t);
 void flux_from_acc(pic_ctx *c);        // fixed point -> FP64 fluxes, clears the accumulators
 int64_t sort32(pic_ctx *c);            // tile sort + removal; returns live count

@@ -28,9 +28,10 @@ PIC_MEM_HOST, PIC_MEM_DEVICE = 0, 1
 
 EXPORTS = ["pic_init_grid", "pic_load_particles", "pic_step", "pic_get_fields", "pic_set_fields", "pic_get_flux",
            "pic_get_particles", "pic_get_particles_noalloc", "pic_get_live", "pic_get_moments", "pic_get_luminosity",
-           "pic_gauss_snapshot", "pic_set_clock", "pic_profile",
-           "pic_get_profile", "pic_get_launches", "pic_ensemble_step", "pic_autotune", "pic_destroy", "pic_last_error",
-           "pic_struct_sizes", "pic_get_charge", "pic_grid_coords", "pic_get_axis_ties", "pic_set_axis_hints", "pic_wait_selftest",
+           "pic_gauss_snapshot", "pic_set_clock", "pic_profile", "pic_get_profile", "pic_get_launches",
+           "pic_ensemble_step", "pic_autotune", "pic_autotune_ensemble", "pic_destroy", "pic_last_error",
+           "pic_struct_sizes", "pic_get_charge", "pic_grid_coords", "pic_get_axis_ties", "pic_set_axis_hints",
+           "pic_wait_selftest",
            "pic_slabs_init", "pic_slabs_load_particles", "pic_slabs_step", "pic_slabs_get_fields",
            "pic_slabs_get_flux", "pic_slabs_get_particles", "pic_slabs_get_moments", "pic_slabs_destroy"]
 
@@ -97,6 +98,7 @@ def lib():
         "pic_get_launches": [P, C.POINTER(C.c_int64)],
         "pic_ensemble_step": [C.POINTER(C.c_void_p), I32, I32, C.POINTER(C.c_int64)],
         "pic_autotune": [P, I32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+        "pic_autotune_ensemble": [C.POINTER(C.c_void_p), I32, I32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
         "pic_destroy": [P],
         "pic_get_axis_ties": [P, C.POINTER(C.c_int64), P, P, P],
         "pic_wait_selftest": [I64, I32, P],
@@ -414,6 +416,15 @@ class Slabs:
 def wait_selftest(polls, arrive_first, stream=0):
     """Return code of pic_wait_selftest (PIC_ETIMEOUT or PIC_OK expected)."""
     return lib().pic_wait_selftest(polls, 1 if arrive_first else 0, C.c_void_p(stream))
+
+
+def autotune_ensemble(sims, trial_steps=40):
+    """One tile shape and sort interval for all members, by timing the
+    batched step on clones (pic_autotune_ensemble)."""
+    arr = (C.c_void_p * len(sims))(*[s.h for s in sims])
+    S, sh = C.c_int32(0), C.c_int32(0)
+    check(lib().pic_autotune_ensemble(arr, len(sims), trial_steps, C.byref(S), C.byref(sh)))
+    return {"sort_interval": S.value, "tile_shape": sh.value}
 
 
 def ensemble_step(sims, nsteps):

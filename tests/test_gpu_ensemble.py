@@ -197,6 +197,28 @@ def test_one_launch_per_phase_for_all_members():
             assert np.array_equal(pa[key][oa], pb[key][ob]), (k, key)
 
 
+def test_ensemble_autotune_applies_one_choice_and_keeps_results():
+    """pic_autotune_ensemble times the batched step on clones: the members do
+    not advance, every member takes the chosen shape and interval, and the
+    results stay bit-identical to independent steps (the deposit sums are
+    exact whatever the tiles and sorts)."""
+    from paper_1407_1810_gb300 import picsar as P
+
+    ens, ref = _pairs(4, "fp32")
+    P.ensemble_step(ens, 3)
+    for s in ref:
+        s.step(3)
+    choice = P.autotune_ensemble(ens, trial_steps=10)
+    assert choice["sort_interval"] in (10, 20, 40) and choice["tile_shape"] in (0, 1, 2)
+    assert all(s.moments()["step"] == 3 for s in ens)
+    P.ensemble_step(ens, 45)
+    for s in ref:
+        s.step(45)
+    for k, (a, b) in enumerate(zip(ens, ref)):
+        assert np.array_equal(a.fields(), b.fields()), k
+        assert a.moments()["live"] == b.moments()["live"], k
+
+
 def test_ensemble_member_against_the_oracle():
     """One member of a batched FP32 ensemble, 100 steps, against the FP64
     oracle run from the same state (following the member's branches at
