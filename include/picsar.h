@@ -28,8 +28,10 @@
  *     host pointer when mem == PIC_MEM_HOST and a device pointer of the
  *     context's device when mem == PIC_MEM_DEVICE;
  *   - all GPU work runs on the stream given to pic_init_grid (a cudaStream_t,
- *     NULL = the legacy default stream).  pic_step only enqueues work; calls
- *     that return data to the host synchronise that stream.
+ *     NULL = the legacy default stream).  pic_step enqueues its steps and
+ *     synchronises the stream only at a particle sort (every sort_interval
+ *     steps, to read the live count) or when it grows the particle buffer;
+ *     calls that return data to the host synchronise that stream.
  * Errors found by a kernel (a particle moving more than one cell in a step, a
  * full particle buffer, a non-finite momentum) are latched in the context and
  * reported by the next call that synchronises.
@@ -153,7 +155,10 @@ int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const double *x2
                        const double *qw, int32_t mem);
 
 /* Enqueue nsteps full time steps (gather, push, move, deposit, filter, field
- * update, lossy layer, injection).  Returns errors latched by earlier steps. */
+ * update, lossy layer, injection).  Every sort_interval steps the particles
+ * are sorted (FP32: by tile, removing deleted ones; FP64: compacted), which
+ * synchronises the stream once to read the live count; between sorts the
+ * steps are only enqueued.  Returns errors latched by earlier steps. */
 int pic_step(pic_ctx *c, int32_t nsteps);
 
 /* Fields: out6 = 6 planes [E_r, E_th, E_ph, B_r, B_th, B_ph], each
