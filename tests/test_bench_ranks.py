@@ -64,3 +64,17 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     bench.reference_arm(bench.parse(["--impl", "reference", "--steps", "1", "--warmup", "0"]))
     assert capsys.readouterr().out == ""
+
+
+def test_ensemble_members_split_across_ranks():
+    """The ensemble's members are independent: N ranks hold disjoint sets of
+    them that together are the whole ensemble, within one member of even."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    for world in (1, 2, 3, 4, 8):
+        parts = [bench.ensemble_members(64, r, world) for r in range(world)]
+        flat = sorted(m for p in parts for m in p)
+        assert flat == list(range(64))
+        sizes = [len(p) for p in parts]
+        assert max(sizes) - min(sizes) <= 1

@@ -197,6 +197,31 @@ def test_one_launch_per_phase_for_all_members():
             assert np.array_equal(pa[key][oa], pb[key][ob]), (k, key)
 
 
+def test_more_members_than_one_tile_launch_holds():
+    """52 members of one tile kind: the tile kernel takes its members'
+    arguments as kernel parameters, at most 48 per launch, so each step's
+    tile phase is two launches; every member stays bit-identical to its own
+    run."""
+    from paper_1407_1810_gb300 import picsar as P
+
+    ens, ref = [], []
+    for m in range(52):
+        cfg = dict(configs.CONFIGS["monopole-64x64"], nr=16, nth=16, pairs_per_cell=1, T=0.05 + 0.01 * m,
+                   seed=100 + m, precision="fp32")
+        s1, _, plasma, _ = setup(cfg)
+        s2, _, _, _ = setup(cfg, plasma=plasma)
+        ens.append(s1)
+        ref.append(s2)
+    kernels = P.ensemble_step(ens, 25)
+    for s in ref:
+        s.step(25)
+    # per step: 2 tile launches + flux + 3 Yee sub-steps + lossy + ghosts + copies
+    assert kernels >= 25 * 9
+    for k, (a, b) in enumerate(zip(ens, ref)):
+        assert np.array_equal(a.fields(), b.fields()), k
+        assert a.moments()["live"] == b.moments()["live"], k
+
+
 def test_ensemble_autotune_applies_one_choice_and_keeps_results():
     """pic_autotune_ensemble times the batched step on clones: the members do
     not advance, every member takes the chosen shape and interval, and the
