@@ -546,10 +546,15 @@ int pic_create_context(pic_ctx **out, const pic_desc &d, void *stream, int i0, i
     {
       std::vector<float> rn(d.nr + 2 * G.PI + 1);
       for (size_t ii = 0; ii < rn.size(); ++ii) rn[ii] = (float)h_fr(d, G.dxi, (double)ii - G.PI);
-      // displacements per step relative to r stay below dt / r(-g) (speed < c)
-      // and one cell spans dxi in log r: both below 1/64 let the step use
-      // its short series without the general fallback
-      c->small_steps = d.r_map == PIC_R_LOG && G.dxi <= 1.0 / 64 && G.dt / h_fr(d, G.dxi, -G.g) <= 1.0 / 64;
+      // The grid bounds the arguments of the move's series: dx dxi <= dxi for
+      // exp; with eps = dt / r(-g) (speed < c) the relative displacement s <=
+      // 2 eps + 3 eps^2 for log1p and the turning angle below eps for atan and
+      // the sin / cos series.  With dxi <= 1/16 and eps <= 1/40 every series'
+      // relative truncation stays below 2^-28, 1/16 of an FP32 ulp (at the
+      // bounds, evaluated in FP64: exp 8.8e-11, log1p 2.9e-9, atan and the
+      // sin / cos series below 1e-13), so the step uses the series without
+      // the general fallback
+      c->small_steps = d.r_map == PIC_R_LOG && G.dxi <= 1.0 / 16 && G.dt / h_fr(d, G.dxi, -G.g) <= 1.0 / 40;
       if ((e = dalloc(&c->r_n32, rn.size()))) return fail(e);
       PIC_CUDA(cudaMemcpy(c->r_n32, rn.data(), rn.size() * sizeof(float), cudaMemcpyHostToDevice));
     }

@@ -169,7 +169,7 @@ struct pic_ctx {
   int host_err = 0;
   int steps_since_sort = 0;
   bool need_sort = false;
-  bool small_steps = false; // FP32: every step's relative displacement < 1/64 (series without fallback)
+  bool small_steps = false; // FP32: the grid bounds the move's series arguments (series without fallback)
   bool mix_sort = true;    // FP32: the next sort orders by cell and mixes each tile's bin
   // profiling: one start/stop event pair per phase per step, read back lazily
   bool prof = false;
