@@ -348,8 +348,10 @@ int pic_destroy(pic_ctx *c);
  * crossed the interface (at most one cell per step, by the Courant limit).
  * Each exchange is a contiguous block copied on the stream, the message a
  * point-to-point send would carry between GPUs.  The results are those of one
- * context over the whole grid (pic_init_grid) up to the order of the FP64
- * current sums.  FP64 path only (precision must be PIC_FP64). */
+ * context over the whole grid (pic_init_grid): on the FP64 path up to the
+ * order of the FP64 current sums; on the FP32 path bit for bit (every slab
+ * deposits in one shared fixed-point quantum and the neighbours' int64 sums
+ * are added exactly before the conversion to FP64). */
 typedef struct pic_slabs pic_slabs;
 
 /* d: the whole grid's descriptor (as for pic_init_grid; dt <= 0 takes the

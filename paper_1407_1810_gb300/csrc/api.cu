@@ -372,7 +372,7 @@ __global__ void k_load32(Grid G, Parts32 P, int64_t base, int64_t n, const doubl
     // all six reads first, then the checks (without short-circuit): from
     // pinned host memory each dependent read would cost a host-link round trip
     const double a = x1[k], b = x2[k], q = qw[k], vr = ur[k], vt = ut[k], vp = up[k];
-    const bool ok = (a >= -(double)(G.n_filt + 1)) & (a < (double)(G.nr + G.n_filt + 1)) & (b >= 0.0) &
+    const bool ok = (a >= -(double)(G.n_filt + 1)) & (a < (double)(G.nr_glob + G.n_filt + 1)) & (b >= 0.0) &
                     (b <= G.nth) & (fabs(q) >= 0x1p-100) & (fabs(q) <= 0x1p100) & isfinite(vr) & isfinite(vt) &
                     isfinite(vp);
     const int64_t d = base + k;
@@ -386,7 +386,7 @@ __global__ void k_load32(Grid G, Parts32 P, int64_t base, int64_t n, const doubl
       float ox = (float)(a - ci), oy = (float)(b - cj);
       if (ox >= 1.0f) { ox = 0.0f; ++ci; }
       if (oy >= 1.0f && cj < G.nth - 1) { oy = 0.0f; ++cj; }
-      P.cell[d] = ((uint32_t)(ci + CELL_BIAS) << 16) | (uint32_t)cj;
+      P.cell[d] = ((uint32_t)(ci + CELL_BIAS) << 16) | (uint32_t)cj;  // whole-grid row
       P.dx[d] = ox; P.dy[d] = oy;
       P.ur[d] = (float)vr; P.ut[d] = (float)vt; P.up[d] = (float)vp; P.qw[d] = (float)q;
       P.id[d] = id0 + k;
@@ -545,7 +545,8 @@ int pic_create_context(pic_ctx **out, const pic_desc &d, void *stream, int i0, i
     }
     {
       std::vector<float> rn(d.nr + 2 * G.PI + 1);
-      for (size_t ii = 0; ii < rn.size(); ++ii) rn[ii] = (float)h_fr(d, G.dxi, (double)ii - G.PI);
+      // f_r of each padded row (global rows: a radial slab starts at row i0)
+      for (size_t ii = 0; ii < rn.size(); ++ii) rn[ii] = (float)h_fr(d, G.dxi, (double)ii - G.PI + G.i0);
       // The grid bounds the arguments of the move's series: dx dxi <= dxi for
       // exp; with eps = dt / r(-g) (speed < c) the relative displacement s <=
       // 2 eps + 3 eps^2 for log1p and the turning angle below eps for atan and
@@ -566,11 +567,12 @@ int pic_create_context(pic_ctx **out, const pic_desc &d, void *stream, int i0, i
   if ((e = dalloc(&c->d_err, 1)) || (e = dalloc(&c->d_cnt, CNT_N)) || (e = dalloc(&c->d_acc, ACC_N))) return fail(e);
   cudaMemset(c->d_err, 0, sizeof(int));
   cudaMemset(c->d_cnt, 0, CNT_N * sizeof(long long));
+  c->qexp = c->d_cnt + CNT_QEXP;
   {  // fixed-point exponent: raised on the device by the charges loaded or injected
     long long q0 = QEXP_NONE;
     if (d.flux_quantum > 0.0)
       q0 = std::min<long long>(QEXP_MAX, std::max<long long>(QEXP_MIN, (long long)std::ceil(std::log2(d.flux_quantum)) + KFIX));
-    PIC_CUDA(cudaMemcpy(c->d_cnt + CNT_QEXP, &q0, sizeof q0, cudaMemcpyHostToDevice));
+    PIC_CUDA(cudaMemcpy(c->qexp, &q0, sizeof q0, cudaMemcpyHostToDevice));
   }
   if ((e = dalloc(&c->tie_step, TIE_LOG)) || (e = dalloc(&c->tie_id, TIE_LOG)) || (e = dalloc(&c->tie_sign, TIE_LOG)))
     return fail(e);
@@ -648,7 +650,7 @@ extern "C" int pic_load_particles(pic_ctx *c, int64_t n, const double *x1, const
                                              dv[5], c->next_id + off, c->d_err);
     else
       ++c->launches, k_load32<<<blocks, 256, 0, c->stream>>>(c->G, c->p32, c->n_used + off, m, dv[0], dv[1], dv[2], dv[3], dv[4],
-                                             dv[5], c->next_id + off, c->d_err, c->d_cnt + CNT_QEXP);
+                                             dv[5], c->next_id + off, c->d_err, c->qexp);
     if (!direct) PIC_CUDA(cudaStreamSynchronize(c->stream));
   }
   PIC_CUDA(cudaGetLastError());
@@ -1428,7 +1430,7 @@ static int clone_context(pic_ctx *c, pic_ctx **out) {
     if (e) return e;
   }
   // the same fixed-point quantum as the original (its charges may have left)
-  cudaMemcpyAsync(k->d_cnt + CNT_QEXP, c->d_cnt + CNT_QEXP, sizeof(long long), cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(k->qexp, c->qexp, sizeof(long long), cudaMemcpyDeviceToDevice, c->stream);
   k->step = c->step;
   k->next_id = c->next_id;
   PIC_CUDA(cudaStreamSynchronize(c->stream));

@@ -460,7 +460,7 @@ __global__ void k_ens_write(const EnsFieldArg *__restrict__ tab, EnsList L) {
   const double *sig = (E.inject_smooth & 1) ? E.sig + (E.G.nth + 1) : E.sig;
   const Parts64 none;
   inject_slot<true>(idx, E.G, sig, E.cnt + CNT_SMAX, none, E.p32, E.inj_base, E.inj_id0, ens_rule(E),
-                    E.cnt + CNT_INJECTED, E.cnt + CNT_CAPPED, E.cnt + CNT_QEXP);
+                    E.cnt + CNT_INJECTED, E.cnt + CNT_CAPPED, E.qexp);
 }
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
@@ -499,6 +499,7 @@ void ens_fill_field_arg(const pic_ctx *c, EnsFieldArg *a) {
   }
   a->grid_elems = c->grid_elems;
   a->cnt = c->d_cnt;
+  a->qexp = c->qexp;
   a->sig = c->sig;
   a->p32 = c->p32;
   a->f_inj = c->d.f_inj;
@@ -552,14 +553,17 @@ void fields_e_full(pic_ctx *c) {
       G, c->f[ER], c->f[ETH], c->f[EPH], c->f[BR], c->f[BTH], c->f[BPH], c->F[0], c->F[1], c->F[2]);
 }
 
+void fields_copy32(pic_ctx *c) {
+  const Grid &G = c->G;
+  ++c->launches, k_copy32<<<grid2(G.nr + 2 * G.g + 1, G.nth + 2), dim3(BX, BY), 0, c->stream>>>(
+      G, c->f[0], c->f[1], c->f[2], c->f[3], c->f[4], c->f[5], c->f32[0], c->f32[1], c->f32[2], c->f32[3], c->f32[4],
+      c->f32[5]);
+}
+
 void fields_fill_ghosts(pic_ctx *c) {
   const Grid &G = c->G;
   ++c->launches, k_axis_ghosts<<<(G.nr + 1 + 127) / 128, 128, 0, c->stream>>>(G, c->f[ETH], c->f[BR], c->f[BPH]);
-  if (c->d.precision == PIC_FP32) {
-    ++c->launches, k_copy32<<<grid2(G.nr + 2 * G.g + 1, G.nth + 2), dim3(BX, BY), 0, c->stream>>>(
-        G, c->f[0], c->f[1], c->f[2], c->f[3], c->f[4], c->f[5], c->f32[0], c->f32[1], c->f32[2], c->f32[3], c->f32[4],
-        c->f32[5]);
-  }
+  if (c->d.precision == PIC_FP32) fields_copy32(c);
 }
 
 void fields_finish(pic_ctx *c) {
@@ -615,10 +619,10 @@ void inject(pic_ctx *c, double t) {
   const int blocks = (int)((nslots + 255) / 256);
   if (c->d.precision == PIC_FP32)
     ++c->launches, k_inject_write<true><<<blocks, 256, 0, c->stream>>>(G, a, smax, c->p64, c->p32, c->n_used, c->next_id, R,
-                                                        c->d_cnt + CNT_INJECTED, c->d_cnt + CNT_CAPPED, c->d_cnt + CNT_QEXP);
+                                                        c->d_cnt + CNT_INJECTED, c->d_cnt + CNT_CAPPED, c->qexp);
   else
     ++c->launches, k_inject_write<false><<<blocks, 256, 0, c->stream>>>(G, a, smax, c->p64, c->p32, c->n_used, c->next_id, R,
-                                                         c->d_cnt + CNT_INJECTED, c->d_cnt + CNT_CAPPED, c->d_cnt + CNT_QEXP);
+                                                         c->d_cnt + CNT_INJECTED, c->d_cnt + CNT_CAPPED, c->qexp);
   c->n_used += nslots;
   c->next_id += nslots;
 }

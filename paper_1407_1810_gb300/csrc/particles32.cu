@@ -752,7 +752,7 @@ __global__ void k_ens_flux(const EnsFieldArg *__restrict__ tab, EnsList L) {
   const unsigned b = (unsigned)e.y, gx = (unsigned)(G.nth + 1 + 31) / 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   flux_node(-G.g + (int)((b / gx) * 8 + ty), (int)((b % gx) * 32 + tx), G.nr, G.nth, G.g, G.PI, G.LD, G.PJ,
-            E.cnt + CNT_QEXP, E.acc[0], E.acc[1], E.acc[2], E.Fin[0], E.Fin[1], E.Fin[2]);
+            E.qexp, E.acc[0], E.acc[1], E.acc[2], E.Fin[0], E.Fin[1], E.Fin[2]);
 }
 
 // ---- counting sort into tile bins (drops removed particles) ---------------
@@ -1062,7 +1062,7 @@ Args32 make_args(pic_ctx *c, double t) {
   A.k2_hi = (float)(G.nth / M_PI);
   A.k2_lo = (float)(G.nth / M_PI - (double)A.k2_hi);
   A.inv_nth = (float)(1.0 / G.nth); A.nth_f = (float)G.nth;
-  A.qexp = c->d_cnt + CNT_QEXP;
+  A.qexp = c->qexp;
   A.ids = c->p32.id;
   A.ties = axis_ties(c);
   A.r_n = c->r_n32;
@@ -1071,6 +1071,14 @@ Args32 make_args(pic_ctx *c, double t) {
   A.err = c->d_err;
   A.cnt = c->d_cnt;
   A.row0 = c->tiles.row0; A.ntj = c->tiles.ntj; A.ntiles = c->tiles.ntiles;
+  // Particles keep whole-grid rows in their packed cell.  A radial slab
+  // (rows i0.. of a grid of nr_glob rows) indexes its arrays through a
+  // padding offset shifted by i0, tests the conductors and removal against
+  // the whole grid and places its tiles at its own rows; a whole grid has
+  // i0 = 0 and nr_glob = nr, i.e. these are its own values.
+  A.nr = G.nr_glob;
+  A.PI = G.PI - G.i0;
+  A.row0 = c->tiles.row0 + G.i0;
   A.ti = c->tiles.TI; A.tj = c->tiles.TJ; A.tc = c->tiles.tc;
   A.mix = 0;
   A.start = c->tiles.start;
@@ -1243,7 +1251,7 @@ void ens_flux_from_acc(const EnsFieldArg *tab, const EnsList &L, int blocks, cud
 void flux_from_acc(pic_ctx *c) {
   const Grid &G = c->G;
   dim3 gr((G.nth + 1 + 31) / 32, (G.nr + 2 * G.g + 1 + 7) / 8);
-  ++c->launches, k_flux_from_acc<<<gr, dim3(32, 8), 0, c->stream>>>(G.nr, G.nth, G.g, G.PI, G.PJ, G.LD, c->d_cnt + CNT_QEXP,
+  ++c->launches, k_flux_from_acc<<<gr, dim3(32, 8), 0, c->stream>>>(G.nr, G.nth, G.g, G.PI, G.PJ, G.LD, c->qexp,
                                                      c->acc[0], c->acc[1], c->acc[2], c->F[0], c->F[1], c->F[2]);
 }
 
@@ -1447,7 +1455,8 @@ int ens_sort32(pic_ctx *const *cs, int m, cudaStream_t st, EnsSortScratch &sc, i
 
 void charge32(pic_ctx *c, double *Q, double *Qa) {
   if (c->n_used == 0) return;
-  ++c->launches, k_charge32<<<(unsigned)((c->n_used + 255) / 256), 256, 0, c->stream>>>(c->G.PI, c->G.PJ, c->G.LD, c->p32,
+  // particles keep whole-grid rows: a radial slab's arrays start at row i0
+  ++c->launches, k_charge32<<<(unsigned)((c->n_used + 255) / 256), 256, 0, c->stream>>>(c->G.PI - c->G.i0, c->G.PJ, c->G.LD, c->p32,
                                                                         c->n_used, Q, Qa);
 }
 

@@ -113,6 +113,7 @@ struct EnsFieldArg {
   long long *acc[3];
   size_t grid_elems;
   long long *cnt;
+  long long *qexp;                     // the fixed-point exponent counter
   double *sig;                         // two buffers of nth + 1
   Parts32 p32;
   int64_t inj_base, inj_id0;           // first slot and id of the step's injected pairs
@@ -156,6 +157,9 @@ struct pic_ctx {
   size_t scratch_bytes = 0;
   int *d_err = nullptr;
   long long *d_cnt = nullptr;
+  // the fixed-point exponent counter: d_cnt + CNT_QEXP, or the one the
+  // radial slabs of a grid share (every slab's fluxes in one quantum)
+  long long *qexp = nullptr;
   double *d_acc = nullptr;
   long long *h_pinned = nullptr;  // pinned host mirror for small reads
   // axis-crossing ties: the log of this context and the hints it follows
@@ -187,7 +191,8 @@ void fields_b_half(pic_ctx *c);
 void fields_e_full(pic_ctx *c);
 void fields_finish(pic_ctx *c);        // lossy layer + axis ghosts (+ FP32 copies)
 void fields_filter(pic_ctx *c);        // n_filt passes on F
-void fields_fill_ghosts(pic_ctx *c);   // axis ghosts only (after pic_set_fields)
+void fields_fill_ghosts(pic_ctx *c);   // axis ghosts (+ FP32 copies) (after pic_set_fields)
+void fields_copy32(pic_ctx *c);        // FP32 gather copies of the fields (FP32 path)
 void inject(pic_ctx *c, double t);     // surface pairs into slots [n_used, n_used + 2 npp nth)
 void moments(pic_ctx *c, bool snapshot, pic_moments *out);
 void luminosity(pic_ctx *c, double t, double *L);  // nr + 1 device values (Sec. 5.3)

@@ -101,7 +101,7 @@ def test_header_compiles_as_plain_c_and_cpp(lang, std):
     (16, None, {}),              # slabs of 4 rows are narrower than their halos (2 (n_filt + 2) + 2 rows)
     (2, [0, 40, 60], {}),        # the rows do not end at nr
     (2, [0, 56, 64], {}),        # the lossy layer (8 cells) does not fit in the last slab
-    (2, None, {"precision": "fp32"}),  # slabs run the FP64 path
+    (3, [0, 30, 20, 64], {}),    # the rows do not increase
     (0, None, {}),
 ])
 def test_slab_descriptor_and_rows_are_checked(nslabs, rows, over):

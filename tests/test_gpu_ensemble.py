@@ -197,6 +197,31 @@ def test_one_launch_per_phase_for_all_members():
             assert np.array_equal(pa[key][oa], pb[key][ob]), (k, key)
 
 
+def test_mixed_precision_ensemble_takes_the_branch_form():
+    """Any FP64 member sends the ensemble to the per-member graph branches:
+    FP32 members stay bit-identical to their own runs, FP64 members agree to
+    the rounding of their atomic sums."""
+    from paper_1407_1810_gb300 import picsar as P
+
+    ens, ref = [], []
+    for m, prec in ((0, "fp32"), (1, "fp64"), (2, "fp32")):
+        cfg = _member_cfg(m, prec)
+        s1, _, plasma, _ = setup(cfg)
+        s2, _, _, _ = setup(cfg, plasma=plasma)
+        ens.append(s1)
+        ref.append(s2)
+    P.ensemble_step(ens, 30)
+    for s in ref:
+        s.step(30)
+    for k, (a, b) in enumerate(zip(ens, ref)):
+        fa, fb = a.fields(), b.fields()
+        if k != 1:
+            assert np.array_equal(fa, fb), k
+        else:
+            assert np.max(np.abs(fa - fb)) <= 1e-13 * np.max(np.abs(fb)), k
+        assert a.moments()["live"] == b.moments()["live"], k
+
+
 def test_more_members_than_one_tile_launch_holds():
     """52 members of one tile kind: the tile kernel takes its members'
     arguments as kernel parameters, at most 48 per launch, so each step's

@@ -4,10 +4,12 @@ against the oracle, through the C-ABI.
 
 Each slab is a context of its own on one GPU; every step exchanges field
 halos, sums back the flux deposited across each interface before the filter
-and hands migrating particles to the neighbouring slab.  Bars: the FP64
-path's, i.e. fields and fluxes within 1e-12 relative (L2 and per-component
-max-norm) of the unsplit run and of the oracle, particle counts, deletions,
-injections and the set of live ids exactly equal.
+and hands migrating particles to the neighbouring slab.  Bars: on the FP64
+path fields and fluxes within 1e-12 relative (L2 and per-component max-norm)
+of the unsplit run and of the oracle, particle counts, deletions, injections
+and the set of live ids exactly equal; on the FP32 path the split run equals
+the unsplit FP32 run bit for bit (fields, fluxes, every particle) and the
+oracle at the FP32 bar.
 """
 import numpy as np
 import pytest
@@ -15,7 +17,7 @@ import pytest
 import oracle as O
 from paper_1407_1810_gb300 import configs, synthetic
 
-from gpu_common import KEYS, by_id, maxnorm_rel, rel_l2, setup
+from gpu_common import KEYS, MAX_FP32, by_id, close, follow_ties, maxnorm_rel, rel_l2, setup
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -113,3 +115,39 @@ def test_particles_migrate_both_ways():
     start = x0[pg["id"]]
     assert np.sum((start < 32) & (pg["x1"] >= 32)) > 0 and np.sum((start >= 32) & (pg["x1"] < 32)) > 0
     assert rel_l2(g.fields(), s.fields()) < TOL
+
+
+FP32_CASES = {
+    "monopole": dict(CASES["monopole"], precision="fp32"),
+    "rotator": dict(CASES["rotator"], precision="fp32"),
+}
+
+
+@pytest.mark.parametrize("case", ["monopole", "rotator"])
+@pytest.mark.parametrize("nslabs,rows", [(2, None), (3, [0, 13, 40, 64]), (4, None)])
+def test_fp32_slabs_equal_one_context_bit_for_bit(case, nslabs, rows):
+    """The FP32 path split into slabs: one fixed-point quantum for all slabs
+    and exact int64 sums across the interfaces, so the split run equals the
+    unsplit one in every bit; both against the oracle at the FP32 bar."""
+    cfg = FP32_CASES[case]
+    s, o, plasma, dt = setup(cfg)
+    g = _slabs(cfg, dt, s.desc.b0, nslabs, rows)
+    g.load(*(np.ascontiguousarray(plasma[k]) for k in KEYS))
+    o.gauss_snapshot()
+    for _ in range(4):
+        s.step(25)
+        g.step(25)
+    assert np.array_equal(g.fields(), s.fields())
+    assert np.array_equal(g.flux(), s.flux())
+    ms, mg = s.moments(), g.moments()
+    for k in ("live", "deleted", "injected", "step"):
+        assert mg[k] == ms[k], k
+    assert mg["deleted"] > 0
+    assert mg["gauss_residual"] < 1e-6
+    pg, ps = by_id(g.particles()), by_id(s.particles())
+    assert np.array_equal(pg["id"], ps["id"])
+    for k in KEYS:
+        assert np.array_equal(pg[k], ps[k]), k
+    follow_ties(s, o)
+    o.step(100)
+    close(g.fields(), o.fields(), 1e-5, MAX_FP32 if cfg["th_map"] == "equal_area" else 1e-3)
