@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpicsar_gb300.so")
-SOURCES = ["api.cu", "fields.cu", "particles64.cu", "particles32.cu", "noalloc.cu", "slabs.cu"]
+SOURCES = ["api.cu", "ensemble.cu", "fields.cu", "particles64.cu", "particles32.cu", "noalloc.cu", "slabs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The FP32 particle kernel takes approximate division and square root (within
 # 2 ulp) and flushes denormals: 5% faster, and the FP32 parity tests against the

@@ -267,6 +267,11 @@ int pic_desc_defaults(pic_desc *d);  // fill the zero defaults and check the des
 int pic_create_context(pic_ctx **out, const pic_desc &d, void *stream, int i0, int nr_glob, int open_lo, int open_hi);
 int pic_grow_particles(pic_ctx *c, int64_t new_cap);  // keep [0, n_used), reallocate
 int pic_compact(pic_ctx *c);                          // remove free slots (sort on the FP32 path)
+// stepping internals of api.cu that the ensemble (ensemble.cu) drives
+void pic_step_body(pic_ctx *c);                        // enqueue one full step on c->stream
+int pic_prepare_steps(pic_ctx *c, int steps);          // host work before `steps` steps can be enqueued blindly
+int pic_set_tiles(pic_ctx *c, int shape);              // re-bin an FP32 context for another tile shape
+int pic_clone_context(pic_ctx *c, pic_ctx **out);      // a new context holding the same fields, particles and clock
 int pic_reserve(pic_ctx *c, int64_t need);            // capacity for at least `need` particle slots
 #define PIC_CUDA(call)                                          \
   do {                                                          \

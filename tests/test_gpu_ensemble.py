@@ -222,6 +222,31 @@ def test_mixed_precision_ensemble_takes_the_branch_form():
         assert a.moments()["live"] == b.moments()["live"], k
 
 
+def test_members_without_particles():
+    """An empty member (no tile launch, its grid phases still run), one that
+    starts empty and fills by surface injection during the batched steps, and
+    a plasma member: each equals its own run bit for bit."""
+    from paper_1407_1810_gb300 import picsar as P
+
+    cfgs = [dict(_member_cfg(0), pairs_per_cell=0),
+            dict(configs.CONFIGS["rotator-1024x1024"], nr=24, nth=16, pairs_per_cell=0, absorb_cells=4, t_spin=0.5),
+            _member_cfg(1)]
+    ens, ref = [], []
+    for cfg in cfgs:
+        s1, _, plasma, _ = setup(cfg)
+        s2, _, _, _ = setup(cfg, plasma=plasma)
+        ens.append(s1)
+        ref.append(s2)
+    P.ensemble_step(ens, 30)
+    for s in ref:
+        s.step(30)
+    for k, (a, b) in enumerate(zip(ens, ref)):
+        assert np.array_equal(a.fields(), b.fields()), k
+        ma, mb = a.moments(), b.moments()
+        assert ma["live"] == mb["live"] and ma["injected"] == mb["injected"], k
+    assert ens[0].moments()["live"] == 0 and ens[1].moments()["injected"] > 0
+
+
 def test_more_members_than_one_tile_launch_holds():
     """52 members of one tile kind: the tile kernel takes its members'
     arguments as kernel parameters, at most 48 per launch, so each step's
