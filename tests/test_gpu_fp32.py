@@ -107,6 +107,24 @@ def test_rotator_injection_filter_fp32(th_map):
     assert m["gauss_residual"] < 1e-6
 
 
+def test_series_bound_grid_against_the_oracle():
+    """A 64 x 64 log-r grid (dxi = 0.036, dt / r(-g) = 0.020): coarser than
+    1/64 but inside the series' bounds (dxi <= 1/16, dt / r <= 1/40), so the
+    step takes the monopole specialisation's series without fallback; 100
+    steps against the oracle at the FP32 bar."""
+    cfg = _cfg(nr=64, nth=64)
+    s, o, plasma, dt = setup(cfg)
+    o.gauss_snapshot()
+    s.step(100)
+    follow_ties(s, o)
+    o.step(100)
+    close(s.fields(), o.fields(), FIELD_TOL, MAX_FP32)
+    m = s.moments()
+    assert m["gauss_residual"] < 1e-6
+    assert abs(m["live"] - o.num_particles()) <= max(1, 1e-4 * o.num_particles())
+    assert m["kinetic_energy"] == pytest.approx(o.kinetic_energy(), rel=1e-5)
+
+
 def test_dense_tiles_split_into_work_units():
     """About 300 particles per cell, one bin of ~70 000 particles per tile:
     each bin is split into work units of 4096 particles, one CTA each.  The
