@@ -63,6 +63,8 @@ def parse(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tile-shape", type=int, default=None, help="FP32 tile: 0 = 16x16, 1 = 8x32, 2 = 32x8 cells")
     ap.add_argument("--sort-interval", type=int, default=None)
+    ap.add_argument("--slabs", type=int, default=0,
+                    help="run the workload split into this many radial slabs on this GPU (pic_slabs_*)")
     return ap.parse_args(argv)
 
 
@@ -598,6 +600,57 @@ def ensemble_arm(args, n_members=64):
         torch.distributed.destroy_process_group()
 
 
+def slabs_arm(args):
+    """The workload split into args.slabs equal radial slabs on this GPU
+    (pic_slabs_*: field and flux halos and particle migration every step)
+    beside the same workload on one context: the cost of the decomposition's
+    exchanges.  Host clock around the steps (a slab step reads its migration
+    counts on the host)."""
+    import torch
+
+    from paper_1407_1810_gb300 import configs
+    from paper_1407_1810_gb300 import picsar as P
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream()
+    cfg = dict(configs.CONFIGS[args.workload])
+    if args.precision:
+        cfg["precision"] = args.precision
+    out = {}
+    for split in (True, False):
+        if split:
+            dt = configs.courant_dt(cfg)
+            b0, qw = configs.physics(cfg, dt)
+            sim = P.Slabs(P.make_desc(**configs.desc_kwargs(cfg, dt, b0)), args.slabs, stream=stream.cuda_stream)
+        else:
+            sim, qw, _, _ = W.make_sim(cfg, stream=stream.cuda_stream)
+        W.load_plasma(sim, cfg, qw, dev, stream)
+        sim.step(args.warmup)
+        live0 = sim.moments()["live"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step(args.steps)
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0)
+        live1 = sim.moments()["live"]
+        out[split] = (0.5 * (live0 + live1) * args.steps / (ms * 1e-3), ms / args.steps)
+        sim.close()
+        del sim
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    line = {"metric": METRIC, "value": out[True][0], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out[True][1], "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32" if cfg["precision"] == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "slabs": args.slabs, "path": cfg["precision"],
+                       "timing": "host clock around pic_slabs_step / pic_step"},
+            "one_context": {"value": out[False][0], "ms_per_step": out[False][1]},
+            "exchange_ms_per_step": out[True][1] - out[False][1]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def steady_arm(args):
     """The Table 1 monopole rotator run to its steady state (two rotation
     periods from an empty domain): throughput over the run and its physics
@@ -645,6 +698,9 @@ def main():
         return
     if args.workload == "ensemble-64":
         ensemble_arm(args)
+        return
+    if args.slabs:
+        slabs_arm(args)
         return
     if args.workload == "rotator-steady":
         steady_arm(args)
