@@ -320,3 +320,43 @@ def test_ensemble_member_against_the_oracle():
     assert maxnorm_rel(fs, fo) < 1e-4
     n = o.num_particles()
     assert abs(s.moments()["live"] - n) <= max(1, 1e-4 * n)
+
+
+def test_benchmark_ensemble_members_against_the_oracle():
+    """The benchmark's own ensemble (`bench.py --workload ensemble-64`: 64
+    members, grids 64-256 x 64-512, 1e4-2e6 particles), autotuned and advanced
+    20 steps by the batched step; two of its members -- member 8 (256 x 256,
+    2.6e5 particles) and member 36 (64 x 64, 1.26e6: 300 per cell, many work
+    units per tile) -- against the oracle from the same FP32 state, following
+    their axis ties: fields within the FP32 bar, live counts within the
+    near-ties."""
+    import bench
+    import oracle as O
+
+    from paper_1407_1810_gb300 import picsar as P
+
+    from gpu_common import KEYS, MAX_FP32_SPHERICAL, close, follow_ties, fp32_state
+
+    O.build_oracle()
+    sims, states = [], {}
+    for m in range(64):
+        cfg = configs.ensemble_member_config(m)
+        dt = configs.courant_dt(cfg)
+        b0, qw = configs.physics(cfg, dt)
+        s = P.Simulation(P.make_desc(**configs.desc_kwargs(cfg, dt, b0)))
+        d = bench.ensemble_plasma(cfg, qw)
+        s.load(*(d[k] for k in KEYS))
+        sims.append(s)
+        if m in (8, 36):
+            states[m] = (cfg, dt, b0, fp32_state(d))
+    P.autotune_ensemble(sims, trial_steps=10)
+    P.ensemble_step(sims, 20)
+    for m, (cfg, dt, b0, d) in states.items():
+        o = O.Oracle(O.params(**configs.oracle_kwargs(cfg, dt, b0)))
+        o.load(*(d[k] for k in KEYS))
+        follow_ties(sims[m], o)
+        o.step(20)
+        close(sims[m].fields(), o.fields(), 1e-5, MAX_FP32_SPHERICAL)
+        n = o.num_particles()
+        assert abs(sims[m].moments()["live"] - n) <= max(1, 1e-4 * n), m
+
