@@ -16,13 +16,16 @@ the FP64 CPU oracle on bounded samples on every host core and on one
 The FP64 leg also runs both paths for 100 steps from one FP32-rounded state
 and reports their field difference on the whole grid (relative L2 and per
 component max-norm), the FP64 run following the FP32 run's branches at its
-axis-crossing ties.
+axis-crossing ties.  On one GPU the default run then measures the batched
+64-member ensemble for 200 steps (ensemble_64; --no-ensemble skips it).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
   python bench.py --workload NAME [--precision fp32|fp64]   # any workload on either path
-  python bench.py --workload ensemble-64                     # 64 uneven members in CUDA graphs
+  python bench.py --workload ensemble-64                     # 64 uneven members, one launch per phase
   python bench.py --workload rotator-steady                  # the Table 1 run and its physics
-Under torchrun every rank runs an independent replica (weak scaling).
+  python bench.py --workload NAME --slabs S                  # the workload split into S radial slabs
+Under torchrun every rank runs an independent replica (weak scaling); the
+ensemble's members are split across the ranks.
 """
 from __future__ import annotations
 
@@ -40,6 +43,7 @@ sys.path.insert(0, ROOT)
 
 from paper_1407_1810_gb300 import workload as W  # noqa: E402
 
+DEFAULT_WORKLOAD = "monopole-4096x4096"  # the largest single-GPU configuration
 METRIC = "particle-steps/s (gather+push+deposit), FP32 vs FP64 path, at stated Gauss residual"
 UNIT = "particle-steps/s"
 ALG_BYTES_FP32 = 52  # per particle-step: read cell, dx, dy, u (3), qw = 28 B; write cell, dx, dy, u = 24 B
@@ -52,7 +56,7 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="monopole-4096x4096")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--compare-steps", type=int, default=100,
                     help="steps of the FP32 against FP64 field comparison (the FP64 timing is inside them)")
@@ -61,6 +65,8 @@ def parse(argv=None):
     ap.add_argument("--precision", choices=("fp32", "fp64"), default=None,
                     help="run the workload on this particle path instead of its own")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the batched 64-member ensemble the default run measures after the main workload")
     ap.add_argument("--tile-shape", type=int, default=None, help="FP32 tile: 0 = 16x16, 1 = 8x32, 2 = 32x8 cells")
     ap.add_argument("--sort-interval", type=int, default=None)
     ap.add_argument("--slabs", type=int, default=0,
@@ -285,6 +291,11 @@ def gpu_arm(args):
             out["e2e"] = {"value": None, "unit": UNIT, "error": repr(exc)[:200]}
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(cfg)
+    if world == 1 and not args.no_ensemble and args.workload == DEFAULT_WORKLOAD:
+        # the batched ensemble (64 uneven plasmas), 200 steps, on this GPU
+        ens = ensemble_measure(args, rank, world, local, steps=200, warmup=5)
+        out["ensemble_64"] = {k: ens[k] for k in ("value", "unit", "ms_per_step", "steps", "config",
+                                                   "sequential_pic_step", "autotune", "clocks", "gpu_launches")}
     if world > 1:
         torch.distributed.barrier()
     if rank == 0:
@@ -521,22 +532,19 @@ def ensemble_members(n_members, rank, world):
     return list(range(rank, n_members, world))
 
 
-def ensemble_arm(args, n_members=64):
-    """64 independent monopole plasmas with uneven grids and particle counts:
-    every member autotuned (tile shape, sort interval), then advanced by the
-    batched, graph-captured pic_ensemble_step; the same members advanced one
-    after another by pic_step are timed for comparison."""
+def ensemble_measure(args, rank, world, local, n_members=64, steps=None, warmup=None):
+    """64 independent monopole plasmas with uneven grids and particle counts
+    (this rank's share of them): the members autotuned together
+    (pic_autotune_ensemble), then advanced by the batched, graph-captured
+    pic_ensemble_step; the same members advanced one after another by
+    pic_step are timed for comparison.  Returns the result line."""
     import torch
 
     from paper_1407_1810_gb300 import configs
     from paper_1407_1810_gb300 import picsar as P
 
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
+    steps = steps or args.steps
+    warmup = warmup or args.warmup
     stream = torch.cuda.Stream()
     sims, total = [], 0
     mine = ensemble_members(n_members, rank, world)
@@ -552,7 +560,7 @@ def ensemble_arm(args, n_members=64):
     t0 = time.perf_counter()
     choice = P.autotune_ensemble(sims, trial_steps=40)
     t_tune = time.perf_counter() - t0
-    P.ensemble_step(sims, args.warmup)
+    P.ensemble_step(sims, warmup)
     torch.cuda.synchronize()
     live0 = sum(s.live() for s in sims)
     clocks = ClockSampler(local)
@@ -563,37 +571,52 @@ def ensemble_arm(args, n_members=64):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     torch.cuda.nvtx.range_push("timed_steps")  # lets a profiler keep to the timed launches
-    launches = P.ensemble_step(sims, args.steps)
+    launches = P.ensemble_step(sims, steps)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     torch.cuda.nvtx.range_pop()
     ck = clocks.stop()
     live1 = sum(s.live() for s in sims)
-    units = 0.5 * (live0 + live1) * args.steps
+    units = 0.5 * (live0 + live1) * steps
     ms_max, units_all = combine_ranks(1e3 * (t1 - t0), units, torch.device("cuda", local))
     value = units_all / (ms_max * 1e-3)
     # the same members stepped one after another
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     for s in sims:
-        s.step(args.steps)
+        s.step(steps)
     torch.cuda.synchronize()
     t3 = time.perf_counter()
     seq_ms, seq_units = combine_ranks(1e3 * (t3 - t2), units, torch.device("cuda", local))
     seq = seq_units / (seq_ms * 1e-3)
     total_all = combine_ranks(0.0, float(total), torch.device("cuda", local))[1]
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-           "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "ensemble-64", "members": n_members, "members_per_rank": len(mine),
-                      "split": "member m on rank m mod N", "particles": int(total_all), "path": "fp32",
-                      "timing": "host clock around pic_ensemble_step (one launch per phase for all members, "
-                                "one graph per sort interval)"},
-           "sequential_pic_step": {"value": seq, "speedup_of_ensemble": value / seq},
-           "autotune": {"seconds": t_tune, "choice": choice,
-                        "how": "one tile shape and sort interval for all members, timed on clones through "
-                               "pic_ensemble_step"},
-           "clocks": ck, "gpu_launches": launches}
+    for s in sims:
+        s.close()
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ensemble-64", "members": n_members, "members_per_rank": len(mine),
+                       "split": "member m on rank m mod N", "particles": int(total_all), "path": "fp32",
+                       "timing": "host clock around pic_ensemble_step (one launch per phase for all members, "
+                                 "one graph per sort interval)"},
+            "sequential_pic_step": {"value": seq, "speedup_of_ensemble": value / seq},
+            "autotune": {"seconds": t_tune, "choice": choice,
+                         "how": "one tile shape and sort interval for all members, timed on clones through "
+                                "pic_ensemble_step"},
+            "clocks": ck, "gpu_launches": launches}
+
+
+def ensemble_arm(args, n_members=64):
+    """`--workload ensemble-64`: the batched ensemble on its own line."""
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    out = ensemble_measure(args, rank, world, local, n_members)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
