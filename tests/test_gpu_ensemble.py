@@ -247,6 +247,30 @@ def test_members_without_particles():
     assert ens[0].moments()["live"] == 0 and ens[1].moments()["injected"] > 0
 
 
+def test_long_blocks_and_single_steps():
+    """Sort interval 1000: 150 steps are three graphs (64, 64 and 22 steps,
+    the last one re-instantiated for its shorter length) with no sort between
+    them; then 10 calls of one step each.  Every member stays bit-identical to
+    its own run."""
+    from paper_1407_1810_gb300 import picsar as P
+
+    ens, ref = [], []
+    for m in range(4):
+        cfg = dict(_member_cfg(m), sort_interval=1000)
+        s1, _, plasma, _ = setup(cfg)
+        s2, _, _, _ = setup(cfg, plasma=plasma)
+        ens.append(s1)
+        ref.append(s2)
+    P.ensemble_step(ens, 150)
+    for _ in range(10):
+        P.ensemble_step(ens, 1)
+    for s in ref:
+        s.step(160)
+    for k, (a, b) in enumerate(zip(ens, ref)):
+        assert np.array_equal(a.fields(), b.fields()), k
+        assert a.moments()["live"] == b.moments()["live"] and a.moments()["step"] == 160, k
+
+
 def test_more_members_than_one_tile_launch_holds():
     """52 members of one tile kind: the tile kernel takes its members'
     arguments as kernel parameters, at most 48 per launch, so each step's
