@@ -376,11 +376,19 @@ __device__ inline bool step32(const Args32 &A, const W &w, int64_t k, uint32_t &
     return false;
   }
   // ---- Villasenor-Buneman deposit along the grid-coordinate path -----------
-  // Always three segments, split where the path crosses the x and y grid
-  // lines in the order it meets them; a line not crossed puts its segment at
-  // zero length (zero terms are skipped).  Branch-free, so lanes that cross
-  // and lanes that do not run the same instructions.
+  // Three segments, split where the path crosses the x and y grid lines in
+  // the order it meets them; a line not crossed puts its segment at zero
+  // length (zero terms are skipped).  Branch-free, so lanes that cross and
+  // lanes that do not run the same instructions -- except when no lane of
+  // the converged group crosses a line (a vote): then the path is its one
+  // nonzero segment, the same call with the same arguments as in the general
+  // form, which that group takes alone.  The move of one step is a small
+  // fraction of a cell away from the inner boundary (about 0.35 / r of one at
+  // 4096 log cells), so most warps take it there.
   const float scale = qw * w.fs;  // exact: fs is a power of two
+  if (__all_sync(__activemask(), (kx | ky) == 0)) {
+    vb_seg(w, scale, ci, cj, dx, dy, nx, ny);
+  } else {
   const float Dxs = kx == 0 ? nx - dx : (kx > 0 ? (1.f - dx) + nx : -(dx + (1.f - nx)));
   const float Dys = ky == 0 ? ny - dy : (ky > 0 ? (1.f - dy) + ny : -(dy + (1.f - ny)));
   // crossing parameters: any point on the crossed grid line keeps charge
@@ -409,6 +417,7 @@ __device__ inline bool step32(const Args32 &A, const W &w, int64_t k, uint32_t &
   vb_seg(w, scale, ci, cj, dx, dy, c1x, c1y);
   vb_seg(w, scale, mi, mj, e1x, e1y, c2x, c2y);
   vb_seg(w, scale, ci + kx, cj + ky, e2x, e2y, nx, ny);
+  }
   // azimuthal flux: charge crossing the meridional half-plane, qw dphi / 2 pi,
   // area weights at the midpoint of the grid path
   {
