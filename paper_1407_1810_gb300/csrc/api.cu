@@ -558,6 +558,17 @@ int pic_create_context(pic_ctx **out, const pic_desc &d, void *stream, int i0, i
       c->small_steps = d.r_map == PIC_R_LOG && G.dxi <= 1.0 / 16 && G.dt / h_fr(d, G.dxi, -G.g) <= 1.0 / 40;
       if ((e = dalloc(&c->r_n32, rn.size()))) return fail(e);
       PIC_CUDA(cudaMemcpy(c->r_n32, rn.data(), rn.size() * sizeof(float), cudaMemcpyHostToDevice));
+      // sine and cosine of the node angle pi j / nth of the linear theta map
+      // per padded column, each the sine of an angle measured from the nearer
+      // pole or from the equator (exact zeros and ones at the poles and the
+      // equator), rounded once to FP32
+      std::vector<float2> tn(G.LD);
+      for (int jj = 0; jj < G.LD; ++jj) {
+        const double j = (double)(jj - G.PJ), m = std::min(j, d.nth - j);
+        tn[jj] = make_float2((float)std::sin(M_PI * m / d.nth), (float)std::sin(M_PI * (d.nth - 2.0 * j) / (2.0 * d.nth)));
+      }
+      if ((e = dalloc(&c->th_n32, tn.size()))) return fail(e);
+      PIC_CUDA(cudaMemcpy(c->th_n32, tn.data(), tn.size() * sizeof(float2), cudaMemcpyHostToDevice));
     }
     c->tiles.row0 = -G.g;
     if ((e = alloc_bins(c, d.tile_shape))) return fail(e);
@@ -1089,6 +1100,7 @@ extern "C" int pic_destroy(pic_ctx *c) {
   cudaFree(c->metric_buf);
   for (int k = 0; k < 6; ++k) { cudaFree(c->f[k]); cudaFree(c->f32[k]); }
   cudaFree(c->r_n32);
+  cudaFree(c->th_n32);
   cudaFree(c->d_tile_maps);
   for (int k = 0; k < 3; ++k) { cudaFree(c->F[k]); cudaFree(c->Ft[k]); cudaFree(c->acc[k]); }
   cudaFree(c->Q); cudaFree(c->Qa); cudaFree(c->Qt); cudaFree(c->gsnap); cudaFree(c->sig);

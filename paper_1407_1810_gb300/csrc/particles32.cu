@@ -60,10 +60,12 @@ struct Args32 {
   // grows linearly with the step count)
   float dt_lo, inv_dxi_lo, k2_hi, k2_lo;  // k2 = nth / pi (linear theta map)
   float b0_lo, qmdt;     // qmdt = (q/m) dt rounded once
+  float pi_nth;          // pi / nth (linear theta map: angle per column)
   const long long *qexp;    // fixed-point exponent e: one flux unit is 2^(e - KFIX)
   const int64_t *ids;       // particle ids (read only for an axis-crossing tie)
   AxisTies ties;
   const float *r_n;         // f_r(i) per padded row (FP32)
+  const float2 *th_n;       // (sin, cos) of the node angle per padded column (FP32, linear theta map)
   const float *f[6];        // FP32 field copies (padded)
   long long *acc[3];        // global fixed-point flux accumulators (padded)
   int *err;
@@ -89,10 +91,12 @@ struct SmemAcc {  // window accessors (shared memory)
   int *hi;                  // 3 * WN : sums of the high parts
   int *lo;                  // 3 * WN : sums of the low parts
   const float *rn;          // f_r(i) of the window's rows
+  const float2 *tn;         // (sin, cos) of the node angles of the window's columns
   int wi0, wj0;
   float fs;                 // flux units per unit charge, 2^(KFIX - e)
   __device__ float fld(int c, int i, int j) const { return f[c * WN + (i - wi0) * WJ + (j - wj0)]; }
   __device__ float rad(int i) const { return rn[i - wi0]; }
+  __device__ float2 ang(int j) const { return tn[j - wj0]; }
   // unconditional: a test for zero terms would branch around every atomic,
   // which costs more than adding the rare zero
   __device__ void add(int k, int i, int j, int h, int l) const {
@@ -107,6 +111,7 @@ struct GlobAcc {  // global-memory accessors (particles outside the window)
   float fs;
   __device__ float fld(int c, int i, int j) const { return A->f[c][pidx(*A, i, j)]; }
   __device__ float rad(int i) const { return A->r_n[i + A->PI]; }
+  __device__ float2 ang(int j) const { return A->th_n[j + A->PJ]; }
   __device__ void add(int k, int i, int j, int h, int l) const {
     const long long v = ((long long)h << SPLIT) + (long long)l;
     if (v) atomicAdd(reinterpret_cast<unsigned long long *>(A->acc[k] + pidx(*A, i, j)), (unsigned long long)v);
@@ -132,20 +137,22 @@ __device__ inline float bilin(const W &w, int c, int i, int j, float a, float b)
          (1.f - a) * b * w.fld(c, i, j + 1) + a * b * w.fld(c, i + 1, j + 1);
 }
 
-// Villasenor-Buneman fluxes of a straight path p -> q inside cell (i, j),
-// local coordinates in [0, 1] (Eq. Jcons, Sec. 3.3)
-template <class W>
+// Villasenor-Buneman fluxes of a straight path p -> q inside cell (i, j)
+// (local coordinates in [0, 1], Eq. Jcons, Sec. 3.3).  GUARD skips the terms
+// of a zero component, which the segments of a split path often have; a zero
+// term adds nothing to the exact sums, so either form gives the same bits.
+template <bool GUARD = true, class W>
 __device__ inline void vb_seg(const W &w, float scale, int i, int j, float p1, float p2, float q1, float q2) {
   const float d1 = q1 - p1, d2 = q2 - p2, m1 = 0.5f * (p1 + q1), m2 = 0.5f * (p2 + q2);
   const float a = scale * d1, b = scale * d2;
   int h, l;
-  if (a != 0.f) {
+  if (!GUARD || a != 0.f) {
     split_fix(a * (1.f - m2), h, l);
     w.add(0, i, j, h, l);
     split_fix(a * m2, h, l);
     w.add(0, i, j + 1, h, l);
   }
-  if (b != 0.f) {
+  if (!GUARD || b != 0.f) {
     split_fix(b * (1.f - m1), h, l);
     w.add(1, i, j, h, l);
     split_fix(b * m1, h, l);
@@ -197,6 +204,14 @@ __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf
 __device__ __forceinline__ float cross_(float a, float b, float c, float d) { return fma_(a, b, -mul_(c, d)); }
 __device__ __forceinline__ float dot3_(float a0, float a1, float a2, float b0, float b1, float b2) {
   return fma_(a0, b0, fma_(a1, b1, mul_(a2, b2)));
+}
+// sin x and cos x - 1 of a small angle: x (1 - x^2/6 + x^4/120) and
+// -x^2/2 (1 - x^2/12 + x^4/360), relative truncation below x^6/5040 (under
+// 2^-28 for |x| < 0.16)
+__device__ __forceinline__ void sin_cosm1_series(float x, float &s, float &cm1) {
+  const float x2 = mul_(x, x);
+  s = mul_(x, fma_(-x2, fma_(-x2, 0.008333334f, 0.16666667f), 1.f));
+  cm1 = mul_(mul_(-0.5f, x2), fma_(-x2, fma_(-x2, 0.0027777778f, 0.083333336f), 1.f));
 }
 
 // Vay (2008) push, Sec. 2, as u' - u: with a = u + (q dt/m) E + v x tau and
@@ -279,6 +294,18 @@ __device__ inline bool step32(const Args32 &A, const W &w, int64_t k, uint32_t &
   if (F.th_ea) {  // cos th = 1 - 2 x2/nth, sin th = 2 sqrt(x2 (nth - x2))/nth
     ct = (rest - x2) * A.inv_nth;
     st = 2.f * sqrtf(fmaxf(x2 * rest, 0.f)) * A.inv_nth;
+  } else if (series) {
+    // linear map: the node angle's sine and cosine from the column table,
+    // turned by the offset's angle (at most pi / nth, nth >= 32 on the
+    // specialised grids: short series).  The node taken is the one on the
+    // pole's side of the particle in its hemisphere, so both terms of sin th
+    // have one sign and sin th keeps FP32 relative precision up to the poles.
+    const bool north = 2 * cj < A.nth;
+    const float2 n = w.ang(north ? cj : cj + 1);
+    float sb, cb1;
+    sin_cosm1_series(mul_(north ? dy : dy - 1.f, A.pi_nth), sb, cb1);
+    st = fma_(n.y, sb, fma_(n.x, cb1, n.x));   // sin th_n cos b + cos th_n sin b
+    ct = fma_(-n.x, sb, fma_(n.y, cb1, n.y));  // cos th_n cos b - sin th_n sin b
   } else if (x2 <= rest) {
     sincospif(x2 * A.inv_nth, &st, &ct);
   } else {
@@ -338,10 +365,8 @@ __device__ inline bool step32(const Args32 &A, const W &w, int64_t k, uint32_t &
     sd = mul_(2.f, mul_(sh, ch));
     cd1 = mul_(-2.f, mul_(sh, sh));
     D2 = F.th_ea ? A.nth_f * (st * ch + ct * sh) * sh : fmaf(dth, A.k2_hi, dth * A.k2_lo);
-  } else {  // sin x = x (1 - x^2/6 + x^4/120), cos x - 1 = -x^2/2 (1 - x^2/12 + x^4/360)
-    const float d2 = mul_(dth, dth);
-    sd = mul_(dth, fma_(-d2, fma_(-d2, 0.008333334f, 0.16666667f), 1.f));
-    cd1 = mul_(mul_(-0.5f, d2), fma_(-d2, fma_(-d2, 0.0027777778f, 0.083333336f), 1.f));
+  } else {
+    sin_cosm1_series(dth, sd, cd1);
     D2 = fmaf(dth, A.k2_hi, dth * A.k2_lo);
   }
   // new cell and offsets (carries are exact integers)
@@ -381,13 +406,14 @@ __device__ inline bool step32(const Args32 &A, const W &w, int64_t k, uint32_t &
   // length (zero terms are skipped).  Branch-free, so lanes that cross and
   // lanes that do not run the same instructions -- except when no lane of
   // the converged group crosses a line (a vote): then the path is its one
-  // nonzero segment, the same call with the same arguments as in the general
-  // form, which that group takes alone.  The move of one step is a small
+  // nonzero segment, the same terms as in the general form (without the
+  // zero-component tests: a zero term adds nothing), which that group takes
+  // alone.  The move of one step is a small
   // fraction of a cell away from the inner boundary (about 0.35 / r of one at
   // 4096 log cells), so most warps take it there.
   const float scale = qw * w.fs;  // exact: fs is a power of two
   if (__all_sync(__activemask(), (kx | ky) == 0)) {
-    vb_seg(w, scale, ci, cj, dx, dy, nx, ny);
+    vb_seg<false>(w, scale, ci, cj, dx, dy, nx, ny);
   } else {
   const float Dxs = kx == 0 ? nx - dx : (kx > 0 ? (1.f - dx) + nx : -(dx + (1.f - nx)));
   const float Dys = ky == 0 ? ny - dy : (ky > 0 ? (1.f - dy) + ny : -(dy + (1.f - ny)));
@@ -579,6 +605,7 @@ __device__ __forceinline__ void tiles32_block(const Args32 &A, const Parts32 &P,
   int *const shi = reinterpret_cast<int *>(sbuf + BX_::SF);    // 3 WN: then the accumulators
   int *const slo = shi + 3 * WN;                               // 3 WN
   __shared__ float srn[WI];
+  __shared__ float2 stn[WJ];
   __shared__ int sdead, sok;
   __shared__ __align__(8) uint64_t sbar;
   int dead = 0;
@@ -616,6 +643,8 @@ __device__ __forceinline__ void tiles32_block(const Args32 &A, const Parts32 &P,
       sok = ok ? 1 : 0;
     }
     for (int e = threadIdx.x; e < WI; e += NT) srn[e] = A.r_n[wi0 + e + A.PI];
+    if (SPEC != SPEC_GENERIC)
+      for (int e = threadIdx.x; e < WJ; e += NT) stn[e] = A.th_n[wj0 + e + A.PJ];
     __syncthreads();
     if (!sok) return;
     for (int e = threadIdx.x; e < WN; e += NT) {
@@ -626,7 +655,7 @@ __device__ __forceinline__ void tiles32_block(const Args32 &A, const Parts32 &P,
     __syncthreads();  // the staging area becomes the accumulators
     for (int e = threadIdx.x; e < 3 * WN; e += NT) { shi[e] = 0; slo[e] = 0; }
     __syncthreads();
-    const SmemAcc<WJ, WN> sw{sf, shi, slo, srn, wi0, wj0, fs};
+    const SmemAcc<WJ, WN> sw{sf, shi, slo, srn, stn, wi0, wj0, fs};
     {
       const int t = threadIdx.x;
       auto fetch = [&](int buf, int64_t k) {
@@ -663,7 +692,7 @@ __device__ __forceinline__ void tiles32_block(const Args32 &A, const Parts32 &P,
     }
     if (threadIdx.x == 0 && sdead) add_ll(A.cnt + CNT_DELETED, sdead);
   } else {  // particles outside any bin (injected since the last sort)
-    const SmemAcc<WJ, WN> none{nullptr, nullptr, nullptr, nullptr, 0, 0, fs};
+    const SmemAcc<WJ, WN> none{nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, fs};
     const int64_t k = A.sorted_end + (int64_t)(blk - A.nunits) * NT + threadIdx.x;
     if (k < A.n_used) process<SPEC>(A, P, k, false, none, 0, 0, 0, 0, dead);
     if (dead) add_ll(A.cnt + CNT_DELETED, dead);
@@ -1075,6 +1104,8 @@ Args32 make_args(pic_ctx *c, double t) {
   A.ids = c->p32.id;
   A.ties = axis_ties(c);
   A.r_n = c->r_n32;
+  A.th_n = c->th_n32;
+  A.pi_nth = (float)(M_PI / G.nth);
   for (int k = 0; k < 6; ++k) A.f[k] = c->f32[k];
   for (int k = 0; k < 3; ++k) A.acc[k] = c->acc[k];
   A.err = c->d_err;
@@ -1156,11 +1187,13 @@ int tiles32_setup(pic_ctx *c) {
   return 0;
 }
 
-// the compile-time specialisation of the tile kernel a context takes
+// the compile-time specialisation of the tile kernel a context takes (the
+// monopole one turns each column's node angle by the offset with a short
+// series: nth >= 32 keeps that angle below pi / 32)
 static int tile_spec(const pic_ctx *c) {
   const pic_desc &d = c->d;
   return c->small_steps && d.r_map == PIC_R_LOG && d.pusher == PIC_VAY
-             ? (d.th_map == PIC_TH_LINEAR && d.vacuum == PIC_VAC_MONOPOLE ? SPEC_MONOPOLE
+             ? (d.th_map == PIC_TH_LINEAR && d.vacuum == PIC_VAC_MONOPOLE && d.nth >= 32 ? SPEC_MONOPOLE
                 : d.th_map == PIC_TH_EQUAL_AREA && d.vacuum == PIC_VAC_MONOPOLE_ROTATOR ? SPEC_ROTATOR
                                                                                          : SPEC_GENERIC)
              : SPEC_GENERIC;

@@ -142,6 +142,7 @@ struct pic_ctx {
   double *Ft[3] = {};     // filter double buffer
   float *f32[6] = {};     // FP32 gather copies (FP32 path)
   float *r_n32 = nullptr; // f_r(i) per padded row, FP32 (FP32 path)
+  float2 *th_n32 = nullptr; // (sin, cos) of the linear map's node angle per padded column (FP32 path)
   long long *acc[3] = {}; // fixed-point flux accumulators (FP32 path)
   alignas(64) unsigned char tile_maps[3][6 * 128] = {}; // FP32: field tensor maps per tile shape (TMA)
   unsigned char *d_tile_maps = nullptr;  // the same maps in device memory (batched ensemble launches)
