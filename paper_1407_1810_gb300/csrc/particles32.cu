@@ -131,8 +131,18 @@ __device__ inline void split_fix(float cs, int &h, int &l) {
   l = __float_as_int(__fadd_rn(lf, MAGIC)) - 0x4B400000;
 }
 
-template <class W>
+// bilinear interpolation of field c in cell (i, j) at offsets (a, b).  LERP:
+// two linear interpolations along i and one along j (six operations, no
+// weights); otherwise the four weights, shared by the components that share a
+// staggered point (the form the kernels that hold more live values keep: the
+// other one makes them spill)
+template <bool LERP, class W>
 __device__ inline float bilin(const W &w, int c, int i, int j, float a, float b) {
+  if (LERP) {
+    const float v0 = fmaf(a, w.fld(c, i + 1, j) - w.fld(c, i, j), w.fld(c, i, j));
+    const float v1 = fmaf(a, w.fld(c, i + 1, j + 1) - w.fld(c, i, j + 1), w.fld(c, i, j + 1));
+    return fmaf(b, v1 - v0, v0);
+  }
   return (1.f - a) * (1.f - b) * w.fld(c, i, j) + a * (1.f - b) * w.fld(c, i + 1, j) +
          (1.f - a) * b * w.fld(c, i, j + 1) + a * b * w.fld(c, i + 1, j + 1);
 }
@@ -326,12 +336,13 @@ __device__ inline bool step32(const Args32 &A, const W &w, int64_t k, uint32_t &
       const bool hx = dx >= 0.5f, hy = dy >= 0.5f;
       const int ih = hx ? ci : ci - 1, jh = hy ? cj : cj - 1;
       const float ah = hx ? dx - 0.5f : dx + 0.5f, bh = hy ? dy - 0.5f : dy + 0.5f;
-      E[0] += bilin(w, ER, ih, cj, ah, dy);
-      E[1] += bilin(w, ETH, ci, jh, dx, bh);
-      E[2] += bilin(w, EPH, ci, cj, dx, dy);
-      B[0] += bilin(w, BR, ci, jh, dx, bh);
-      B[1] += bilin(w, BTH, ih, cj, ah, dy);
-      B[2] += bilin(w, BPH, ih, jh, ah, bh);
+      constexpr bool L = SPEC == SPEC_MONOPOLE;
+      E[0] += bilin<L>(w, ER, ih, cj, ah, dy);
+      E[1] += bilin<L>(w, ETH, ci, jh, dx, bh);
+      E[2] += bilin<L>(w, EPH, ci, cj, dx, dy);
+      B[0] += bilin<L>(w, BR, ci, jh, dx, bh);
+      B[1] += bilin<L>(w, BTH, ih, cj, ah, dy);
+      B[2] += bilin<L>(w, BPH, ih, jh, ah, bh);
     }
     const float u[3] = {ur, ut, up};
     // local (r, th, ph) is a right-handed orthonormal frame: the Cartesian
@@ -404,15 +415,17 @@ __device__ inline bool step32(const Args32 &A, const W &w, int64_t k, uint32_t &
   // Three segments, split where the path crosses the x and y grid lines in
   // the order it meets them; a line not crossed puts its segment at zero
   // length (zero terms are skipped).  Branch-free, so lanes that cross and
-  // lanes that do not run the same instructions -- except when no lane of
-  // the converged group crosses a line (a vote): then the path is its one
-  // nonzero segment, the same terms as in the general form (without the
-  // zero-component tests: a zero term adds nothing), which that group takes
-  // alone.  The move of one step is a small
+  // lanes that do not run the same instructions -- except for two votes of
+  // the converged group: when no lane crosses a line the path is its one
+  // nonzero segment (the same terms as in the general form, without the
+  // zero-component tests: a zero term adds nothing), and when no lane crosses
+  // both lines the third segment is empty for every lane.  Each lane's terms
+  // are the same whichever form its group takes.  The move of one step is a small
   // fraction of a cell away from the inner boundary (about 0.35 / r of one at
   // 4096 log cells), so most warps take it there.
   const float scale = qw * w.fs;  // exact: fs is a power of two
-  if (__all_sync(__activemask(), (kx | ky) == 0)) {
+  const unsigned grp = __activemask();
+  if (__all_sync(grp, (kx | ky) == 0)) {
     vb_seg<false>(w, scale, ci, cj, dx, dy, nx, ny);
   } else {
   const float Dxs = kx == 0 ? nx - dx : (kx > 0 ? (1.f - dx) + nx : -(dx + (1.f - nx)));
@@ -431,6 +444,13 @@ __device__ inline bool step32(const Args32 &A, const W &w, int64_t k, uint32_t &
   // cell of the middle segment and the entry point there
   const int mi = ci + (xfirst ? kx : 0), mj = cj + (xfirst ? 0 : ky);
   const float e1x = (xfirst && kx) ? Xn : c1x, e1y = (!xfirst) ? Yn : c1y;
+  vb_seg(w, scale, ci, cj, dx, dy, c1x, c1y);
+  if (__all_sync(grp, (kx & ky) == 0)) {
+    // no lane of the group crosses both lines (kx & ky is nonzero only when
+    // both are): the middle segment ends at the end point and the third has
+    // zero length, as in the general form below
+    vb_seg(w, scale, mi, mj, e1x, e1y, nx, ny);
+  } else {
   // second crossing point, in the frame of the middle cell
   float c2x, c2y;
   if (kx && ky) {
@@ -440,9 +460,9 @@ __device__ inline bool step32(const Args32 &A, const W &w, int64_t k, uint32_t &
     c2x = nx; c2y = ny;
   }
   const float e2x = (kx && ky && !xfirst) ? Xn : c2x, e2y = (kx && ky && xfirst) ? Yn : c2y;
-  vb_seg(w, scale, ci, cj, dx, dy, c1x, c1y);
   vb_seg(w, scale, mi, mj, e1x, e1y, c2x, c2y);
   vb_seg(w, scale, ci + kx, cj + ky, e2x, e2y, nx, ny);
+  }
   }
   // azimuthal flux: charge crossing the meridional half-plane, qw dphi / 2 pi,
   // area weights at the midpoint of the grid path
